@@ -1,0 +1,394 @@
+/*
+ * pg_oracle.c - plain FP64 CPU oracle for Gaussian-density voxelization
+ * (ParticleGrid, arXiv 2211.08506).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark may load this file's library.  It shares no code, header, table or
+ * constant with the CUDA library; it is slow on purpose and written so each function
+ * can be checked against the paper by eye.
+ *
+ * What it computes (Sec. III-A, Eq. 1, with the point-sampled, unnormalised reading):
+ *
+ *   G[b,c,i,j,k] = sum over atoms a of molecule b with elem(a) = c of
+ *                  chi(d) * exp(-|d|^2 / (2 sigma_c^2)),
+ *   d = v_ijk - x_a,  v_ijk = o_b + ((i+1/2) h_x, (j+1/2) h_y, (k+1/2) h_z),
+ *
+ * where, for periodic cells (Sec. III-A, nearest image), each component of d is replaced
+ * by its minimum image d - L round(d/L) with L = n h on that axis, and chi is the cutoff
+ * indicator: [|d|^2 <= r_c^2] (sphere), [max_a |d_a| <= r_c] (box) or 1 (none), with
+ * r_c = k sigma_c.  Output layout [B][C][nx][ny][nz], z fastest.
+ *
+ * The coordinate gradient of L = <W, G> (Sec. IV-C, generalised from the MSE loss to any
+ * upstream weight W = dL/dG) is
+ *
+ *   dL/dx_a = sum_v W[b, elem(a), v] * chi(d) * exp(-|d|^2/(2 sigma^2)) * d / sigma^2.
+ *
+ * Readings taken where the paper is silent or differs from the point-sampled form:
+ * voxel values are sampled at voxel centres; sigma is the standard deviation; the cutoff
+ * is inclusive; atoms outside the grid still contribute wherever their support reaches.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { PGO_SPHERE = 0, PGO_NONE = 1, PGO_BOX = 2 };
+enum { PGO_OK = 0, PGO_BAD_ARG = 1, PGO_BAD_ELEM = 2, PGO_UNSUPPORTED = 3 };
+
+typedef struct {
+    int32_t n_mol;
+    const int32_t *mol_off;  /* [B+1] */
+    const double *coords;    /* [N][3] */
+    const int32_t *elem;     /* [N] */
+    const double *origin;    /* [B][3] */
+    const double *spacing;   /* [B][3] */
+    int32_t nx, ny, nz, n_channels;
+    const double *sigma;     /* [C] */
+    double cutoff_k;
+    int32_t cutoff;          /* PGO_SPHERE / PGO_NONE / PGO_BOX */
+    int32_t periodic;
+} pgo_problem;
+
+/* Voxel centre along one axis: o + (i + 1/2) h. */
+static double centre(double o, double h, long i) { return o + ((double)i + 0.5) * h; }
+
+/* Nearest-image displacement on a periodic axis of length L (Sec. III-A). */
+static double min_image(double d, double L) { return d - L * round(d / L); }
+
+/* Cutoff indicator chi for displacement (dx, dy, dz) and radius r. */
+static int inside(int cutoff, double dx, double dy, double dz, double r)
+{
+    if (cutoff == PGO_SPHERE) return dx * dx + dy * dy + dz * dz <= r * r;
+    if (cutoff == PGO_BOX) return fabs(dx) <= r && fabs(dy) <= r && fabs(dz) <= r;
+    return 1;
+}
+
+static long grid_index(const pgo_problem *p, long b, long c, long i, long j, long k)
+{
+    return (((b * p->n_channels + c) * p->nx + i) * p->ny + j) * p->nz + k;
+}
+
+static int check(const pgo_problem *p)
+{
+    if (!p || p->n_mol < 0 || p->nx <= 0 || p->ny <= 0 || p->nz <= 0 || p->n_channels <= 0)
+        return PGO_BAD_ARG;
+    if (p->cutoff != PGO_SPHERE && p->cutoff != PGO_NONE && p->cutoff != PGO_BOX)
+        return PGO_BAD_ARG;
+    for (int b = 0; b < p->n_mol; ++b)
+        for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a)
+            if (p->elem[a] < 0 || p->elem[a] >= p->n_channels) return PGO_BAD_ELEM;
+    return PGO_OK;
+}
+
+/* Displacement d = v - x on axis ax for voxel index i of molecule b. */
+static double disp(const pgo_problem *p, int b, int ax, long i, double x)
+{
+    const int n[3] = {p->nx, p->ny, p->nz};
+    double o = p->origin[3 * b + ax], h = p->spacing[3 * b + ax];
+    double d = centre(o, h, i) - x;
+    if (p->periodic) d = min_image(d, n[ax] * h);
+    return d;
+}
+
+/*
+ * Brute force: every voxel of every channel sums over every atom of the molecule, in
+ * atom order.  This is the definition with nothing skipped.
+ */
+static void brute_molecule(const pgo_problem *p, int b, double *out)
+{
+    for (int c = 0; c < p->n_channels; ++c) {
+        double s2 = 2.0 * p->sigma[c] * p->sigma[c];
+        double r = p->cutoff_k * p->sigma[c];
+        for (long i = 0; i < p->nx; ++i)
+            for (long j = 0; j < p->ny; ++j)
+                for (long k = 0; k < p->nz; ++k) {
+                    double s = 0.0;
+                    for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a) {
+                        if (p->elem[a] != c) continue;
+                        double dx = disp(p, b, 0, i, p->coords[3 * a + 0]);
+                        double dy = disp(p, b, 1, j, p->coords[3 * a + 1]);
+                        double dz = disp(p, b, 2, k, p->coords[3 * a + 2]);
+                        if (inside(p->cutoff, dx, dy, dz, r))
+                            s += exp(-(dx * dx + dy * dy + dz * dz) / s2);
+                    }
+                    out[grid_index(p, b, c, i, j, k)] = s;
+                }
+    }
+}
+
+/*
+ * Index range [lo, hi] on one axis that holds every voxel centre within r of x
+ * (widened by one voxel each side; chi decides exactly).  Non-periodic ranges are
+ * clamped to the grid; periodic ranges are left unwrapped but cover at most n
+ * consecutive indices, so after wrapping no voxel is visited twice.
+ */
+static void support(const pgo_problem *p, int b, int ax, double x, double r, long *lo, long *hi)
+{
+    const int n[3] = {p->nx, p->ny, p->nz};
+    if (p->cutoff == PGO_NONE) {
+        *lo = 0;
+        *hi = n[ax] - 1;
+        return;
+    }
+    double o = p->origin[3 * b + ax], h = p->spacing[3 * b + ax];
+    long l = (long)floor((x - r - o) / h - 0.5) - 1;
+    long u = (long)ceil((x + r - o) / h - 0.5) + 1;
+    if (p->periodic) {
+        if (u - l + 1 > n[ax]) u = l + n[ax] - 1;
+    } else {
+        if (l < 0) l = 0;
+        if (u > n[ax] - 1) u = n[ax] - 1;
+    }
+    *lo = l;
+    *hi = u;
+}
+
+static long wrap_index(long i, long n) { return ((i % n) + n) % n; }
+
+/*
+ * Support-box mode: the same sum, visited atom by atom over each atom's cutoff box
+ * only (chi is zero outside it).  Per voxel the atoms are still added in atom order, so
+ * the result equals brute force bit for bit.  With eps > 0 it instead splits each
+ * contribution into out (strictly inside, |d|^2 < r^2 (1 - eps)) and band (within eps
+ * relative of the cutoff surface), for parity checks of an FP32 cutoff test.
+ */
+static void bbox_molecule(const pgo_problem *p, int b, double *out, double eps, double *band)
+{
+    long per_mol = (long)p->n_channels * p->nx * p->ny * p->nz;
+    memset(out + b * per_mol, 0, sizeof(double) * per_mol);
+    if (band) memset(band + b * per_mol, 0, sizeof(double) * per_mol);
+    for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a) {
+        int c = p->elem[a];
+        double s2 = 2.0 * p->sigma[c] * p->sigma[c];
+        double r = p->cutoff_k * p->sigma[c];
+        double x = p->coords[3 * a + 0], y = p->coords[3 * a + 1], z = p->coords[3 * a + 2];
+        long ilo, ihi, jlo, jhi, klo, khi;
+        support(p, b, 0, x, r, &ilo, &ihi);
+        support(p, b, 1, y, r, &jlo, &jhi);
+        support(p, b, 2, z, r, &klo, &khi);
+        for (long iu = ilo; iu <= ihi; ++iu) {
+            long i = p->periodic ? wrap_index(iu, p->nx) : iu;
+            double dx = disp(p, b, 0, i, x);
+            for (long ju = jlo; ju <= jhi; ++ju) {
+                long j = p->periodic ? wrap_index(ju, p->ny) : ju;
+                double dy = disp(p, b, 1, j, y);
+                for (long ku = klo; ku <= khi; ++ku) {
+                    long k = p->periodic ? wrap_index(ku, p->nz) : ku;
+                    double dz = disp(p, b, 2, k, z);
+                    if (!inside(p->cutoff, dx, dy, dz, r)) continue;
+                    double d2 = dx * dx + dy * dy + dz * dz;
+                    double g = exp(-d2 / s2);
+                    long v = grid_index(p, b, c, i, j, k);
+                    if (eps > 0.0 && p->cutoff != PGO_NONE) {
+                        double m2 = (p->cutoff == PGO_SPHERE)
+                                        ? d2
+                                        : fmax(dx * dx, fmax(dy * dy, dz * dz));
+                        if (fabs(m2 - r * r) <= eps * r * r) {
+                            band[v] += g;
+                            continue;
+                        }
+                    }
+                    out[v] += g;
+                }
+            }
+        }
+    }
+}
+
+static int threads_or_default(int n_threads)
+{
+#ifdef _OPENMP
+    return n_threads > 0 ? n_threads : omp_get_max_threads();
+#else
+    (void)n_threads;
+    return 1;
+#endif
+}
+
+/* mode 0: brute force, mode 1: support box.  out: [B][C][nx][ny][nz]. */
+int pgo_voxelize(const pgo_problem *p, int mode, double *out, int n_threads)
+{
+    int st = check(p);
+    if (st) return st;
+    int nt = threads_or_default(n_threads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int b = 0; b < p->n_mol; ++b) {
+        if (mode == 0)
+            brute_molecule(p, b, out);
+        else
+            bbox_molecule(p, b, out, 0.0, NULL);
+    }
+    return PGO_OK;
+}
+
+/* Split into strictly-inside and cutoff-band contributions (see bbox_molecule). */
+int pgo_voxelize_band(const pgo_problem *p, double eps, double *out_in, double *out_band,
+                      int n_threads)
+{
+    int st = check(p);
+    if (st) return st;
+    if (!(eps > 0.0)) return PGO_BAD_ARG;
+    int nt = threads_or_default(n_threads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int b = 0; b < p->n_mol; ++b) bbox_molecule(p, b, out_in, eps, out_band);
+    return PGO_OK;
+}
+
+/*
+ * Separable form (Sec. III-A after Eq. 5; Sec. VI-A): for the no-cutoff and box-cutoff
+ * indicators the Gaussian factors per axis, so the grid is the per-channel sum of outer
+ * products of three per-axis tables
+ *   g_x[a][i] = [|d_x| <= r] exp(-d_x^2 / 2 sigma^2)  (the bracket is 1 with no cutoff)
+ * and G[c,i,j,k] = sum_{a: elem(a)=c} g_x[a][i] g_y[a][j] g_z[a][k].
+ * The spherical indicator does not factor; that case is rejected.
+ */
+int pgo_separable(const pgo_problem *p, double *out, int n_threads)
+{
+    int st = check(p);
+    if (st) return st;
+    if (p->cutoff == PGO_SPHERE) return PGO_UNSUPPORTED;
+    int nt = threads_or_default(n_threads);
+    (void)nt;
+    long per_mol = (long)p->n_channels * p->nx * p->ny * p->nz;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int b = 0; b < p->n_mol; ++b) {
+        double *gx = malloc(sizeof(double) * p->nx);
+        double *gy = malloc(sizeof(double) * p->ny);
+        double *gz = malloc(sizeof(double) * p->nz);
+        memset(out + b * per_mol, 0, sizeof(double) * per_mol);
+        for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a) {
+            int c = p->elem[a];
+            double s2 = 2.0 * p->sigma[c] * p->sigma[c];
+            double r = p->cutoff_k * p->sigma[c];
+            const int n[3] = {p->nx, p->ny, p->nz};
+            double *g[3] = {gx, gy, gz};
+            for (int ax = 0; ax < 3; ++ax)
+                for (long i = 0; i < n[ax]; ++i) {
+                    double d = disp(p, b, ax, i, p->coords[3 * a + ax]);
+                    int keep = (p->cutoff == PGO_NONE) || fabs(d) <= r;
+                    g[ax][i] = keep ? exp(-d * d / s2) : 0.0;
+                }
+            for (long i = 0; i < p->nx; ++i)
+                for (long j = 0; j < p->ny; ++j)
+                    for (long k = 0; k < p->nz; ++k)
+                        out[grid_index(p, b, c, i, j, k)] += gx[i] * gy[j] * gz[k];
+        }
+        free(gx);
+        free(gy);
+        free(gz);
+    }
+    return PGO_OK;
+}
+
+/*
+ * Coordinate gradient of L = <W, G> (Sec. IV-C):
+ *   dL/dx_a = sum_v W(v) chi(d) exp(-|d|^2/2 sigma^2) d / sigma^2,  d = v - x_a.
+ * mode 0 visits every voxel of the atom's channel, mode 1 only its cutoff box.
+ * W has the grid layout [B][C][nx][ny][nz]; grad is [N][3].
+ */
+int pgo_gradient(const pgo_problem *p, int mode, const double *W, double *grad, int n_threads)
+{
+    int st = check(p);
+    if (st) return st;
+    int nt = threads_or_default(n_threads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int b = 0; b < p->n_mol; ++b) {
+        for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a) {
+            int c = p->elem[a];
+            double sg2 = p->sigma[c] * p->sigma[c];
+            double r = p->cutoff_k * p->sigma[c];
+            double x = p->coords[3 * a + 0], y = p->coords[3 * a + 1], z = p->coords[3 * a + 2];
+            long ilo = 0, ihi = p->nx - 1, jlo = 0, jhi = p->ny - 1, klo = 0, khi = p->nz - 1;
+            if (mode == 1) {
+                support(p, b, 0, x, r, &ilo, &ihi);
+                support(p, b, 1, y, r, &jlo, &jhi);
+                support(p, b, 2, z, r, &klo, &khi);
+            }
+            double gx = 0.0, gy = 0.0, gz = 0.0;
+            for (long iu = ilo; iu <= ihi; ++iu) {
+                long i = p->periodic ? wrap_index(iu, p->nx) : iu;
+                double dx = disp(p, b, 0, i, x);
+                for (long ju = jlo; ju <= jhi; ++ju) {
+                    long j = p->periodic ? wrap_index(ju, p->ny) : ju;
+                    double dy = disp(p, b, 1, j, y);
+                    for (long ku = klo; ku <= khi; ++ku) {
+                        long k = p->periodic ? wrap_index(ku, p->nz) : ku;
+                        double dz = disp(p, b, 2, k, z);
+                        if (!inside(p->cutoff, dx, dy, dz, r)) continue;
+                        double w = W[grid_index(p, b, c, i, j, k)] *
+                                   exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * sg2));
+                        gx += w * dx;
+                        gy += w * dy;
+                        gz += w * dz;
+                    }
+                }
+            }
+            grad[3 * a + 0] = gx / sg2;
+            grad[3 * a + 1] = gy / sg2;
+            grad[3 * a + 2] = gz / sg2;
+        }
+    }
+    return PGO_OK;
+}
+
+/*
+ * Central finite differences of L = <W, G> with the support frozen: chi and the
+ * periodic image are taken at the unperturbed position, and only the Gaussian sees the
+ * shifted atom.  That is the derivative of the piecewise-smooth loss away from the
+ * cutoff surface, which is what the analytic gradient computes.  Only atom a's own
+ * terms depend on x_a (G is a sum over atoms), so the difference is formed from them.
+ */
+int pgo_fd_gradient_frozen(const pgo_problem *p, const double *W, double step, double *grad,
+                           int n_threads)
+{
+    int st = check(p);
+    if (st) return st;
+    if (!(step > 0.0)) return PGO_BAD_ARG;
+    int nt = threads_or_default(n_threads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int b = 0; b < p->n_mol; ++b) {
+        for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a) {
+            int c = p->elem[a];
+            double s2 = 2.0 * p->sigma[c] * p->sigma[c];
+            double r = p->cutoff_k * p->sigma[c];
+            double x = p->coords[3 * a + 0], y = p->coords[3 * a + 1], z = p->coords[3 * a + 2];
+            double lp[3] = {0, 0, 0}, lm[3] = {0, 0, 0};
+            for (long i = 0; i < p->nx; ++i) {
+                double dx = disp(p, b, 0, i, x);
+                for (long j = 0; j < p->ny; ++j) {
+                    double dy = disp(p, b, 1, j, y);
+                    for (long k = 0; k < p->nz; ++k) {
+                        double dz = disp(p, b, 2, k, z);
+                        if (!inside(p->cutoff, dx, dy, dz, r)) continue;
+                        double w = W[grid_index(p, b, c, i, j, k)];
+                        double d[3] = {dx, dy, dz};
+                        for (int ax = 0; ax < 3; ++ax) {
+                            double e[3] = {d[0], d[1], d[2]};
+                            e[ax] = d[ax] - step; /* atom moved by +step */
+                            lp[ax] += w * exp(-(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) / s2);
+                            e[ax] = d[ax] + step; /* atom moved by -step */
+                            lm[ax] += w * exp(-(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) / s2);
+                        }
+                    }
+                }
+            }
+            for (int ax = 0; ax < 3; ++ax) grad[3 * a + ax] = (lp[ax] - lm[ax]) / (2.0 * step);
+        }
+    }
+    return PGO_OK;
+}
+
+/* <W, G> for the whole batch (used by the raw finite-difference driver). */
+double pgo_inner(const double *W, const double *G, long n)
+{
+    double s = 0.0;
+    for (long i = 0; i < n; ++i) s += W[i] * G[i];
+    return s;
+}
