@@ -1,0 +1,423 @@
+#!/usr/bin/env python
+"""Throughput of batched Gaussian-density voxelization on GB300.
+
+One step = one pass of the voxelization hot path over one batch.  Default workload: the
+QM9-shaped batch (4096 molecules, 3-29 atoms, 5 channels of 32^3 at 0.5 A, per-element
+sigma, spherical cutoff 3 sigma, FP32 grids; 2.68 GB written per step, larger than L2),
+autotuned, CUDA-graph captured.  Prints one JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Under torchrun each rank voxelizes its own batch of the same size (weak scaling, no
+collective on the data path); the timed region is bracketed by barriers and the slowest
+rank's time is reported.  --impl reference times the FP64 CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "grids/sec (and voxels/sec) at 32^3x5ch FP32 vs FP16/BF16 form; fraction of HBM roofline"
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self._reader = threading.Thread(target=self._read, daemon=True)
+        self._reader.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def mark(self, which):
+        if which == "start":
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self._reader.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "samples": 0}
+        inside = [r for t, r in self.rows if self.t0 and self.t1 and self.t0 <= t <= self.t1]
+        rows = inside if inside else [r for _, r in self.rows]
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if len(r) > 8 and num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if len(r) > 8 and num(r[2]) is not None]
+        reasons = set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            if len(r) > 8:
+                for name, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons),
+                "samples": len(rows),
+                "samples_in_timed_region": len(inside)}
+
+
+def kernel_source_sha():
+    h = hashlib.sha256()
+    for f in ("pg_direct.cu", "pg_separable.cu"):
+        p = os.path.join(ROOT, "paper_2211_08506_gb300", "csrc", f)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str, kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current
+    kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            entries = json.load(f)
+    except Exception:
+        return None
+    e = entries.get(f"{kernel}:{workload}")
+    if not e or e.get("kernel_source_sha") != kernel_source_sha():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def cpu_baseline(wl, budget_s=12.0, reps_cap=4):
+    """Time the FP64 oracle (support-box mode, all host cores) on a bounded sample."""
+    import oracle
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    n = wl.batch.n_mol
+    calib = wl.batch.subset(range(min(n, 64)))
+    prob = oracle.Problem.from_workload(wl, batch=calib)
+    t = time.perf_counter()
+    oracle.voxelize(prob, "bbox", threads)
+    per_mol = (time.perf_counter() - t) / max(1, calib.n_mol)
+    n_sample = max(1, min(n, int(budget_s / max(per_mol, 1e-9) / 2)))
+    sub = wl.batch.subset(range(n_sample))
+    prob = oracle.Problem.from_workload(wl, batch=sub)
+    times = []
+    for _ in range(reps_cap):
+        t = time.perf_counter()
+        oracle.voxelize(prob, "bbox", threads)
+        times.append(time.perf_counter() - t)
+        if sum(times) > budget_s:
+            break
+    best = min(times)
+    return {"value": n_sample / best, "unit": "grids/s", "cores": threads, "kind": "oracle",
+            "sample": f"first {n_sample} molecules of the {wl.name} batch, FP64 support-box "
+                      f"oracle, OpenMP over molecules, best of {len(times)}"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle as it stands, on the host cores, rank 0 only."""
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return
+    import oracle
+    import synth
+
+    oracle.build()
+    wl = synth.workload(args.workload)
+    threads = os.cpu_count() or 1
+    n = wl.batch.n_mol
+    calib = wl.batch.subset(range(min(n, 32)))
+    t = time.perf_counter()
+    oracle.voxelize(oracle.Problem.from_workload(wl, batch=calib), "bbox", threads)
+    per_mol = (time.perf_counter() - t) / calib.n_mol
+    steps = args.steps + args.warmup
+    budget = 150.0
+    per_step = max(1, min(n, int(budget / steps / max(per_mol, 1e-9))))
+    sub = wl.batch.subset(range(per_step))
+    prob = oracle.Problem.from_workload(wl, batch=sub)
+    for _ in range(args.warmup):
+        oracle.voxelize(prob, "bbox", threads)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.voxelize(prob, "bbox", threads)
+    dt = time.perf_counter() - t
+    value = per_step * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "grids/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "description": wl.description,
+                   "batch_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": "grids/s", "cores": threads, "kind": "oracle",
+                         "sample": f"{per_step} molecules of the {wl.name} batch per step"},
+        "e2e": {"value": value, "unit": "grids/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2211_08506_gb300 as pkg
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    pkg.build()
+    from paper_2211_08506_gb300 import api
+
+    wl = synth.workload(args.workload, shard=rank if world > 1 else None)
+    dtype = args.dtype or wl.out_dtype
+    path = args.path
+    grid = api.Grid.from_workload(wl)
+    db = api.DeviceBatch.from_numpy(wl.batch)
+    B = wl.batch.n_mol
+    esz = 4 if dtype == "f32" else 2
+    out_bytes = B * wl.voxels_per_grid * esz
+    out = torch.empty(grid.out_shape(B), dtype=api.DTYPES[dtype][1], device="cuda")
+    stream = torch.cuda.Stream()
+
+    # Untimed: autotune the launch for this bucket, then capture one step in a graph.
+    with torch.cuda.stream(stream):
+        tuning = api.autotune(db, grid, dtype=dtype, path=path, out=out)
+        api.voxelize(db, grid, dtype=dtype, path=path, out=out)
+    api.sync_status(stream)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        api.voxelize(db, grid, dtype=dtype, path=path, out=out)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            graph.replay()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    sampler.mark("start")
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for i in range(args.steps):
+            graph.replay()
+            ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    sampler.mark("stop")
+    if dist:
+        dist.barrier()
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    sampler.stop()
+    assert api.sync_status(stream) == 0
+
+    ms = total_ms / args.steps
+    value = world * B / (ms / 1e3)
+    voxels = world * B * wl.voxels_per_grid / (ms / 1e3)
+
+    # End to end through the public API: pinned host inputs -> plan (graph: H2D + kernel)
+    # -> device error word back to the host, every step.
+    b = wl.batch
+    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            for a in (b.coords, b.elem, b.mol_off, b.origin, b.spacing)]
+    h2d = sum(t.numel() * t.element_size() for t in host)
+    plan = api.Plan(grid, dtype, max_mol=B, max_atoms=b.n_atoms, path=path)
+    with torch.cuda.stream(stream):
+        for _ in range(max(3, args.warmup)):
+            plan.run(*host, out=out)
+    e2e_steps = max(3, min(args.steps, 200))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for _ in range(e2e_steps):
+            plan.run(*host, out=out)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    plan.close()
+
+    # Write-only reference: a plain device fill of at least 4 GB.
+    probe = None
+    if rank == 0:
+        buf = torch.empty(4 << 30, dtype=torch.uint8, device="cuda")
+        for _ in range(3):
+            buf.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(10):
+            buf.zero_()
+        e1.record()
+        torch.cuda.synchronize()
+        probe = buf.numel() * 10 / (e0.elapsed_time(e1) / 1e3) / 1e9
+        del buf
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    peak, peak_src = load_peaks()
+    kernel = "separable" if tuning.get("path") == 2 else "direct"
+    launch_ms = statistics.mean(per_step)
+    achieved = out_bytes / (launch_ms / 1e3) / 1e9
+    traffic = profiled_traffic(wl.name, kernel)
+    base = None
+    if world == 1 and not args.no_cpu_baseline:
+        base = cpu_baseline(wl)
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "grids/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32" if dtype == "f32" else dtype,
+        "data": "synthetic",
+        "config": {
+            "workload": wl.name,
+            "description": wl.description,
+            "batch_per_gpu": B,
+            "grid": [wl.n_channels, wl.nx, wl.ny, wl.nz],
+            "out_dtype": dtype,
+            "path": kernel,
+            "tuning": tuning,
+            "parallelism": f"dp{world}" if world > 1 else "single",
+            "l2": f"output {out_bytes / 1e9:.2f} GB per step > 129 MB L2; no flush",
+            "cuda_graph": True,
+        },
+        "voxels_per_sec": voxels,
+        "roofline": {
+            "bound": "hbm",
+            "achieved": achieved,
+            "peak": peak,
+            "unit": "GB/s",
+            "frac": achieved / peak,
+            "traffic": traffic,
+            "peak_source": f"{peak_src} hbm_gbs (copy)",
+            "algorithmic_bytes_per_launch": out_bytes,
+            "kernel": f"{kernel} voxelization kernel",
+            "write_probe_gbs": probe,
+            "frac_of_write_probe": (achieved / probe) if probe else None,
+        },
+        "e2e": {
+            "value": world * B / e2e_s,
+            "unit": "grids/s",
+            "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": 4,
+            "api": "pg_plan_run (pinned host CSR batch -> graph: H2D + kernel -> error word D2H)",
+        },
+        "gpu_launches": args.steps,
+        "clocks": sampler.summary(),
+        "cpu_baseline": base,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="qm9_shaped",
+                    choices=["qm9_shaped", "plain_small", "precision_form", "crystal_shaped",
+                             "differentiation"])
+    ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default=None)
+    ap.add_argument("--path", choices=["auto", "direct", "separable"], default="auto")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

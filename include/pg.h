@@ -1,0 +1,224 @@
+/*
+ * pg.h - C ABI of a GB300 (sm_103a) library for batched Gaussian-density voxelization,
+ * the grid-generation method of ParticleGrid (arXiv 2211.08506).
+ *
+ * What is computed (Sec. III-A, Eq. 1, point-sampled and unnormalised): for molecule b,
+ * channel c, voxel (i, j, k)
+ *
+ *     G[b][c][i][j][k] = sum over atoms a of b with elem[a] == c of
+ *                        chi(d) * exp(-|d|^2 / (2 sigma_c^2)),
+ *     d = v - x_a,   v = origin_b + ((i + 1/2) h_x, (j + 1/2) h_y, (k + 1/2) h_z),
+ *
+ * with h = spacing_b.  For periodic cells (Sec. III-A, nearest image) every component of
+ * d is replaced by d - L round(d / L), L = n h on that axis (orthorhombic cell, origin at
+ * its corner).  chi is the cutoff indicator with r_c = cutoff_k * sigma_c:
+ * PG_CUTOFF_SPHERE: |d|^2 <= r_c^2; PG_CUTOFF_BOX: max_axis |d_axis| <= r_c;
+ * PG_CUTOFF_NONE: always 1.  Sec. VI-B truncates where the Gaussian is negligible; here
+ * the truncation radius is explicit.
+ *
+ * General conventions
+ *  - All buffers belong to the caller.  The library keeps only a small per-device error
+ *    word, per-plan buffers (pg_plan_*) and an in-memory tuning cache; pg_shutdown()
+ *    frees them.
+ *  - Calls are asynchronous and stream-ordered on `stream` (a cudaStream_t passed as
+ *    void*; NULL is the legacy default stream) unless stated otherwise.  Device pointers
+ *    must belong to the device that is current on the calling thread.
+ *  - Errors found on the host (null pointers, negative counts, unsupported combinations)
+ *    return immediately with a status and a message in pg_last_error(); nothing is
+ *    launched.  Errors only visible in device data (an element id outside [0, C), CSR
+ *    offsets that are not monotone or exceed n_atoms, non-positive spacing, a periodic
+ *    cutoff radius of half a cell edge or more) never fault: the kernels skip the bad
+ *    atom or molecule (its grid is written as zeros) and set a device error word that
+ *    pg_sync_status() reports and clears.
+ *  - No exception crosses this ABI and no kernel traps.
+ */
+#ifndef PG_H_
+#define PG_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PG_ABI_VERSION 1
+#define PG_MAX_CHANNELS 64
+
+typedef enum {
+    PG_OK = 0,
+    PG_ERR_INVALID_ARG = 1,       /* rejected on the host, nothing launched */
+    PG_ERR_UNSUPPORTED = 2,       /* valid but not implemented (e.g. separable + sphere) */
+    PG_ERR_CUDA = 3,              /* a CUDA runtime call failed; message has the detail */
+    PG_ERR_DEVICE_VALIDATION = 4, /* the device error word was set (see pg_sync_status) */
+    PG_ERR_TIMEOUT = 5            /* reserved: a bounded device wait gave up */
+} pg_status;
+
+typedef enum { PG_F32 = 0, PG_F16 = 1, PG_BF16 = 2 } pg_dtype;
+
+typedef enum { PG_CUTOFF_SPHERE = 0, PG_CUTOFF_NONE = 1, PG_CUTOFF_BOX = 2 } pg_cutoff;
+
+typedef enum {
+    PG_PATH_AUTO = 0,      /* tuned choice for this problem's bucket, else DIRECT */
+    PG_PATH_DIRECT = 1,    /* per-voxel gather: any cutoff, any dtype */
+    PG_PATH_SEPARABLE = 2  /* tcgen05 BF16 contraction: NONE or BOX cutoff only */
+} pg_path;
+
+/* Device-error bits reported by pg_sync_status() / pg_plan_run(). */
+#define PG_DEVERR_ELEMENT 0x1u   /* elem[a] outside [0, n_channels) */
+#define PG_DEVERR_OFFSETS 0x2u   /* mol_off not monotone, negative, or > n_atoms */
+#define PG_DEVERR_SPACING 0x4u   /* spacing <= 0 or not finite */
+#define PG_DEVERR_PERIODIC 0x8u  /* periodic cell with r_c >= L/2 on some axis */
+
+/*
+ * A batch of B molecules in CSR form (Sec. V: points carry (channel, x, y, z); Sec. III-A:
+ * per-molecule box and resolution).  For pg_voxelize* all pointers are DEVICE pointers;
+ * for pg_plan_run they are HOST pointers.
+ *   coords   float  [n_atoms][3]  Cartesian positions, Angstrom
+ *   elem     int32  [n_atoms]     channel (element) id in [0, n_channels)
+ *   mol_off  int32  [n_mol + 1]   atoms of molecule b are mol_off[b] .. mol_off[b+1]-1;
+ *                                 mol_off[0] >= 0, non-decreasing, mol_off[n_mol] <= n_atoms
+ *   origin   float  [n_mol][3]    lower corner of molecule b's grid box
+ *   spacing  float  [n_mol][3]    voxel edges (h_x, h_y, h_z) of molecule b, > 0
+ */
+typedef struct {
+    int32_t n_mol;
+    int32_t n_atoms;
+    const float *coords;
+    const int32_t *elem;
+    const int32_t *mol_off;
+    const float *origin;
+    const float *spacing;
+} pg_batch;
+
+/*
+ * Grid description shared by the whole batch.
+ *   nx, ny, nz   grid shape (>= 1); the output of a batch is the dense, contiguous array
+ *                out[n_mol][n_channels][nx][ny][nz] (z fastest, Sec. III-A's
+ *                (Channel, H, W, D) per molecule)
+ *   n_channels   C, 1 .. PG_MAX_CHANNELS
+ *   sigma        HOST float[C]: Gaussian width per channel (standard deviation, Angstrom,
+ *                > 0; the paper's "variance" parameter, Sec. III-A / Sec. V)
+ *   cutoff_k     r_c = cutoff_k * sigma_c (> 0; ignored for PG_CUTOFF_NONE)
+ *   cutoff       pg_cutoff
+ *   periodic     0: open boundaries; 1: orthorhombic cell of edges n*h with nearest-image
+ *                distances (requires r_c < L/2 on every axis, checked on the device)
+ */
+typedef struct {
+    int32_t nx, ny, nz;
+    int32_t n_channels;
+    const float *sigma;
+    float cutoff_k;
+    int32_t cutoff;
+    int32_t periodic;
+} pg_grid;
+
+/*
+ * Launch choice for one problem bucket.  Zeros mean "library default".
+ *   path           pg_path (DIRECT or SEPARABLE; AUTO resolves through the tuning cache)
+ *   block_threads  threads per CTA of the direct kernel: 128, 256 or 512
+ *   blocks_per_sm  persistent CTAs per SM (0 = as many as fit)
+ *   store_hint     0: default global stores; 1: streaming (evict-first) stores
+ *   n_tile         separable path: output columns per tensor-core tile (64, 128 or 256)
+ */
+typedef struct {
+    int32_t path;
+    int32_t block_threads;
+    int32_t blocks_per_sm;
+    int32_t store_hint;
+    int32_t n_tile;
+    int32_t reserved[3];
+} pg_tuning;
+
+/* Library ABI version (PG_ABI_VERSION). */
+int32_t pg_version(void);
+
+/* Message of the last failed call on this thread ("" if none).  Valid until the next call
+   on the same thread. */
+const char *pg_last_error(void);
+
+/* Static name of a status code. */
+const char *pg_status_string(int32_t status);
+
+/*
+ * Forward voxelization (Sec. III-A, Eq. 1; Sec. VI-B truncation): writes every element of
+ * out[n_mol][C][nx][ny][nz] (zeros included; no pre-zeroing needed).
+ *   out_dtype  pg_dtype of `out` (accumulation is always FP32; FP16/BF16 are rounded to
+ *              nearest even on store)
+ *   out        DEVICE buffer; 16-byte alignment enables vector stores (any alignment of
+ *              the element type is accepted)
+ *   path       pg_path.  SEPARABLE with PG_CUTOFF_SPHERE returns PG_ERR_UNSUPPORTED.
+ * Returns PG_OK once the work is enqueued.
+ */
+pg_status pg_voxelize(const pg_batch *batch, const pg_grid *grid, int32_t out_dtype, void *out,
+                      int32_t path, void *stream);
+
+/* pg_voxelize with an explicit launch choice (used by the tuner and by tests that check
+   every candidate). */
+pg_status pg_voxelize_tuned(const pg_batch *batch, const pg_grid *grid, int32_t out_dtype,
+                            void *out, const pg_tuning *tuning, void *stream);
+
+/*
+ * Adjoint of pg_voxelize with respect to the atom coordinates (Sec. IV-C, generalised from
+ * the MSE loss to any upstream gradient): for L with dL/dG = grad_out,
+ *     grad_coords[a] = sum_v grad_out[b][elem[a]][v] * chi(d) * exp(-|d|^2/(2 sigma^2))
+ *                      * d / sigma^2,        d = v - x_a (nearest image if periodic).
+ *   grad_dtype   pg_dtype of grad_out (read and widened to FP32)
+ *   grad_out     DEVICE [n_mol][C][nx][ny][nz]
+ *   grad_coords  DEVICE float [n_atoms][3], overwritten (not accumulated); atoms outside
+ *                every molecule's CSR range get 0
+ * Deterministic: one warp per atom, fixed-order reduction, no atomics.
+ */
+pg_status pg_voxelize_backward(const pg_batch *batch, const pg_grid *grid, int32_t grad_dtype,
+                               const void *grad_out, float *grad_coords, void *stream);
+
+/* Synchronize `stream`, then read and clear the device error word.  Returns
+   PG_ERR_DEVICE_VALIDATION (bits in *bits_out if non-NULL) if it was set. */
+pg_status pg_sync_status(void *stream, uint32_t *bits_out);
+
+/*
+ * Time every launch candidate for this problem's bucket (grid shape, dtype, cutoff,
+ * periodicity, atoms-per-molecule bucket), check each against the first candidate's
+ * output (bitwise for the direct kernel's launch shapes, 1e-2 of the grid maximum for
+ * the separable path), and record the fastest passing one for PG_PATH_AUTO.
+ * `out` is used as scratch and holds an arbitrary candidate's result afterwards.
+ * `path` restricts the search (AUTO = all eligible paths).  Synchronizes `stream`.
+ * The chosen tuning is written to *chosen if non-NULL.
+ */
+pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dtype, void *out,
+                      int32_t path, void *stream, pg_tuning *chosen);
+
+/* The tuning PG_PATH_AUTO (or the given path) would use for this problem. */
+pg_status pg_get_tuning(const pg_batch *batch, const pg_grid *grid, int32_t out_dtype,
+                        int32_t path, pg_tuning *tuning);
+
+/* Tuning cache as text lines "key value..."; load merges into the in-memory cache. */
+pg_status pg_tuning_save(const char *file);
+pg_status pg_tuning_load(const char *file);
+
+/*
+ * Plans: fixed-capacity input buffers plus a CUDA graph holding the host-to-device copy
+ * of a batch and the voxelization launch, for on-the-fly grid generation from host data
+ * (the data-loader use of Sec. V / Sec. VI-D).
+ *   pg_plan_create  capacity max_mol molecules / max_atoms atoms; grid and dtype fixed.
+ *   pg_plan_run     batch holds HOST pointers (pinned memory is copied directly;
+ *                   pageable memory is first packed into the plan's pinned staging);
+ *                   replays the graph on `stream`, writes `out` (DEVICE), then copies the
+ *                   4-byte device error word back and synchronizes the stream.  Returns
+ *                   PG_ERR_DEVICE_VALIDATION if it was set.  Not thread-safe per plan.
+ *   pg_plan_destroy frees the plan (synchronize users of it first).
+ */
+typedef struct pg_plan pg_plan;
+pg_status pg_plan_create(pg_plan **plan, const pg_grid *grid, int32_t out_dtype, int32_t path,
+                         int32_t max_mol, int32_t max_atoms);
+pg_status pg_plan_run(pg_plan *plan, const pg_batch *host_batch, void *out, void *stream);
+pg_status pg_plan_destroy(pg_plan *plan);
+
+/* Free per-device state and the tuning cache.  Later calls re-create what they need. */
+void pg_shutdown(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PG_H_ */

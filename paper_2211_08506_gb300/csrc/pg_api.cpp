@@ -1,0 +1,841 @@
+// Host runtime behind the C ABI in pg.h: argument validation, per-call constants, kernel
+// dispatch, the device error word, the launch autotuner with its cache, and plans
+// (CUDA graphs holding the host-to-device copy of a batch plus the launch).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "pg.h"
+#include "pg_internal.h"
+
+using namespace pgi;
+
+namespace {
+
+thread_local std::string t_last_error;
+
+pg_status fail(pg_status s, const char *fmt, ...)
+{
+    char buf[768];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return s;
+}
+
+pg_status cuda_fail(cudaError_t e, const char *what)
+{
+    (void)cudaGetLastError();  // clear the non-sticky error state
+    return fail(PG_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+#define PG_CUDA(call, what)                          \
+    do {                                             \
+        cudaError_t e_ = (call);                     \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// ---------------------------------------------------------------- per-device state
+
+struct Device {
+    int id = -1;
+    int sms = 0;
+    unsigned *err = nullptr;  // device error word (PG_DEVERR_* bits)
+    std::string name;
+};
+
+std::mutex g_mu;
+std::map<int, Device> g_devices;
+
+pg_status get_device(Device **out)
+{
+    int id = 0;
+    PG_CUDA(cudaGetDevice(&id), "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_devices.find(id);
+    if (it == g_devices.end()) {
+        Device d;
+        d.id = id;
+        PG_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, id),
+                "cudaDeviceGetAttribute");
+        cudaDeviceProp prop;
+        PG_CUDA(cudaGetDeviceProperties(&prop, id), "cudaGetDeviceProperties");
+        d.name = prop.name;
+        for (char &ch : d.name)
+            if (ch == ' ') ch = '_';
+        PG_CUDA(cudaMalloc(&d.err, sizeof(unsigned)), "cudaMalloc(error word)");
+        PG_CUDA(cudaMemset(d.err, 0, sizeof(unsigned)), "cudaMemset(error word)");
+        PG_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize(setup)");
+        it = g_devices.emplace(id, d).first;
+    }
+    *out = &it->second;
+    return PG_OK;
+}
+
+// ---------------------------------------------------------------- validation
+
+size_t dtype_size(int dtype) { return dtype == PG_F32 ? 4 : 2; }
+
+pg_status validate(const pg_batch *b, const pg_grid *g)
+{
+    if (!b || !g) return fail(PG_ERR_INVALID_ARG, "batch and grid must not be NULL");
+    if (b->n_mol < 0 || b->n_atoms < 0)
+        return fail(PG_ERR_INVALID_ARG, "negative n_mol (%d) or n_atoms (%d)", b->n_mol,
+                    b->n_atoms);
+    if (b->n_mol > 0 && (!b->mol_off || !b->origin || !b->spacing))
+        return fail(PG_ERR_INVALID_ARG, "mol_off, origin and spacing are required when n_mol > 0");
+    if (b->n_atoms > 0 && (!b->coords || !b->elem))
+        return fail(PG_ERR_INVALID_ARG, "coords and elem are required when n_atoms > 0");
+    if (g->nx < 1 || g->ny < 1 || g->nz < 1)
+        return fail(PG_ERR_INVALID_ARG, "grid shape %dx%dx%d must be positive", g->nx, g->ny,
+                    g->nz);
+    if (g->n_channels < 1 || g->n_channels > kMaxC)
+        return fail(PG_ERR_INVALID_ARG, "n_channels %d outside 1..%d", g->n_channels, kMaxC);
+    if (!g->sigma) return fail(PG_ERR_INVALID_ARG, "sigma must not be NULL");
+    for (int c = 0; c < g->n_channels; ++c)
+        if (!(g->sigma[c] > 0.0f) || !std::isfinite(g->sigma[c]))
+            return fail(PG_ERR_INVALID_ARG, "sigma[%d] = %g must be positive and finite", c,
+                        (double)g->sigma[c]);
+    if (g->cutoff != PG_CUTOFF_SPHERE && g->cutoff != PG_CUTOFF_NONE && g->cutoff != PG_CUTOFF_BOX)
+        return fail(PG_ERR_INVALID_ARG, "unknown cutoff mode %d", g->cutoff);
+    if (g->cutoff != PG_CUTOFF_NONE && (!(g->cutoff_k > 0.0f) || !std::isfinite(g->cutoff_k)))
+        return fail(PG_ERR_INVALID_ARG, "cutoff_k = %g must be positive and finite",
+                    (double)g->cutoff_k);
+    if (g->periodic != 0 && g->periodic != 1)
+        return fail(PG_ERR_INVALID_ARG, "periodic must be 0 or 1");
+    const long long plane = (long long)g->ny * g->nz;
+    if (plane > INT32_MAX || (long long)g->nx * plane > INT32_MAX)
+        return fail(PG_ERR_INVALID_ARG, "one channel grid must hold fewer than 2^31 voxels");
+    const long long per_mol = (long long)g->n_channels * g->nx * plane;
+    if (b->n_mol > 0 && per_mol > (1ll << 60) / b->n_mol)
+        return fail(PG_ERR_INVALID_ARG, "output too large");
+    return PG_OK;
+}
+
+pg_status check_dtype(int dtype)
+{
+    if (dtype != PG_F32 && dtype != PG_F16 && dtype != PG_BF16)
+        return fail(PG_ERR_INVALID_ARG, "unknown dtype %d", dtype);
+    return PG_OK;
+}
+
+void make_geometry(const pg_batch *b, const pg_grid *g, Geometry *G)
+{
+    std::memset(G, 0, sizeof *G);
+    G->n_mol = b->n_mol;
+    G->n_atoms = b->n_atoms;
+    G->nx = g->nx;
+    G->ny = g->ny;
+    G->nz = g->nz;
+    G->C = g->n_channels;
+    G->cutoff = g->cutoff;
+    G->periodic = g->periodic;
+    const double log2e = 1.4426950408889634;
+    for (int c = 0; c < g->n_channels; ++c) {
+        const double s = g->sigma[c];
+        const double r = (double)g->cutoff_k * s;
+        G->q[c] = (float)(log2e / (2.0 * s * s));
+        G->inv_s2[c] = (float)(1.0 / (s * s));
+        if (g->cutoff == PG_CUTOFF_NONE) {
+            G->r2[c] = INFINITY;
+            G->rcull[c] = INFINITY;
+        } else {
+            G->r2[c] = (float)(r * r);
+            G->rcull[c] = (float)(r * (1.0 + 1e-5) + 1e-6);
+        }
+    }
+}
+
+Inputs make_inputs(const pg_batch *b)
+{
+    return Inputs{b->coords, b->elem, b->mol_off, b->origin, b->spacing};
+}
+
+pg_tuning default_tuning(int path)
+{
+    pg_tuning t;
+    std::memset(&t, 0, sizeof t);
+    t.path = path == PG_PATH_SEPARABLE ? PG_PATH_SEPARABLE : PG_PATH_DIRECT;
+    t.block_threads = 256;
+    t.blocks_per_sm = 0;
+    t.store_hint = 0;
+    t.n_tile = 128;
+    return t;
+}
+
+bool vec_stores_ok(const void *out, const pg_grid *g, int dtype)
+{
+    return ((uintptr_t)out % 16 == 0) && (((size_t)g->nz * dtype_size(dtype)) % 16 == 0);
+}
+
+// Resolve one forward launch without issuing it.
+pg_status plan_forward(const pg_batch *b, const pg_grid *g, int dtype, void *out,
+                       const pg_tuning &t, const Device &d, unsigned *err, KernelLaunch *kl)
+{
+    Geometry G;
+    make_geometry(b, g, &G);
+    if (t.path == PG_PATH_SEPARABLE) {
+        if (g->cutoff == PG_CUTOFF_SPHERE)
+            return fail(PG_ERR_UNSUPPORTED,
+                        "the separable path needs a separable cutoff (NONE or BOX); the "
+                        "spherical cutoff does not factor per axis");
+        if (!separable_supported(G, dtype))
+            return fail(PG_ERR_UNSUPPORTED, "separable path does not cover this grid/dtype");
+        SeparableArgs a;
+        std::memset(&a, 0, sizeof a);
+        a.in = make_inputs(b);
+        a.out = out;
+        a.err = err;
+        a.geo = G;
+        a.n_tile = t.n_tile;
+        cudaError_t e = separable_plan(a, dtype, t, d.sms, kl);
+        if (e == cudaErrorNotSupported)
+            return fail(PG_ERR_UNSUPPORTED, "separable path does not cover this grid/dtype");
+        if (e != cudaSuccess) return cuda_fail(e, "separable_plan");
+        return PG_OK;
+    }
+    DirectArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.in = make_inputs(b);
+    a.out = out;
+    a.err = err;
+    a.geo = G;
+    cudaError_t e = direct_plan(a, dtype, vec_stores_ok(out, g, dtype) ? 1 : 0, t, d.sms, kl);
+    if (e != cudaSuccess) return cuda_fail(e, "direct_plan");
+    return PG_OK;
+}
+
+pg_status forward(const pg_batch *b, const pg_grid *g, int dtype, void *out, const pg_tuning &t,
+                  cudaStream_t s)
+{
+    pg_status st = validate(b, g);
+    if (st) return st;
+    if ((st = check_dtype(dtype))) return st;
+    if (t.path != PG_PATH_DIRECT && t.path != PG_PATH_SEPARABLE)
+        return fail(PG_ERR_INVALID_ARG, "tuning.path must be DIRECT or SEPARABLE");
+    if (b->n_mol > 0 && !out) return fail(PG_ERR_INVALID_ARG, "out must not be NULL");
+    if ((uintptr_t)out % dtype_size(dtype) != 0)
+        return fail(PG_ERR_INVALID_ARG, "out is not aligned to its element size");
+    Device *d = nullptr;
+    if ((st = get_device(&d))) return st;
+    if (b->n_mol == 0) return PG_OK;
+    KernelLaunch kl;
+    if ((st = plan_forward(b, g, dtype, out, t, *d, d->err, &kl))) return st;
+    PG_CUDA(launch(kl, s), "voxelize launch");
+    return PG_OK;
+}
+
+// ---------------------------------------------------------------- tuning cache
+
+std::mutex g_tune_mu;
+std::map<std::string, pg_tuning> g_tune;
+
+std::string bucket_key(const pg_batch *b, const pg_grid *g, int dtype, int path,
+                       const Device &d)
+{
+    const double apm = b->n_mol > 0 ? (double)b->n_atoms / b->n_mol : 0.0;
+    const int bucket = apm >= 1.0 ? (int)std::floor(std::log2(apm)) : 0;
+    char buf[256];
+    snprintf(buf, sizeof buf, "%s|%dx%dx%d|C%d|dt%d|cut%d|per%d|apm%d|path%d", d.name.c_str(),
+             g->nx, g->ny, g->nz, g->n_channels, dtype, g->cutoff, g->periodic, bucket, path);
+    return buf;
+}
+
+pg_tuning resolve(const pg_batch *b, const pg_grid *g, int dtype, int path, const Device &d)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(bucket_key(b, g, dtype, path, d));
+    if (it != g_tune.end()) return it->second;
+    return default_tuning(path);
+}
+
+// ---------------------------------------------------------------- plans
+
+bool is_pinned(const void *p)
+{
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return attr.type == cudaMemoryTypeHost;
+}
+
+}  // namespace
+
+struct pg_plan {
+    int device = -1;
+    pg_grid grid;
+    std::vector<float> sigma;
+    int dtype = 0;
+    pg_tuning tuning;
+    int max_mol = 0, max_atoms = 0;
+    float *d_coords = nullptr;
+    int *d_elem = nullptr;
+    int *d_moloff = nullptr;
+    float *d_origin = nullptr;
+    float *d_spacing = nullptr;
+    unsigned *d_err = nullptr;
+    unsigned char *h_stage = nullptr;
+    size_t stage_off[5] = {0, 0, 0, 0, 0};
+    unsigned *h_err = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t n_memset = nullptr, n_copy[5] = {}, n_kernel = nullptr, n_errcopy = nullptr;
+    const void *kernel_func = nullptr;
+};
+
+namespace {
+
+void plan_free(pg_plan *p)
+{
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    cudaFree(p->d_coords);
+    cudaFree(p->d_elem);
+    cudaFree(p->d_moloff);
+    cudaFree(p->d_origin);
+    cudaFree(p->d_spacing);
+    cudaFree(p->d_err);
+    if (p->h_stage) cudaFreeHost(p->h_stage);
+    if (p->h_err) cudaFreeHost(p->h_err);
+    delete p;
+}
+
+pg_status plan_build_graph(pg_plan *p, const void *const src[5], const size_t bytes[5],
+                           void *const dst[5], KernelLaunch &kl)
+{
+    if (p->exec) {
+        cudaGraphExecDestroy(p->exec);
+        p->exec = nullptr;
+    }
+    if (p->graph) {
+        cudaGraphDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    PG_CUDA(cudaGraphCreate(&p->graph, 0), "cudaGraphCreate");
+    cudaMemsetParams ms;
+    std::memset(&ms, 0, sizeof ms);
+    ms.dst = p->d_err;
+    ms.value = 0;
+    ms.elementSize = sizeof(unsigned);
+    ms.width = 1;
+    ms.height = 1;
+    ms.pitch = sizeof(unsigned);
+    PG_CUDA(cudaGraphAddMemsetNode(&p->n_memset, p->graph, nullptr, 0, &ms), "add memset node");
+    cudaGraphNode_t deps[6];
+    deps[0] = p->n_memset;
+    for (int i = 0; i < 5; ++i) {
+        PG_CUDA(cudaGraphAddMemcpyNode1D(&p->n_copy[i], p->graph, nullptr, 0, dst[i], src[i],
+                                         bytes[i], cudaMemcpyHostToDevice),
+                "add H2D node");
+        deps[i + 1] = p->n_copy[i];
+    }
+    kl.params[0] = kl.args;
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof kp);
+    kp.func = const_cast<void *>(kl.func);
+    kp.gridDim = kl.grid;
+    kp.blockDim = kl.block;
+    kp.sharedMemBytes = (unsigned)kl.smem;
+    kp.kernelParams = kl.params;
+    PG_CUDA(cudaGraphAddKernelNode(&p->n_kernel, p->graph, deps, 6, &kp), "add kernel node");
+    PG_CUDA(cudaGraphAddMemcpyNode1D(&p->n_errcopy, p->graph, &p->n_kernel, 1, p->h_err,
+                                     p->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost),
+            "add D2H node");
+    PG_CUDA(cudaGraphInstantiate(&p->exec, p->graph, 0), "cudaGraphInstantiate");
+    p->kernel_func = kl.func;
+    return PG_OK;
+}
+
+pg_status plan_update_graph(pg_plan *p, const void *const src[5], const size_t bytes[5],
+                            void *const dst[5], KernelLaunch &kl)
+{
+    if (!p->exec || kl.func != p->kernel_func) return plan_build_graph(p, src, bytes, dst, kl);
+    for (int i = 0; i < 5; ++i) {
+        if (cudaGraphExecMemcpyNodeSetParams1D(p->exec, p->n_copy[i], dst[i], src[i], bytes[i],
+                                               cudaMemcpyHostToDevice) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return plan_build_graph(p, src, bytes, dst, kl);
+        }
+    }
+    kl.params[0] = kl.args;
+    cudaKernelNodeParams kp;
+    std::memset(&kp, 0, sizeof kp);
+    kp.func = const_cast<void *>(kl.func);
+    kp.gridDim = kl.grid;
+    kp.blockDim = kl.block;
+    kp.sharedMemBytes = (unsigned)kl.smem;
+    kp.kernelParams = kl.params;
+    if (cudaGraphExecKernelNodeSetParams(p->exec, p->n_kernel, &kp) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return plan_build_graph(p, src, bytes, dst, kl);
+    }
+    return PG_OK;
+}
+
+pg_status report_bits(unsigned bits)
+{
+    if (!bits) return PG_OK;
+    return fail(PG_ERR_DEVICE_VALIDATION,
+                "device validation failed (bits 0x%x:%s%s%s%s)", bits,
+                (bits & PG_DEVERR_ELEMENT) ? " element id outside [0, C)" : "",
+                (bits & PG_DEVERR_OFFSETS) ? " bad CSR offsets" : "",
+                (bits & PG_DEVERR_SPACING) ? " non-positive spacing" : "",
+                (bits & PG_DEVERR_PERIODIC) ? " periodic cutoff >= half a cell edge" : "");
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t pg_version(void) { return PG_ABI_VERSION; }
+
+const char *pg_last_error(void) { return t_last_error.c_str(); }
+
+const char *pg_status_string(int32_t s)
+{
+    switch (s) {
+    case PG_OK: return "PG_OK";
+    case PG_ERR_INVALID_ARG: return "PG_ERR_INVALID_ARG";
+    case PG_ERR_UNSUPPORTED: return "PG_ERR_UNSUPPORTED";
+    case PG_ERR_CUDA: return "PG_ERR_CUDA";
+    case PG_ERR_DEVICE_VALIDATION: return "PG_ERR_DEVICE_VALIDATION";
+    case PG_ERR_TIMEOUT: return "PG_ERR_TIMEOUT";
+    default: return "PG_ERR_UNKNOWN";
+    }
+}
+
+pg_status pg_voxelize_tuned(const pg_batch *batch, const pg_grid *grid, int32_t out_dtype,
+                            void *out, const pg_tuning *tuning, void *stream)
+{
+    if (!tuning) return fail(PG_ERR_INVALID_ARG, "tuning must not be NULL");
+    t_last_error.clear();
+    return forward(batch, grid, out_dtype, out, *tuning, (cudaStream_t)stream);
+}
+
+pg_status pg_voxelize(const pg_batch *batch, const pg_grid *grid, int32_t out_dtype, void *out,
+                      int32_t path, void *stream)
+{
+    t_last_error.clear();
+    if (path != PG_PATH_AUTO && path != PG_PATH_DIRECT && path != PG_PATH_SEPARABLE)
+        return fail(PG_ERR_INVALID_ARG, "unknown path %d", path);
+    pg_status st = validate(batch, grid);
+    if (st) return st;
+    Device *d = nullptr;
+    if ((st = get_device(&d))) return st;
+    pg_tuning t = resolve(batch, grid, out_dtype, path, *d);
+    if (path == PG_PATH_AUTO && t.path == PG_PATH_SEPARABLE && grid->cutoff == PG_CUTOFF_SPHERE)
+        t = default_tuning(PG_PATH_DIRECT);
+    return forward(batch, grid, out_dtype, out, t, (cudaStream_t)stream);
+}
+
+pg_status pg_voxelize_backward(const pg_batch *batch, const pg_grid *grid, int32_t grad_dtype,
+                               const void *grad_out, float *grad_coords, void *stream)
+{
+    t_last_error.clear();
+    pg_status st = validate(batch, grid);
+    if (st) return st;
+    if ((st = check_dtype(grad_dtype))) return st;
+    if (batch->n_mol > 0 && !grad_out)
+        return fail(PG_ERR_INVALID_ARG, "grad_out must not be NULL");
+    if (batch->n_atoms > 0 && !grad_coords)
+        return fail(PG_ERR_INVALID_ARG, "grad_coords must not be NULL");
+    if ((uintptr_t)grad_out % dtype_size(grad_dtype) != 0 || (uintptr_t)grad_coords % 4 != 0)
+        return fail(PG_ERR_INVALID_ARG, "grad_out / grad_coords misaligned");
+    Device *d = nullptr;
+    if ((st = get_device(&d))) return st;
+    if (batch->n_atoms == 0) return PG_OK;
+    BackwardArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.in = make_inputs(batch);
+    a.grad_out = grad_out;
+    a.grad_coords = grad_coords;
+    a.err = d->err;
+    make_geometry(batch, grid, &a.geo);
+    KernelLaunch kl;
+    PG_CUDA(backward_plan(a, grad_dtype, d->sms, &kl), "backward_plan");
+    PG_CUDA(launch(kl, (cudaStream_t)stream), "backward launch");
+    return PG_OK;
+}
+
+pg_status pg_sync_status(void *stream, uint32_t *bits_out)
+{
+    t_last_error.clear();
+    Device *d = nullptr;
+    pg_status st = get_device(&d);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    PG_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    unsigned bits = 0;
+    PG_CUDA(cudaMemcpyAsync(&bits, d->err, sizeof bits, cudaMemcpyDeviceToHost, s),
+            "read error word");
+    PG_CUDA(cudaMemsetAsync(d->err, 0, sizeof(unsigned), s), "clear error word");
+    PG_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (bits_out) *bits_out = bits;
+    return report_bits(bits);
+}
+
+pg_status pg_get_tuning(const pg_batch *batch, const pg_grid *grid, int32_t out_dtype,
+                        int32_t path, pg_tuning *tuning)
+{
+    t_last_error.clear();
+    pg_status st = validate(batch, grid);
+    if (st) return st;
+    if (!tuning) return fail(PG_ERR_INVALID_ARG, "tuning must not be NULL");
+    Device *d = nullptr;
+    if ((st = get_device(&d))) return st;
+    *tuning = resolve(batch, grid, out_dtype, path, *d);
+    return PG_OK;
+}
+
+pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dtype, void *out,
+                      int32_t path, void *stream, pg_tuning *chosen)
+{
+    t_last_error.clear();
+    pg_status st = validate(batch, grid);
+    if (st) return st;
+    if ((st = check_dtype(out_dtype))) return st;
+    if (path != PG_PATH_AUTO && path != PG_PATH_DIRECT && path != PG_PATH_SEPARABLE)
+        return fail(PG_ERR_INVALID_ARG, "unknown path %d", path);
+    if (batch->n_mol > 0 && !out) return fail(PG_ERR_INVALID_ARG, "out must not be NULL");
+    Device *d = nullptr;
+    if ((st = get_device(&d))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (batch->n_mol == 0) {
+        if (chosen) *chosen = default_tuning(path);
+        return PG_OK;
+    }
+
+    std::vector<pg_tuning> cands;
+    if (path != PG_PATH_SEPARABLE) {
+        for (int threads : {256, 128, 512})
+            for (int bps : {0, 1, 2})
+                for (int hint : {0, 1}) {
+                    pg_tuning t = default_tuning(PG_PATH_DIRECT);
+                    t.block_threads = threads;
+                    t.blocks_per_sm = bps;
+                    t.store_hint = hint;
+                    cands.push_back(t);
+                }
+    }
+    Geometry G;
+    make_geometry(batch, grid, &G);
+    const bool sep_ok = grid->cutoff != PG_CUTOFF_SPHERE && separable_supported(G, out_dtype);
+    if (path != PG_PATH_DIRECT && sep_ok) {
+        for (int nt : {128, 256, 64})
+            for (int hint : {0, 1}) {
+                pg_tuning t = default_tuning(PG_PATH_SEPARABLE);
+                t.n_tile = nt;
+                t.store_hint = hint;
+                cands.push_back(t);
+            }
+    }
+    if (cands.empty())
+        return fail(PG_ERR_UNSUPPORTED, "no eligible candidate for path %d (separable needs a "
+                                        "NONE or BOX cutoff)", path);
+
+    // Reference: the first candidate's output, as a full-bit hash plus a copy of the first
+    // few molecules for tolerance checks of candidates that round differently.
+    const size_t per_mol = (size_t)grid->n_channels * grid->nx * grid->ny * grid->nz;
+    const int n_sample = std::min(batch->n_mol, 8);
+    const size_t sample_elems = per_mol * n_sample;
+    const size_t esz = dtype_size(out_dtype);
+    void *sample = nullptr;
+    unsigned long long *d_hash = nullptr;
+    float *d_cmp = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    std::vector<float> times(cands.size(), INFINITY);
+    auto cleanup = [&]() {
+        cudaFree(sample);
+        cudaFree(d_hash);
+        cudaFree(d_cmp);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    };
+    auto cu = [&](cudaError_t e, const char *what) -> pg_status {
+        if (e == cudaSuccess) return PG_OK;
+        cleanup();
+        return cuda_fail(e, what);
+    };
+    if ((st = cu(cudaMalloc(&sample, sample_elems * esz), "cudaMalloc(tune sample)"))) return st;
+    if ((st = cu(cudaMalloc(&d_hash, sizeof(unsigned long long)), "cudaMalloc"))) return st;
+    if ((st = cu(cudaMalloc(&d_cmp, 2 * sizeof(float)), "cudaMalloc"))) return st;
+    if ((st = cu(cudaEventCreate(&e0), "cudaEventCreate"))) return st;
+    if ((st = cu(cudaEventCreate(&e1), "cudaEventCreate"))) return st;
+    const size_t out_bytes = per_mol * (size_t)batch->n_mol * esz;
+
+    unsigned long long ref_hash = 0;
+    int ref_index = -1;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        KernelLaunch kl;
+        if (plan_forward(batch, grid, out_dtype, out, cands[i], *d, d->err, &kl) != PG_OK) {
+            t_last_error.clear();
+            continue;
+        }
+        if ((st = cu(launch(kl, s), "tune launch"))) return st;
+        // Parity against the reference candidate.
+        bool pass = true;
+        if (ref_index < 0) {
+            if ((st = cu(buffer_hash(out, out_bytes, d_hash, s), "hash"))) return st;
+            if ((st = cu(cudaMemcpyAsync(&ref_hash, d_hash, sizeof ref_hash,
+                                         cudaMemcpyDeviceToHost, s), "copy hash")))
+                return st;
+            if ((st = cu(cudaMemcpyAsync(sample, out, sample_elems * esz,
+                                         cudaMemcpyDeviceToDevice, s), "copy sample")))
+                return st;
+            if ((st = cu(cudaStreamSynchronize(s), "sync"))) return st;
+            ref_index = (int)i;
+        } else if (cands[i].path == cands[ref_index].path && cands[i].path == PG_PATH_DIRECT) {
+            unsigned long long h = 0;
+            if ((st = cu(buffer_hash(out, out_bytes, d_hash, s), "hash"))) return st;
+            if ((st = cu(cudaMemcpyAsync(&h, d_hash, sizeof h, cudaMemcpyDeviceToHost, s),
+                         "copy hash")))
+                return st;
+            if ((st = cu(cudaStreamSynchronize(s), "sync"))) return st;
+            pass = (h == ref_hash);
+        } else {
+            float cmp[2] = {0, 0};
+            if ((st = cu(buffer_compare(out, sample, sample_elems, out_dtype, d_cmp, s),
+                         "compare")))
+                return st;
+            if ((st = cu(cudaMemcpyAsync(cmp, d_cmp, sizeof cmp, cudaMemcpyDeviceToHost, s),
+                         "copy compare")))
+                return st;
+            if ((st = cu(cudaStreamSynchronize(s), "sync"))) return st;
+            pass = cmp[0] <= 1e-2f * cmp[1];
+        }
+        if (!pass) continue;
+        // Time: median of 5 launches.
+        std::vector<float> ms;
+        for (int r = 0; r < 5; ++r) {
+            if ((st = cu(cudaEventRecord(e0, s), "event"))) return st;
+            if ((st = cu(launch(kl, s), "tune launch"))) return st;
+            if ((st = cu(cudaEventRecord(e1, s), "event"))) return st;
+            if ((st = cu(cudaEventSynchronize(e1), "event sync"))) return st;
+            float t = 0;
+            if ((st = cu(cudaEventElapsedTime(&t, e0, e1), "elapsed"))) return st;
+            ms.push_back(t);
+        }
+        std::sort(ms.begin(), ms.end());
+        times[i] = ms[ms.size() / 2];
+    }
+    cleanup();
+
+    int best = -1, best_direct = -1, best_sep = -1;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        if (!std::isfinite(times[i])) continue;
+        if (best < 0 || times[i] < times[best]) best = (int)i;
+        if (cands[i].path == PG_PATH_DIRECT && (best_direct < 0 || times[i] < times[best_direct]))
+            best_direct = (int)i;
+        if (cands[i].path == PG_PATH_SEPARABLE && (best_sep < 0 || times[i] < times[best_sep]))
+            best_sep = (int)i;
+    }
+    if (best < 0) return fail(PG_ERR_CUDA, "no autotune candidate ran and passed parity");
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[bucket_key(batch, grid, out_dtype, path, *d)] = cands[best];
+        if (best_direct >= 0)
+            g_tune[bucket_key(batch, grid, out_dtype, PG_PATH_DIRECT, *d)] = cands[best_direct];
+        if (best_sep >= 0)
+            g_tune[bucket_key(batch, grid, out_dtype, PG_PATH_SEPARABLE, *d)] = cands[best_sep];
+    }
+    if (chosen) *chosen = cands[best];
+    return PG_OK;
+}
+
+pg_status pg_tuning_save(const char *file)
+{
+    t_last_error.clear();
+    if (!file) return fail(PG_ERR_INVALID_ARG, "file must not be NULL");
+    std::ofstream f(file);
+    if (!f) return fail(PG_ERR_INVALID_ARG, "cannot write %s", file);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &kv : g_tune)
+        f << kv.first << ' ' << kv.second.path << ' ' << kv.second.block_threads << ' '
+          << kv.second.blocks_per_sm << ' ' << kv.second.store_hint << ' ' << kv.second.n_tile
+          << '\n';
+    return PG_OK;
+}
+
+pg_status pg_tuning_load(const char *file)
+{
+    t_last_error.clear();
+    if (!file) return fail(PG_ERR_INVALID_ARG, "file must not be NULL");
+    std::ifstream f(file);
+    if (!f) return fail(PG_ERR_INVALID_ARG, "cannot read %s", file);
+    std::string line;
+    std::map<std::string, pg_tuning> add;
+    while (std::getline(f, line)) {
+        if (line.empty()) continue;
+        std::istringstream is(line);
+        std::string key;
+        pg_tuning t;
+        std::memset(&t, 0, sizeof t);
+        if (!(is >> key >> t.path >> t.block_threads >> t.blocks_per_sm >> t.store_hint >>
+              t.n_tile))
+            return fail(PG_ERR_INVALID_ARG, "malformed tuning line: %s", line.c_str());
+        add[key] = t;
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    for (auto &kv : add) g_tune[kv.first] = kv.second;
+    return PG_OK;
+}
+
+pg_status pg_plan_create(pg_plan **plan, const pg_grid *grid, int32_t out_dtype, int32_t path,
+                         int32_t max_mol, int32_t max_atoms)
+{
+    t_last_error.clear();
+    if (!plan) return fail(PG_ERR_INVALID_ARG, "plan must not be NULL");
+    *plan = nullptr;
+    pg_batch probe;
+    std::memset(&probe, 0, sizeof probe);
+    pg_status st = validate(&probe, grid);
+    if (st) return st;
+    if ((st = check_dtype(out_dtype))) return st;
+    if (max_mol < 1 || max_atoms < 0) return fail(PG_ERR_INVALID_ARG, "bad plan capacity");
+    if (path != PG_PATH_AUTO && path != PG_PATH_DIRECT && path != PG_PATH_SEPARABLE)
+        return fail(PG_ERR_INVALID_ARG, "unknown path %d", path);
+    Device *d = nullptr;
+    if ((st = get_device(&d))) return st;
+    pg_plan *p = new pg_plan();
+    p->device = d->id;
+    p->grid = *grid;
+    p->sigma.assign(grid->sigma, grid->sigma + grid->n_channels);
+    p->grid.sigma = p->sigma.data();
+    p->dtype = out_dtype;
+    p->max_mol = max_mol;
+    p->max_atoms = max_atoms;
+    // The launch choice is fixed at creation: the tuned entry for a batch of this
+    // capacity's shape if one exists, else the default for the path.
+    pg_batch shape = probe;
+    shape.n_mol = max_mol;
+    shape.n_atoms = max_atoms;
+    p->tuning = resolve(&shape, grid, out_dtype, path, *d);
+    if (p->tuning.path == PG_PATH_SEPARABLE && grid->cutoff == PG_CUTOFF_SPHERE)
+        p->tuning = default_tuning(PG_PATH_DIRECT);
+    const size_t A = (size_t)std::max(max_atoms, 1), M = (size_t)max_mol;
+    const size_t sizes[5] = {A * 3 * 4, A * 4, (M + 1) * 4, M * 3 * 4, M * 3 * 4};
+    size_t total = 0;
+    for (int i = 0; i < 5; ++i) {
+        p->stage_off[i] = total;
+        total += (sizes[i] + 255) / 256 * 256;
+    }
+    auto bad = [&](cudaError_t e, const char *what) {
+        plan_free(p);
+        return cuda_fail(e, what);
+    };
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->d_coords, sizes[0])) != cudaSuccess) return bad(e, "cudaMalloc");
+    if ((e = cudaMalloc(&p->d_elem, sizes[1])) != cudaSuccess) return bad(e, "cudaMalloc");
+    if ((e = cudaMalloc(&p->d_moloff, sizes[2])) != cudaSuccess) return bad(e, "cudaMalloc");
+    if ((e = cudaMalloc(&p->d_origin, sizes[3])) != cudaSuccess) return bad(e, "cudaMalloc");
+    if ((e = cudaMalloc(&p->d_spacing, sizes[4])) != cudaSuccess) return bad(e, "cudaMalloc");
+    if ((e = cudaMalloc(&p->d_err, sizeof(unsigned))) != cudaSuccess) return bad(e, "cudaMalloc");
+    if ((e = cudaHostAlloc((void **)&p->h_stage, total, cudaHostAllocDefault)) != cudaSuccess)
+        return bad(e, "cudaHostAlloc");
+    if ((e = cudaHostAlloc((void **)&p->h_err, sizeof(unsigned), cudaHostAllocDefault)) !=
+        cudaSuccess)
+        return bad(e, "cudaHostAlloc");
+    std::memset(p->h_stage, 0, total);
+    *p->h_err = 0;
+    *plan = p;
+    return PG_OK;
+}
+
+pg_status pg_plan_run(pg_plan *p, const pg_batch *hb, void *out, void *stream)
+{
+    t_last_error.clear();
+    if (!p) return fail(PG_ERR_INVALID_ARG, "plan must not be NULL");
+    pg_status st = validate(hb, &p->grid);
+    if (st) return st;
+    if (hb->n_mol > p->max_mol || hb->n_atoms > p->max_atoms)
+        return fail(PG_ERR_INVALID_ARG, "batch (%d molecules, %d atoms) exceeds plan capacity "
+                                        "(%d, %d)", hb->n_mol, hb->n_atoms, p->max_mol,
+                    p->max_atoms);
+    if (hb->n_mol > 0 && !out) return fail(PG_ERR_INVALID_ARG, "out must not be NULL");
+    if ((uintptr_t)out % dtype_size(p->dtype) != 0)
+        return fail(PG_ERR_INVALID_ARG, "out is not aligned to its element size");
+    int dev = -1;
+    PG_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != p->device) return fail(PG_ERR_INVALID_ARG, "plan belongs to device %d", p->device);
+    if (hb->n_mol == 0) return PG_OK;
+    Device *d = nullptr;
+    if ((st = get_device(&d))) return st;
+
+    const void *host[5] = {hb->coords, hb->elem, hb->mol_off, hb->origin, hb->spacing};
+    const size_t bytes[5] = {(size_t)hb->n_atoms * 12, (size_t)hb->n_atoms * 4,
+                             (size_t)(hb->n_mol + 1) * 4, (size_t)hb->n_mol * 12,
+                             (size_t)hb->n_mol * 12};
+    void *const dst[5] = {p->d_coords, p->d_elem, p->d_moloff, p->d_origin, p->d_spacing};
+    const void *src[5];
+    size_t cnt[5];
+    for (int i = 0; i < 5; ++i) {
+        unsigned char *slot = p->h_stage + p->stage_off[i];
+        if (bytes[i] == 0) {  // graphs take no zero-length copies: move 16 dummy bytes
+            src[i] = slot;
+            cnt[i] = 16;
+        } else if (is_pinned(host[i])) {
+            src[i] = host[i];
+            cnt[i] = bytes[i];
+        } else {
+            std::memcpy(slot, host[i], bytes[i]);
+            src[i] = slot;
+            cnt[i] = bytes[i];
+        }
+    }
+    pg_batch db = *hb;
+    db.coords = p->d_coords;
+    db.elem = p->d_elem;
+    db.mol_off = p->d_moloff;
+    db.origin = p->d_origin;
+    db.spacing = p->d_spacing;
+    KernelLaunch kl;
+    if ((st = plan_forward(&db, &p->grid, p->dtype, out, p->tuning, *d, p->d_err, &kl)))
+        return st;
+    if ((st = plan_update_graph(p, src, cnt, dst, kl))) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    PG_CUDA(cudaGraphLaunch(p->exec, s), "cudaGraphLaunch");
+    PG_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    return report_bits(*p->h_err);
+}
+
+pg_status pg_plan_destroy(pg_plan *p)
+{
+    t_last_error.clear();
+    if (p) plan_free(p);
+    return PG_OK;
+}
+
+void pg_shutdown(void)
+{
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        int cur = -1;
+        cudaGetDevice(&cur);
+        for (auto &kv : g_devices) {
+            cudaSetDevice(kv.first);
+            cudaDeviceSynchronize();
+            cudaFree(kv.second.err);
+        }
+        g_devices.clear();
+        if (cur >= 0) cudaSetDevice(cur);
+    }
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune.clear();
+}
+
+}  // extern "C"

@@ -1,0 +1,241 @@
+// Coordinate adjoint of the voxelization (sm_103a).
+//
+// Sec. IV-C differentiates the MSE between two grids with respect to an atom position
+// through the separable voxel function.  Generalised to any upstream gradient
+// g = dL/dG and to the point-sampled Gaussian, the derivative of
+//     G_c(v) = sum_a chi(d) exp(-|d|^2 / 2 sigma_c^2),   d = v - x_a,
+// with respect to x_a is chi(d) exp(-|d|^2 / 2 sigma^2) d / sigma^2, so
+//     dL/dx_a = (1/sigma^2) sum_{v : chi} g_{c(a)}(v) exp(-|d|^2 / 2 sigma^2) d.
+// (The indicator is piecewise constant; its jump at the cutoff surface is not part of the
+// derivative.)
+//
+// One warp owns one atom and walks the voxels of the atom's cutoff box (clamped to the grid,
+// or wrapped for periodic cells), 32 voxels per step with z fastest so the reads of g are
+// coalesced.  Each lane keeps a partial sum; a fixed butterfly reduction combines them.  Each
+// atom's output is written by exactly one lane, so there are no atomics and the result is
+// deterministic.  Reads are ~(2 r_c / h)^3 voxels per atom: this kernel is latency-bound and
+// small next to the forward pass.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "pg_internal.h"
+
+namespace pgi {
+
+namespace {
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float wrap(float d, float L, float invL)
+{
+    return fmaf(-L, rintf(d * invL), d);
+}
+
+template <typename T>
+__device__ __forceinline__ float to_float(T v);
+template <>
+__device__ __forceinline__ float to_float<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ float to_float<__half>(__half v) { return __half2float(v); }
+template <>
+__device__ __forceinline__ float to_float<__nv_bfloat16>(__nv_bfloat16 v)
+{
+    return __bfloat162float(v);
+}
+
+// Support of one axis: first unwrapped index and count of voxels to visit.
+template <int CUT, bool PER>
+__device__ __forceinline__ void axis_support(float a, float o, float h, int n, float rc,
+                                             int &lo, int &cnt)
+{
+    if (CUT == PG_CUTOFF_NONE) {
+        lo = 0;
+        cnt = n;
+        return;
+    }
+    const float inv_h = 1.0f / h;
+    int l = (int)floorf((a - rc - o) * inv_h - 0.5f) - 1;
+    int u = (int)ceilf((a + rc - o) * inv_h - 0.5f) + 1;
+    if (PER) {
+        if (u - l + 1 > n) u = l + n - 1;
+    } else {
+        l = max(l, 0);
+        u = min(u, n - 1);
+    }
+    lo = l;
+    cnt = max(u - l + 1, 0);
+}
+
+__device__ __forceinline__ int wrap_index(int i, int n)
+{
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+template <typename GT, int CUT, bool PER>
+__global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
+{
+    const Geometry &G = A.geo;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int warps = blockDim.x >> 5;
+    const GT *gout = reinterpret_cast<const GT *>(A.grad_out);
+
+    // Atoms before the first molecule or after the last one belong to no molecule.
+    if (G.n_mol > 0) {
+        const int first = __ldg(A.in.mol_off), last = __ldg(A.in.mol_off + G.n_mol);
+        for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < G.n_atoms;
+             a += gridDim.x * blockDim.x)
+            if (a < first || a >= last) {
+                A.grad_coords[3 * a] = 0.0f;
+                A.grad_coords[3 * a + 1] = 0.0f;
+                A.grad_coords[3 * a + 2] = 0.0f;
+            }
+    } else {
+        for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < G.n_atoms;
+             a += gridDim.x * blockDim.x) {
+            A.grad_coords[3 * a] = 0.0f;
+            A.grad_coords[3 * a + 1] = 0.0f;
+            A.grad_coords[3 * a + 2] = 0.0f;
+        }
+    }
+
+    const long long plane = (long long)G.ny * G.nz;
+    const long long grid_elems = (long long)G.nx * plane;
+    for (int b = blockIdx.x; b < G.n_mol; b += gridDim.x) {
+        const int a0 = __ldg(A.in.mol_off + b), a1 = __ldg(A.in.mol_off + b + 1);
+        const float ox = __ldg(A.in.origin + 3 * b), oy = __ldg(A.in.origin + 3 * b + 1),
+                    oz = __ldg(A.in.origin + 3 * b + 2);
+        const float hx = __ldg(A.in.spacing + 3 * b), hy = __ldg(A.in.spacing + 3 * b + 1),
+                    hz = __ldg(A.in.spacing + 3 * b + 2);
+        const bool off_ok = (a0 >= 0) && (a0 <= a1) && (a1 <= G.n_atoms);
+        const bool sp_ok = (hx > 0.0f) && (hy > 0.0f) && (hz > 0.0f) && (hx < INFINITY) &&
+                           (hy < INFINITY) && (hz < INFINITY);
+        if (!off_ok) {
+            if (threadIdx.x == 0) atomicOr(A.err, PG_DEVERR_OFFSETS);
+            continue;
+        }
+        const float Lx = G.nx * hx, Ly = G.ny * hy, Lz = G.nz * hz;
+        const float iLx = 1.0f / Lx, iLy = 1.0f / Ly, iLz = 1.0f / Lz;
+        for (int a = a0 + warp; a < a1; a += warps) {
+            const int c = __ldg(A.in.elem + a);
+            if ((unsigned)c >= (unsigned)G.C || !sp_ok) {
+                if (lane == 0) {
+                    atomicOr(A.err, sp_ok ? PG_DEVERR_ELEMENT : PG_DEVERR_SPACING);
+                    A.grad_coords[3 * a] = 0.0f;
+                    A.grad_coords[3 * a + 1] = 0.0f;
+                    A.grad_coords[3 * a + 2] = 0.0f;
+                }
+                continue;
+            }
+            const float ax = __ldg(A.in.coords + 3 * a), ay = __ldg(A.in.coords + 3 * a + 1),
+                        az = __ldg(A.in.coords + 3 * a + 2);
+            const float q = G.q[c], r2 = G.r2[c], rc = G.rcull[c];
+            int ilo, ni, jlo, nj, klo, nk;
+            axis_support<CUT, PER>(ax, ox, hx, G.nx, rc, ilo, ni);
+            axis_support<CUT, PER>(ay, oy, hy, G.ny, rc, jlo, nj);
+            axis_support<CUT, PER>(az, oz, hz, G.nz, rc, klo, nk);
+            const int njk = nj * nk;
+            const long long total = (long long)ni * njk;
+            const GT *g = gout + ((long long)b * G.C + c) * grid_elems;
+            float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+#pragma unroll 4
+            for (long long f = lane; f < total; f += 32) {
+                const int fi = (int)(f / njk);
+                const int rem = (int)(f - (long long)fi * njk);
+                const int fj = rem / nk;
+                const int fk = rem - fj * nk;
+                int i = ilo + fi, j = jlo + fj, k = klo + fk;
+                if (PER) {
+                    i = wrap_index(i, G.nx);
+                    j = wrap_index(j, G.ny);
+                    k = wrap_index(k, G.nz);
+                }
+                float dx = fmaf((float)i + 0.5f, hx, ox) - ax;
+                float dy = fmaf((float)j + 0.5f, hy, oy) - ay;
+                float dz = fmaf((float)k + 0.5f, hz, oz) - az;
+                if (PER) {
+                    dx = wrap(dx, Lx, iLx);
+                    dy = wrap(dy, Ly, iLy);
+                    dz = wrap(dz, Lz, iLz);
+                }
+                const float dx2 = dx * dx;
+                const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx2));
+                bool in;
+                if (CUT == PG_CUTOFF_SPHERE)
+                    in = d2 <= r2;
+                else if (CUT == PG_CUTOFF_BOX)
+                    in = fmaxf(dx2, fmaxf(dy * dy, dz * dz)) <= r2;
+                else
+                    in = true;
+                if (in) {
+                    const float w =
+                        to_float<GT>(g[(long long)i * plane + (long long)j * G.nz + k]) *
+                        ex2_approx(-q * d2);
+                    sx = fmaf(w, dx, sx);
+                    sy = fmaf(w, dy, sy);
+                    sz = fmaf(w, dz, sz);
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                sz += __shfl_xor_sync(0xffffffffu, sz, o);
+            }
+            if (lane == 0) {
+                const float s = G.inv_s2[c];
+                A.grad_coords[3 * a] = sx * s;
+                A.grad_coords[3 * a + 1] = sy * s;
+                A.grad_coords[3 * a + 2] = sz * s;
+            }
+        }
+    }
+}
+
+template <typename GT>
+const void *pick(int cutoff, int periodic)
+{
+    if (periodic) {
+        if (cutoff == PG_CUTOFF_SPHERE) return (const void *)backward_kernel<GT, PG_CUTOFF_SPHERE, true>;
+        if (cutoff == PG_CUTOFF_BOX) return (const void *)backward_kernel<GT, PG_CUTOFF_BOX, true>;
+        return (const void *)backward_kernel<GT, PG_CUTOFF_NONE, true>;
+    }
+    if (cutoff == PG_CUTOFF_SPHERE) return (const void *)backward_kernel<GT, PG_CUTOFF_SPHERE, false>;
+    if (cutoff == PG_CUTOFF_BOX) return (const void *)backward_kernel<GT, PG_CUTOFF_BOX, false>;
+    return (const void *)backward_kernel<GT, PG_CUTOFF_NONE, false>;
+}
+
+}  // namespace
+
+cudaError_t backward_plan(const BackwardArgs &a, int grad_dtype, int sm_count, KernelLaunch *kl)
+{
+    const void *f = grad_dtype == PG_F32   ? pick<float>(a.geo.cutoff, a.geo.periodic)
+                    : grad_dtype == PG_F16 ? pick<__half>(a.geo.cutoff, a.geo.periodic)
+                                           : pick<__nv_bfloat16>(a.geo.cutoff, a.geo.periodic);
+    const int threads = 256;
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    long long blocks = (long long)sm_count * per_sm;
+    const long long need = a.geo.n_mol > 0 ? a.geo.n_mol : 1;
+    if (blocks > need) blocks = need;
+    // Enough blocks to zero stray atoms even with an empty batch.
+    const long long need_zero = (a.geo.n_atoms + threads - 1) / threads;
+    if (blocks < 1) blocks = 1;
+    if (a.geo.n_mol == 0 && need_zero > blocks) blocks = need_zero < 1024 ? need_zero : 1024;
+    kl->func = f;
+    kl->grid = dim3((unsigned)blocks);
+    kl->block = dim3((unsigned)threads);
+    kl->smem = 0;
+    set_args(kl, a);
+    return cudaSuccess;
+}
+
+}  // namespace pgi

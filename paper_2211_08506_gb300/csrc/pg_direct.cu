@@ -1,0 +1,375 @@
+// Direct per-voxel gather for batched Gaussian-density voxelization (sm_103a).
+//
+// Computes Sec. III-A Eq. 1 in its point-sampled, unnormalised, explicitly truncated form
+// (Sec. VI-B): G[b][c][v] = sum_{a in b, elem a = c} chi(d) 2^(-q_c |d|^2), d = v - x_a.
+//
+// Work decomposition.  The output is a dense [B][C][nx][ny][nz] array and, with ~1% of
+// voxels non-zero, writing it is the whole cost: the kernel is a write-bandwidth-bound
+// fill with sparse splats.  One work item is one contiguous (y, z) plane of one
+// (molecule b, channel c, x index) triple; item index == plane index, so consecutive items
+// are consecutive memory.  Persistent warps walk the items with a fixed stride.
+//
+// Per item, one warp
+//   1. culls the molecule's atoms 32 at a time with a warp ballot: an atom survives if it
+//      belongs to channel c and its (nearest-image) x distance to the plane is within the
+//      cutoff; survivors are compacted, in atom order, into the warp's shared-memory stage
+//      as {dx, y, z};
+//   2. walks the plane 32 lanes x VEC voxels at a time (VEC = 16 bytes of output per
+//      lane).  For each such row group it ballots the staged atoms against the group's
+//      (y, z) bounding box, then every lane adds the survivors' contributions to its VEC
+//      voxels, applying the exact cutoff test per voxel;
+//   3. stores the VEC values with one 16-byte store per lane (FP32, or FP16/BF16 rounded
+//      to nearest even), zeros included.
+// Culls are conservative and survivors are visited in atom order, so every voxel sums the
+// same terms in the same order whatever the launch shape: results are bitwise identical
+// across tunings and equal to the unstaged fallback used when an item has more than
+// kStageCap candidates.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "pg_internal.h"
+
+namespace pgi {
+
+namespace {
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Nearest-image displacement on a ring of length L (invL = 1/L).
+__device__ __forceinline__ float wrap(float d, float L, float invL)
+{
+    return fmaf(-L, rintf(d * invL), d);
+}
+
+template <typename T>
+__device__ __forceinline__ T from_float(float v);
+template <>
+__device__ __forceinline__ float from_float<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __half from_float<__half>(float v) { return __float2half_rn(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_float<__nv_bfloat16>(float v)
+{
+    return __float2bfloat16_rn(v);
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ uint4 pack16(const float (&acc)[VEC]);
+
+template <>
+__device__ __forceinline__ uint4 pack16<float, 4>(const float (&a)[4])
+{
+    return make_uint4(__float_as_uint(a[0]), __float_as_uint(a[1]), __float_as_uint(a[2]),
+                      __float_as_uint(a[3]));
+}
+
+__device__ __forceinline__ unsigned h2u(__half2 h) { return *reinterpret_cast<unsigned *>(&h); }
+__device__ __forceinline__ unsigned b2u(__nv_bfloat162 h)
+{
+    return *reinterpret_cast<unsigned *>(&h);
+}
+
+template <>
+__device__ __forceinline__ uint4 pack16<__half, 8>(const float (&a)[8])
+{
+    return make_uint4(h2u(__floats2half2_rn(a[0], a[1])), h2u(__floats2half2_rn(a[2], a[3])),
+                      h2u(__floats2half2_rn(a[4], a[5])), h2u(__floats2half2_rn(a[6], a[7])));
+}
+
+template <>
+__device__ __forceinline__ uint4 pack16<__nv_bfloat16, 8>(const float (&a)[8])
+{
+    return make_uint4(b2u(__floats2bfloat162_rn(a[0], a[1])),
+                      b2u(__floats2bfloat162_rn(a[2], a[3])),
+                      b2u(__floats2bfloat162_rn(a[4], a[5])),
+                      b2u(__floats2bfloat162_rn(a[6], a[7])));
+}
+
+template <int HINT>
+__device__ __forceinline__ void store16(void *p, uint4 v)
+{
+    if (HINT == 1)
+        __stcs(reinterpret_cast<uint4 *>(p), v);
+    else
+        *reinterpret_cast<uint4 *>(p) = v;
+}
+
+// Per-lane accumulation of one atom's contribution into the lane's VEC voxels.
+template <int VEC, int CUT, bool PER>
+struct LaneVoxels {
+    float vy;        // voxel-centre y of the lane's row
+    float vz[VEC];   // voxel-centre z of the lane's voxels
+    float acc[VEC];
+
+    __device__ __forceinline__ void add(float dx, float ay, float az, float q, float r2, float Ly,
+                                        float iLy, float Lz, float iLz)
+    {
+        float dy = vy - ay;
+        if (PER) dy = wrap(dy, Ly, iLy);
+        const float dx2 = dx * dx;
+        const float dxy2 = fmaf(dy, dy, dx2);
+        const float mxy = fmaxf(dx2, dy * dy);
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) {
+            float dz = vz[k] - az;
+            if (PER) dz = wrap(dz, Lz, iLz);
+            const float d2 = fmaf(dz, dz, dxy2);
+            const float t = ex2_approx(-q * d2);
+            if (CUT == PG_CUTOFF_SPHERE)
+                acc[k] += (d2 <= r2) ? t : 0.0f;
+            else if (CUT == PG_CUTOFF_BOX)
+                acc[k] += (fmaxf(mxy, dz * dz) <= r2) ? t : 0.0f;
+            else
+                acc[k] += t;
+        }
+    }
+};
+
+// Conservative test: can an atom at (dx, ay, az) reach the box of voxel centres
+// [cy +- wy] x [cz +- wz] of the current row group?
+template <int CUT, bool PER>
+__device__ __forceinline__ bool reaches(float dx, float ay, float az, float cy, float wy,
+                                        float cz, float wz, float rc, float Ly, float iLy,
+                                        float Lz, float iLz)
+{
+    if (CUT == PG_CUTOFF_NONE) return true;
+    float ey = cy - ay, ez = cz - az;
+    if (PER) {
+        ey = wrap(ey, Ly, iLy);
+        ez = wrap(ez, Lz, iLz);
+    }
+    const float gy = fmaxf(fabsf(ey) - wy, 0.0f);
+    const float gz = fmaxf(fabsf(ez) - wz, 0.0f);
+    if (CUT == PG_CUTOFF_SPHERE) return fmaf(dx, dx, fmaf(gy, gy, gz * gz)) <= rc * rc;
+    return fmaxf(gy, gz) <= rc;
+}
+
+template <typename T, int VEC, int CUT, bool PER, int HINT>
+__global__ void __launch_bounds__(512) direct_kernel(const DirectArgs A)
+{
+    extern __shared__ float4 stage_all[];
+    const Geometry &G = A.geo;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int warps_per_block = blockDim.x >> 5;
+    float4 *stage = stage_all + warp * kStageCap;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    const long long n_items = (long long)G.n_mol * G.C * G.nx;
+    const int plane = G.ny * G.nz;
+    const int nvec = plane / VEC;
+    // Lane start position inside a plane and its advance per row group of 32*VEC elements.
+    const int y_start = (lane * VEC) / G.nz, z_start = (lane * VEC) % G.nz;
+    const int y_step = (32 * VEC) / G.nz, z_step = (32 * VEC) % G.nz;
+
+    for (long long item = (long long)blockIdx.x * warps_per_block + warp; item < n_items;
+         item += (long long)gridDim.x * warps_per_block) {
+        const int x = (int)(item % G.nx);
+        const long long bc = item / G.nx;
+        const int c = (int)(bc % G.C);
+        const int b = (int)(bc / G.C);
+        T *out = reinterpret_cast<T *>(A.out) + item * (long long)plane;
+
+        int a0 = __ldg(A.in.mol_off + b), a1 = __ldg(A.in.mol_off + b + 1);
+        const float ox = __ldg(A.in.origin + 3 * b), oy = __ldg(A.in.origin + 3 * b + 1),
+                    oz = __ldg(A.in.origin + 3 * b + 2);
+        const float hx = __ldg(A.in.spacing + 3 * b), hy = __ldg(A.in.spacing + 3 * b + 1),
+                    hz = __ldg(A.in.spacing + 3 * b + 2);
+        const bool report = (lane == 0) && (c == 0) && (x == 0);
+        const bool off_ok = (a0 >= 0) && (a0 <= a1) && (a1 <= G.n_atoms);
+        const bool sp_ok = (hx > 0.0f) && (hy > 0.0f) && (hz > 0.0f) && (hx < INFINITY) &&
+                           (hy < INFINITY) && (hz < INFINITY);
+        if (!off_ok || !sp_ok) {
+            if (report) atomicOr(A.err, (off_ok ? 0u : PG_DEVERR_OFFSETS) |
+                                            (sp_ok ? 0u : PG_DEVERR_SPACING));
+            a0 = a1 = 0;
+        }
+        const float q = G.q[c], r2 = G.r2[c], rc = G.rcull[c];
+        const float Lx = G.nx * hx, Ly = G.ny * hy, Lz = G.nz * hz;
+        const float iLx = 1.0f / Lx, iLy = 1.0f / Ly, iLz = 1.0f / Lz;
+        if (PER && CUT != PG_CUTOFF_NONE && (lane == 0) && (x == 0) && sp_ok &&
+            (2.0f * rc >= fminf(Lx, fminf(Ly, Lz))) && a1 > a0)
+            atomicOr(A.err, PG_DEVERR_PERIODIC);
+        const float vx = fmaf((float)x + 0.5f, hx, ox);
+
+        // 1. Cull and stage this channel's atoms near the plane (atom order kept).
+        int count = 0;
+        bool bad_elem = false;
+        for (int base = a0; base < a1; base += 32) {
+            const int ai = base + lane;
+            bool ok = false;
+            float dx = 0.0f, ay = 0.0f, az = 0.0f;
+            if (ai < a1) {
+                const int e = __ldg(A.in.elem + ai);
+                if ((unsigned)e >= (unsigned)G.C) {
+                    bad_elem = true;
+                } else if (e == c) {
+                    const float ax = __ldg(A.in.coords + 3 * ai);
+                    ay = __ldg(A.in.coords + 3 * ai + 1);
+                    az = __ldg(A.in.coords + 3 * ai + 2);
+                    dx = vx - ax;
+                    if (PER) dx = wrap(dx, Lx, iLx);
+                    ok = (CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc);
+                }
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const int pos = count + __popc(m & lt_mask);
+                if (pos < kStageCap) stage[pos] = make_float4(dx, ay, az, 0.0f);
+            }
+            count += __popc(m);
+        }
+        if (__any_sync(0xffffffffu, bad_elem) && report) atomicOr(A.err, PG_DEVERR_ELEMENT);
+        __syncwarp();
+
+        // 2./3. Row groups of 32 lanes x VEC voxels.
+        int y = y_start, z0 = z_start;
+        for (int g = 0; g < nvec; g += 32) {
+            const int v = g + lane;
+            LaneVoxels<VEC, CUT, PER> lv;
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) lv.acc[k] = 0.0f;
+            if (count > 0) {
+                const int last = min(31, nvec - 1 - g);
+                const int y_lo = __shfl_sync(0xffffffffu, y, 0);
+                const int y_hi = __shfl_sync(0xffffffffu, y, last);
+                int z_lo = 0, z_hi = G.nz - 1;
+                if (y_lo == y_hi) {
+                    z_lo = __shfl_sync(0xffffffffu, z0, 0);
+                    z_hi = __shfl_sync(0xffffffffu, z0, last) + VEC - 1;
+                }
+                const float cy = fmaf(0.5f * (float)(y_lo + y_hi) + 0.5f, hy, oy);
+                const float wy = 0.5f * (float)(y_hi - y_lo) * hy;
+                const float cz = fmaf(0.5f * (float)(z_lo + z_hi) + 0.5f, hz, oz);
+                const float wz = 0.5f * (float)(z_hi - z_lo) * hz;
+                lv.vy = fmaf((float)y + 0.5f, hy, oy);
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) lv.vz[k] = fmaf((float)(z0 + k) + 0.5f, hz, oz);
+
+                if (count <= kStageCap) {
+                    for (int cb = 0; cb < count; cb += 32) {
+                        const int j = cb + lane;
+                        bool ok = false;
+                        if (j < count) {
+                            const float4 s = stage[j];
+                            ok = reaches<CUT, PER>(s.x, s.y, s.z, cy, wy, cz, wz, rc, Ly, iLy,
+                                                   Lz, iLz);
+                        }
+                        unsigned m = __ballot_sync(0xffffffffu, ok);
+                        while (m) {
+                            const int src = __ffs(m) - 1;
+                            m &= m - 1;
+                            const float4 s = stage[cb + src];
+                            lv.add(s.x, s.y, s.z, q, r2, Ly, iLy, Lz, iLz);
+                        }
+                    }
+                } else {
+                    // Unstaged fallback: the same atoms in the same order, read from global.
+                    for (int base = a0; base < a1; base += 32) {
+                        const int ai = base + lane;
+                        bool ok = false;
+                        float dx = 0.0f, ay = 0.0f, az = 0.0f;
+                        if (ai < a1 && __ldg(A.in.elem + ai) == c) {
+                            const float ax = __ldg(A.in.coords + 3 * ai);
+                            ay = __ldg(A.in.coords + 3 * ai + 1);
+                            az = __ldg(A.in.coords + 3 * ai + 2);
+                            dx = vx - ax;
+                            if (PER) dx = wrap(dx, Lx, iLx);
+                            ok = ((CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc)) &&
+                                 reaches<CUT, PER>(dx, ay, az, cy, wy, cz, wz, rc, Ly, iLy, Lz,
+                                                   iLz);
+                        }
+                        unsigned m = __ballot_sync(0xffffffffu, ok);
+                        while (m) {
+                            const int src = __ffs(m) - 1;
+                            m &= m - 1;
+                            const float sdx = __shfl_sync(0xffffffffu, dx, src);
+                            const float sy = __shfl_sync(0xffffffffu, ay, src);
+                            const float sz = __shfl_sync(0xffffffffu, az, src);
+                            lv.add(sdx, sy, sz, q, r2, Ly, iLy, Lz, iLz);
+                        }
+                    }
+                }
+            }
+            if (v < nvec) {
+                if constexpr (VEC * sizeof(T) == 16) {
+                    store16<HINT>(out + (long long)v * VEC, pack16<T, VEC>(lv.acc));
+                } else {
+                    out[v] = from_float<T>(lv.acc[0]);
+                }
+            }
+            y += y_step;
+            z0 += z_step;
+            if (z0 >= G.nz) {
+                z0 -= G.nz;
+                ++y;
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T, int VEC, int CUT, bool PER>
+const void *pick_hint(int hint)
+{
+    return hint == 1 ? (const void *)direct_kernel<T, VEC, CUT, PER, 1>
+                     : (const void *)direct_kernel<T, VEC, CUT, PER, 0>;
+}
+
+template <typename T, int VEC>
+const void *pick_shape(int cutoff, int periodic, int hint)
+{
+    if (periodic) {
+        if (cutoff == PG_CUTOFF_SPHERE) return pick_hint<T, VEC, PG_CUTOFF_SPHERE, true>(hint);
+        if (cutoff == PG_CUTOFF_BOX) return pick_hint<T, VEC, PG_CUTOFF_BOX, true>(hint);
+        return pick_hint<T, VEC, PG_CUTOFF_NONE, true>(hint);
+    }
+    if (cutoff == PG_CUTOFF_SPHERE) return pick_hint<T, VEC, PG_CUTOFF_SPHERE, false>(hint);
+    if (cutoff == PG_CUTOFF_BOX) return pick_hint<T, VEC, PG_CUTOFF_BOX, false>(hint);
+    return pick_hint<T, VEC, PG_CUTOFF_NONE, false>(hint);
+}
+
+}  // namespace
+
+cudaError_t direct_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tuning &t,
+                        int sm_count, KernelLaunch *kl)
+{
+    const int hint = t.store_hint == 1 ? 1 : 0;
+    const void *f = nullptr;
+    if (dtype == PG_F32)
+        f = vec_ok ? pick_shape<float, 4>(a.geo.cutoff, a.geo.periodic, hint)
+                   : pick_shape<float, 1>(a.geo.cutoff, a.geo.periodic, hint);
+    else if (dtype == PG_F16)
+        f = vec_ok ? pick_shape<__half, 8>(a.geo.cutoff, a.geo.periodic, hint)
+                   : pick_shape<__half, 1>(a.geo.cutoff, a.geo.periodic, hint);
+    else
+        f = vec_ok ? pick_shape<__nv_bfloat16, 8>(a.geo.cutoff, a.geo.periodic, hint)
+                   : pick_shape<__nv_bfloat16, 1>(a.geo.cutoff, a.geo.periodic, hint);
+
+    int threads = t.block_threads;
+    if (threads != 128 && threads != 256 && threads != 512) threads = 256;
+    const size_t smem = (size_t)(threads / 32) * kStageCap * sizeof(float4);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (t.blocks_per_sm > 0 && t.blocks_per_sm < per_sm) per_sm = t.blocks_per_sm;
+    const long long items = (long long)a.geo.n_mol * a.geo.C * a.geo.nx;
+    const long long need = (items + threads / 32 - 1) / (threads / 32);
+    long long blocks = (long long)sm_count * per_sm;
+    if (blocks > need) blocks = need;
+    if (blocks < 1) blocks = 1;
+    kl->func = f;
+    kl->grid = dim3((unsigned)blocks);
+    kl->block = dim3((unsigned)threads);
+    kl->smem = smem;
+    set_args(kl, a);
+    return cudaSuccess;
+}
+
+}  // namespace pgi

@@ -1,0 +1,107 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "pg.h"
+
+namespace pgi {
+
+constexpr int kMaxC = PG_MAX_CHANNELS;
+// Candidate atoms one warp stages in shared memory for one (molecule, channel, x-plane)
+// item.  Items with more candidates take the unstaged path (same result, bit for bit).
+constexpr int kStageCap = 128;
+
+// Per-call constants (kernel parameter space; uniform across the grid).
+struct Geometry {
+    int n_mol, n_atoms;
+    int nx, ny, nz, C;
+    int cutoff;    // pg_cutoff
+    int periodic;  // 0/1
+    float q[kMaxC];      // log2(e) / (2 sigma_c^2): G = 2^(-q d^2)
+    float r2[kMaxC];     // r_c^2, the exact per-voxel cutoff test
+    float rcull[kMaxC];  // r_c widened by a relative 1e-5 for conservative culling
+    float inv_s2[kMaxC]; // 1 / sigma_c^2 (adjoint)
+};
+
+struct Inputs {
+    const float *coords;
+    const int *elem;
+    const int *mol_off;
+    const float *origin;
+    const float *spacing;
+};
+
+struct DirectArgs {
+    Inputs in;
+    void *out;
+    unsigned *err;
+    Geometry geo;
+};
+
+struct BackwardArgs {
+    Inputs in;
+    const void *grad_out;
+    float *grad_coords;
+    unsigned *err;
+    Geometry geo;
+};
+
+struct SeparableArgs {
+    Inputs in;
+    void *out;
+    unsigned *err;
+    Geometry geo;
+    int m_tiles;  // 128-row tiles of the (channel, x) axis per molecule
+    int n_tile;   // output columns per tensor-core tile
+};
+
+// A fully resolved kernel launch (function, shape, single by-value argument struct), so
+// the same description can be launched directly or added to a CUDA graph.
+struct KernelLaunch {
+    const void *func = nullptr;
+    dim3 grid, block;
+    size_t smem = 0;
+    size_t args_size = 0;
+    alignas(16) unsigned char args[2048];
+    void *params[1];
+};
+
+// Direct per-voxel gather (pg_direct.cu).
+cudaError_t direct_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tuning &t,
+                        int sm_count, KernelLaunch *kl);
+
+// Coordinate adjoint (pg_backward.cu).
+cudaError_t backward_plan(const BackwardArgs &a, int grad_dtype, int sm_count, KernelLaunch *kl);
+
+// Separable tcgen05 contraction (pg_separable.cu).  Returns cudaErrorNotSupported for
+// shapes it does not cover.
+cudaError_t separable_plan(const SeparableArgs &a, int dtype, const pg_tuning &t, int sm_count,
+                           KernelLaunch *kl);
+bool separable_supported(const Geometry &g, int dtype);
+
+// Autotuner helpers (pg_tune.cu): order-independent 64-bit hash of a buffer's bits, and
+// the max-abs difference / max-abs reference of two dtype buffers.
+cudaError_t buffer_hash(const void *buf, size_t bytes, unsigned long long *d_out,
+                        cudaStream_t s);
+cudaError_t buffer_compare(const void *a, const void *b, size_t n, int dtype, float *d_out2,
+                           cudaStream_t s);
+
+inline cudaError_t launch(KernelLaunch &kl, cudaStream_t s)
+{
+    kl.params[0] = kl.args;
+    return cudaLaunchKernel(kl.func, kl.grid, kl.block, kl.params, kl.smem, s);
+}
+
+template <class A>
+inline void set_args(KernelLaunch *kl, const A &a)
+{
+    static_assert(sizeof(A) <= sizeof(kl->args), "kernel argument struct too large");
+    __builtin_memcpy(kl->args, &a, sizeof(A));
+    kl->args_size = sizeof(A);
+}
+
+}  // namespace pgi

@@ -214,6 +214,7 @@ def precision_form(shard: int | None = None, n_mol: int = 4096) -> Workload:
 
 ZIPF_EXPONENT = 1.2
 CRYSTAL_ELEMENTS = 10
+JAMMING_SKIP = 0.32
 
 
 def crystal_cell(rng: np.random.Generator, n_atoms: int, edge_lo=5.0, edge_hi=15.0,
@@ -225,16 +226,22 @@ def crystal_cell(rng: np.random.Generator, n_atoms: int, edge_lo=5.0, edge_hi=15
     the cell edges are redrawn and placement restarts with the same atom count.
     Returns (edges[3], frac[n,3], redraws)."""
     redraws = 0
-    block = 64
+    v_excl = math.pi / 6.0 * min_sep ** 3
     while True:
         edges = rng.uniform(edge_lo, edge_hi, size=3)
+        # Above this packing fraction random sequential addition practically never
+        # places every atom within max_tries, so the cell is redrawn at once.
+        if n_atoms * v_excl / float(np.prod(edges)) > JAMMING_SKIP:
+            redraws += 1
+            continue
         placed = np.zeros((n_atoms, 3))
         ok = True
         for i in range(n_atoms):
             tries = 0
             done = False
             while tries < max_tries:
-                m = min(block, max_tries - tries)
+                # Small proposal blocks while most proposals succeed, larger ones after.
+                m = min(4 if tries == 0 else 64, max_tries - tries)
                 cand = rng.uniform(0.0, 1.0, size=(m, 3))
                 if i == 0:
                     placed[0] = cand[0]
