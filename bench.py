@@ -122,6 +122,45 @@ class ClockSampler:
                 "samples_in_timed_region": len(inside)}
 
 
+def write_probe_gbs(nbytes=4 << 30, reps=10):
+    """Write-only bandwidth of plain device fills over >= 4 GB: torch fill kernels (byte and
+    fp32 views) and, when the CUDA runtime is reachable, cudaMemsetAsync.  Returns
+    (best GB/s, {method: GB/s})."""
+    import ctypes
+    import torch
+
+    buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    methods = {"torch_zero_u8": lambda: buf.zero_(),
+               "torch_fill_f32": lambda: buf.view(torch.float32).fill_(0.0)}
+    for name in ("libcudart.so.13", "/usr/local/cuda/lib64/libcudart.so.13"):
+        try:
+            rt = ctypes.CDLL(name)
+            rt.cudaMemsetAsync.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t,
+                                           ctypes.c_void_p]
+            rt.cudaMemsetAsync.restype = ctypes.c_int
+            stream = torch.cuda.current_stream().cuda_stream
+            methods["cudaMemsetAsync"] = lambda rt=rt, stream=stream: rt.cudaMemsetAsync(
+                ctypes.c_void_p(buf.data_ptr()), 0, ctypes.c_size_t(nbytes),
+                ctypes.c_void_p(stream))
+            break
+        except (OSError, AttributeError):
+            continue
+    res = {}
+    for name, fn in methods.items():
+        for _ in range(3):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        res[name] = nbytes * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+    del buf
+    torch.cuda.empty_cache()
+    return max(res.values()), res
+
+
 def kernel_source_sha():
     h = hashlib.sha256()
     for f in ("pg_direct.cu", "pg_separable.cu"):
@@ -236,8 +275,13 @@ def run_ours(args):
     pkg.build()
     from paper_2211_08506_gb300 import api
 
-    wl = synth.workload(args.workload, shard=rank if world > 1 else None)
+    kw = {"shard": rank if world > 1 else None}
+    if args.n_mol:
+        kw["n_cells" if args.workload == "crystal_shaped" else "n_mol"] = args.n_mol
+    wl = synth.workload(args.workload, **kw)
     dtype = args.dtype or wl.out_dtype
+    if args.profile:
+        return run_profile(args, wl, dtype)
     path = args.path
     grid = api.Grid.from_workload(wl)
     db = api.DeviceBatch.from_numpy(wl.batch)
@@ -315,20 +359,10 @@ def run_ours(args):
         e2e_s = float(t.item())
     plan.close()
 
-    # Write-only reference: a plain device fill of at least 4 GB.
-    probe = None
+    # Write-only reference: plain device fills of at least 4 GB.
+    probe, probe_all = None, None
     if rank == 0:
-        buf = torch.empty(4 << 30, dtype=torch.uint8, device="cuda")
-        for _ in range(3):
-            buf.zero_()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(10):
-            buf.zero_()
-        e1.record()
-        torch.cuda.synchronize()
-        probe = buf.numel() * 10 / (e0.elapsed_time(e1) / 1e3) / 1e9
-        del buf
+        probe, probe_all = write_probe_gbs()
 
     if rank != 0:
         if dist:
@@ -380,6 +414,7 @@ def run_ours(args):
             "algorithmic_bytes_per_launch": out_bytes,
             "kernel": f"{kernel} voxelization kernel",
             "write_probe_gbs": probe,
+            "write_probe_methods": probe_all,
             "frac_of_write_probe": (achieved / probe) if probe else None,
         },
         "e2e": {
@@ -398,6 +433,26 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_profile(args, wl, dtype):
+    """Plain launches for profiler captures: no tuning, no graph, no host-side extras.
+    Prints a line marked "profile" (it is not a benchmark result)."""
+    import torch
+    from paper_2211_08506_gb300 import api
+
+    grid = api.Grid.from_workload(wl)
+    db = api.DeviceBatch.from_numpy(wl.batch)
+    out = torch.empty(grid.out_shape(wl.batch.n_mol), dtype=api.DTYPES[dtype][1], device="cuda")
+    tuning = {"path": 2 if args.path == "separable" else 1, "block_threads": args.threads,
+              "blocks_per_sm": 0, "store_hint": args.store_hint, "n_tile": 128}
+    for _ in range(args.warmup + args.steps):
+        api.voxelize_tuned(db, grid, tuning, dtype=dtype, out=out)
+    torch.cuda.synchronize()
+    assert api.sync_status() == 0
+    print(json.dumps({"profile": True, "workload": wl.name, "n_mol": wl.batch.n_mol,
+                      "launches": args.warmup + args.steps, "tuning": tuning,
+                      "out_bytes": out.numel() * out.element_size()}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawTextHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -410,6 +465,11 @@ def main():
     ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default=None)
     ap.add_argument("--path", choices=["auto", "direct", "separable"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-mol", type=int, default=0, help="override the batch size")
+    ap.add_argument("--profile", action="store_true",
+                    help="plain launches only (for ncu); prints a profile line, not a result")
+    ap.add_argument("--threads", type=int, default=512, help="--profile: threads per CTA")
+    ap.add_argument("--store-hint", type=int, default=1, help="--profile: 1 = streaming stores")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -135,8 +135,8 @@ def voxelize(prob: Problem, mode: str = "bbox", threads: int = 0) -> np.ndarray:
 
 
 def voxelize_band(prob: Problem, eps: float = 1e-5, threads: int = 0):
-    """(inside, band): contributions strictly inside the cutoff by a relative margin eps,
-    and those within eps of the cutoff surface."""
+    """(inside, band): contributions inside the cutoff by more than a relative margin eps,
+    and every contribution (inside or just outside) within eps of the cutoff surface."""
     g_in = np.empty(prob.shape, np.float64)
     g_band = np.empty(prob.shape, np.float64)
     _check(_load().pgo_voxelize_band(ctypes.byref(prob.c), eps, g_in.ctypes.data,

@@ -151,9 +151,10 @@ static long wrap_index(long i, long n) { return ((i % n) + n) % n; }
 /*
  * Support-box mode: the same sum, visited atom by atom over each atom's cutoff box
  * only (chi is zero outside it).  Per voxel the atoms are still added in atom order, so
- * the result equals brute force bit for bit.  With eps > 0 it instead splits each
- * contribution into out (strictly inside, |d|^2 < r^2 (1 - eps)) and band (within eps
- * relative of the cutoff surface), for parity checks of an FP32 cutoff test.
+ * the result equals brute force bit for bit.  With eps > 0 it instead splits the sum into
+ * out (contributions inside the cutoff by more than a relative eps) and band (every
+ * contribution, inside or outside, whose |d|^2 is within eps * r^2 of r^2), so that a
+ * lower-precision implementation of the cutoff test can be bracketed.
  */
 static void bbox_molecule(const pgo_problem *p, int b, double *out, double eps, double *band)
 {
@@ -178,20 +179,21 @@ static void bbox_molecule(const pgo_problem *p, int b, double *out, double eps, 
                 for (long ku = klo; ku <= khi; ++ku) {
                     long k = p->periodic ? wrap_index(ku, p->nz) : ku;
                     double dz = disp(p, b, 2, k, z);
-                    if (!inside(p->cutoff, dx, dy, dz, r)) continue;
                     double d2 = dx * dx + dy * dy + dz * dz;
-                    double g = exp(-d2 / s2);
                     long v = grid_index(p, b, c, i, j, k);
                     if (eps > 0.0 && p->cutoff != PGO_NONE) {
+                        /* Two-sided band: contributions within eps of the cutoff surface,
+                           inside or outside, may flip in a lower-precision test. */
                         double m2 = (p->cutoff == PGO_SPHERE)
                                         ? d2
                                         : fmax(dx * dx, fmax(dy * dy, dz * dz));
                         if (fabs(m2 - r * r) <= eps * r * r) {
-                            band[v] += g;
+                            band[v] += exp(-d2 / s2);
                             continue;
                         }
                     }
-                    out[v] += g;
+                    if (!inside(p->cutoff, dx, dy, dz, r)) continue;
+                    out[v] += exp(-d2 / s2);
                 }
             }
         }

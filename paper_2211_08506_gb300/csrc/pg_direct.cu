@@ -149,8 +149,30 @@ __device__ __forceinline__ bool reaches(float dx, float ay, float az, float cy, 
     return fmaxf(gy, gz) <= rc;
 }
 
+// Zero-fill one plane slice: lanes store 16-byte (or scalar) zeros.
+template <typename T, int VEC, int HINT>
+__device__ __forceinline__ void zero_plane(T *out, int nvec, int lane)
+{
+#pragma unroll 4
+    for (int v = lane; v < nvec; v += 32) {
+        if constexpr (VEC * sizeof(T) == 16)
+            store16<HINT>(out + (long long)v * VEC, make_uint4(0u, 0u, 0u, 0u));
+        else
+            out[v] = from_float<T>(0.0f);
+    }
+}
+
+template <typename T, int VEC, int HINT>
+__device__ __forceinline__ void store_lane(T *out, int v, const float (&acc)[VEC])
+{
+    if constexpr (VEC * sizeof(T) == 16)
+        store16<HINT>(out + (long long)v * VEC, pack16<T, VEC>(acc));
+    else
+        out[v] = from_float<T>(acc[0]);
+}
+
 template <typename T, int VEC, int CUT, bool PER, int HINT>
-__global__ void __launch_bounds__(512) direct_kernel(const DirectArgs A)
+__global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
 {
     extern __shared__ float4 stage_all[];
     const Geometry &G = A.geo;
@@ -160,157 +182,253 @@ __global__ void __launch_bounds__(512) direct_kernel(const DirectArgs A)
     float4 *stage = stage_all + warp * kStageCap;
     const unsigned lt_mask = (1u << lane) - 1u;
 
+    // Each warp owns a contiguous range of items (planes), so consecutive items share the
+    // molecule and, for molecules of at most 32 atoms, the atoms stay in registers.
     const long long n_items = (long long)G.n_mol * G.C * G.nx;
+    const long long n_warps = (long long)gridDim.x * warps_per_block;
+    const long long gw = (long long)blockIdx.x * warps_per_block + warp;
+    long long item = n_items * gw / n_warps;
+    const long long item_end = n_items * (gw + 1) / n_warps;
+    if (item >= item_end) return;
+
     const int plane = G.ny * G.nz;
     const int nvec = plane / VEC;
-    // Lane start position inside a plane and its advance per row group of 32*VEC elements.
     const int y_start = (lane * VEC) / G.nz, z_start = (lane * VEC) % G.nz;
     const int y_step = (32 * VEC) / G.nz, z_step = (32 * VEC) % G.nz;
 
-    for (long long item = (long long)blockIdx.x * warps_per_block + warp; item < n_items;
-         item += (long long)gridDim.x * warps_per_block) {
-        const int x = (int)(item % G.nx);
-        const long long bc = item / G.nx;
-        const int c = (int)(bc % G.C);
-        const int b = (int)(bc / G.C);
-        T *out = reinterpret_cast<T *>(A.out) + item * (long long)plane;
+    int x = (int)(item % G.nx);
+    int c = (int)((item / G.nx) % G.C);
+    int b = (int)(item / ((long long)G.nx * G.C));
+    int cur_b = -1;
 
-        int a0 = __ldg(A.in.mol_off + b), a1 = __ldg(A.in.mol_off + b + 1);
-        const float ox = __ldg(A.in.origin + 3 * b), oy = __ldg(A.in.origin + 3 * b + 1),
-                    oz = __ldg(A.in.origin + 3 * b + 2);
-        const float hx = __ldg(A.in.spacing + 3 * b), hy = __ldg(A.in.spacing + 3 * b + 1),
-                    hz = __ldg(A.in.spacing + 3 * b + 2);
-        const bool report = (lane == 0) && (c == 0) && (x == 0);
-        const bool off_ok = (a0 >= 0) && (a0 <= a1) && (a1 <= G.n_atoms);
-        const bool sp_ok = (hx > 0.0f) && (hy > 0.0f) && (hz > 0.0f) && (hx < INFINITY) &&
-                           (hy < INFINITY) && (hz < INFINITY);
-        if (!off_ok || !sp_ok) {
-            if (report) atomicOr(A.err, (off_ok ? 0u : PG_DEVERR_OFFSETS) |
-                                            (sp_ok ? 0u : PG_DEVERR_SPACING));
-            a0 = a1 = 0;
+    int a0 = 0, a1 = 0;
+    float ox = 0.f, oy = 0.f, oz = 0.f, hx = 1.f, hy = 1.f, hz = 1.f;
+    float Lx = 1.f, Ly = 1.f, Lz = 1.f, iLx = 1.f, iLy = 1.f, iLz = 1.f;
+    bool small = true;
+    // Lane-held atom of a small molecule (lane < a1 - a0).
+    float my_x = 0.f, my_y = 0.f, my_z = 0.f;
+    int my_e = -1;
+
+    for (; item < item_end; ++item) {
+        T *out = reinterpret_cast<T *>(A.out) + item * (long long)plane;
+        if (b != cur_b) {
+            cur_b = b;
+            a0 = __ldg(A.in.mol_off + b);
+            a1 = __ldg(A.in.mol_off + b + 1);
+            ox = __ldg(A.in.origin + 3 * b);
+            oy = __ldg(A.in.origin + 3 * b + 1);
+            oz = __ldg(A.in.origin + 3 * b + 2);
+            hx = __ldg(A.in.spacing + 3 * b);
+            hy = __ldg(A.in.spacing + 3 * b + 1);
+            hz = __ldg(A.in.spacing + 3 * b + 2);
+            const bool off_ok = (a0 >= 0) && (a0 <= a1) && (a1 <= G.n_atoms);
+            const bool sp_ok = (hx > 0.0f) && (hy > 0.0f) && (hz > 0.0f) && (hx < INFINITY) &&
+                               (hy < INFINITY) && (hz < INFINITY);
+            if (!off_ok || !sp_ok) {
+                if (lane == 0)
+                    atomicOr(A.err, (off_ok ? 0u : PG_DEVERR_OFFSETS) |
+                                        (sp_ok ? 0u : PG_DEVERR_SPACING));
+                a0 = a1 = 0;
+            }
+            Lx = G.nx * hx;
+            Ly = G.ny * hy;
+            Lz = G.nz * hz;
+            iLx = 1.0f / Lx;
+            iLy = 1.0f / Ly;
+            iLz = 1.0f / Lz;
+            small = (a1 - a0) <= 32;
+            my_e = -1;
+            bool bad = false;
+            if (small && a0 + lane < a1) {
+                const int ai = a0 + lane;
+                my_e = __ldg(A.in.elem + ai);
+                my_x = __ldg(A.in.coords + 3 * ai);
+                my_y = __ldg(A.in.coords + 3 * ai + 1);
+                my_z = __ldg(A.in.coords + 3 * ai + 2);
+                if ((unsigned)my_e >= (unsigned)G.C) {
+                    bad = true;
+                    my_e = -1;
+                }
+            }
+            if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(A.err, PG_DEVERR_ELEMENT);
         }
+
         const float q = G.q[c], r2 = G.r2[c], rc = G.rcull[c];
-        const float Lx = G.nx * hx, Ly = G.ny * hy, Lz = G.nz * hz;
-        const float iLx = 1.0f / Lx, iLy = 1.0f / Ly, iLz = 1.0f / Lz;
-        if (PER && CUT != PG_CUTOFF_NONE && (lane == 0) && (x == 0) && sp_ok &&
-            (2.0f * rc >= fminf(Lx, fminf(Ly, Lz))) && a1 > a0)
+        if (PER && CUT != PG_CUTOFF_NONE && lane == 0 && x == 0 && a1 > a0 &&
+            (2.0f * rc >= fminf(Lx, fminf(Ly, Lz))))
             atomicOr(A.err, PG_DEVERR_PERIODIC);
         const float vx = fmaf((float)x + 0.5f, hx, ox);
 
-        // 1. Cull and stage this channel's atoms near the plane (atom order kept).
-        int count = 0;
-        bool bad_elem = false;
-        for (int base = a0; base < a1; base += 32) {
-            const int ai = base + lane;
-            bool ok = false;
-            float dx = 0.0f, ay = 0.0f, az = 0.0f;
-            if (ai < a1) {
-                const int e = __ldg(A.in.elem + ai);
-                if ((unsigned)e >= (unsigned)G.C) {
-                    bad_elem = true;
-                } else if (e == c) {
-                    const float ax = __ldg(A.in.coords + 3 * ai);
-                    ay = __ldg(A.in.coords + 3 * ai + 1);
-                    az = __ldg(A.in.coords + 3 * ai + 2);
-                    dx = vx - ax;
-                    if (PER) dx = wrap(dx, Lx, iLx);
-                    ok = (CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc);
-                }
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, ok);
-            if (ok) {
-                const int pos = count + __popc(m & lt_mask);
-                if (pos < kStageCap) stage[pos] = make_float4(dx, ay, az, 0.0f);
-            }
-            count += __popc(m);
-        }
-        if (__any_sync(0xffffffffu, bad_elem) && report) atomicOr(A.err, PG_DEVERR_ELEMENT);
-        __syncwarp();
-
-        // 2./3. Row groups of 32 lanes x VEC voxels.
-        int y = y_start, z0 = z_start;
-        for (int g = 0; g < nvec; g += 32) {
-            const int v = g + lane;
-            LaneVoxels<VEC, CUT, PER> lv;
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) lv.acc[k] = 0.0f;
-            if (count > 0) {
-                const int last = min(31, nvec - 1 - g);
-                const int y_lo = __shfl_sync(0xffffffffu, y, 0);
-                const int y_hi = __shfl_sync(0xffffffffu, y, last);
-                int z_lo = 0, z_hi = G.nz - 1;
-                if (y_lo == y_hi) {
-                    z_lo = __shfl_sync(0xffffffffu, z0, 0);
-                    z_hi = __shfl_sync(0xffffffffu, z0, last) + VEC - 1;
-                }
-                const float cy = fmaf(0.5f * (float)(y_lo + y_hi) + 0.5f, hy, oy);
-                const float wy = 0.5f * (float)(y_hi - y_lo) * hy;
-                const float cz = fmaf(0.5f * (float)(z_lo + z_hi) + 0.5f, hz, oz);
-                const float wz = 0.5f * (float)(z_hi - z_lo) * hz;
-                lv.vy = fmaf((float)y + 0.5f, hy, oy);
-#pragma unroll
-                for (int k = 0; k < VEC; ++k) lv.vz[k] = fmaf((float)(z0 + k) + 0.5f, hz, oz);
-
-                if (count <= kStageCap) {
-                    for (int cb = 0; cb < count; cb += 32) {
-                        const int j = cb + lane;
-                        bool ok = false;
-                        if (j < count) {
-                            const float4 s = stage[j];
-                            ok = reaches<CUT, PER>(s.x, s.y, s.z, cy, wy, cz, wz, rc, Ly, iLy,
-                                                   Lz, iLz);
-                        }
-                        unsigned m = __ballot_sync(0xffffffffu, ok);
-                        while (m) {
-                            const int src = __ffs(m) - 1;
-                            m &= m - 1;
-                            const float4 s = stage[cb + src];
-                            lv.add(s.x, s.y, s.z, q, r2, Ly, iLy, Lz, iLz);
-                        }
+        if (small) {
+            // Candidates of this plane: the lane's own atom if it has channel c and lies
+            // within the cutoff of the plane in x.
+            float dx = vx - my_x;
+            if (PER) dx = wrap(dx, Lx, iLx);
+            const bool cand = (my_e == c) && ((CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc));
+            const unsigned cmask = __ballot_sync(0xffffffffu, cand);
+            if (cmask == 0u) {
+                zero_plane<T, VEC, HINT>(out, nvec, lane);
+            } else {
+                int y = y_start, z0 = z_start;
+                for (int g = 0; g < nvec; g += 32) {
+                    const int last = min(31, nvec - 1 - g);
+                    const int y_lo = __shfl_sync(0xffffffffu, y, 0);
+                    const int y_hi = __shfl_sync(0xffffffffu, y, last);
+                    int z_lo = 0, z_hi = G.nz - 1;
+                    if (y_lo == y_hi) {
+                        z_lo = __shfl_sync(0xffffffffu, z0, 0);
+                        z_hi = __shfl_sync(0xffffffffu, z0, last) + VEC - 1;
                     }
-                } else {
-                    // Unstaged fallback: the same atoms in the same order, read from global.
-                    for (int base = a0; base < a1; base += 32) {
-                        const int ai = base + lane;
-                        bool ok = false;
-                        float dx = 0.0f, ay = 0.0f, az = 0.0f;
-                        if (ai < a1 && __ldg(A.in.elem + ai) == c) {
-                            const float ax = __ldg(A.in.coords + 3 * ai);
-                            ay = __ldg(A.in.coords + 3 * ai + 1);
-                            az = __ldg(A.in.coords + 3 * ai + 2);
-                            dx = vx - ax;
-                            if (PER) dx = wrap(dx, Lx, iLx);
-                            ok = ((CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc)) &&
-                                 reaches<CUT, PER>(dx, ay, az, cy, wy, cz, wz, rc, Ly, iLy, Lz,
-                                                   iLz);
-                        }
-                        unsigned m = __ballot_sync(0xffffffffu, ok);
+                    const float cy = fmaf(0.5f * (float)(y_lo + y_hi) + 0.5f, hy, oy);
+                    const float wy = 0.5f * (float)(y_hi - y_lo) * hy;
+                    const float cz = fmaf(0.5f * (float)(z_lo + z_hi) + 0.5f, hz, oz);
+                    const float wz = 0.5f * (float)(z_hi - z_lo) * hz;
+                    const bool hit = cand && reaches<CUT, PER>(dx, my_y, my_z, cy, wy, cz, wz,
+                                                               rc, Ly, iLy, Lz, iLz);
+                    unsigned m = __ballot_sync(0xffffffffu, hit);
+                    LaneVoxels<VEC, CUT, PER> lv;
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) lv.acc[k] = 0.0f;
+                    if (m) {
+                        lv.vy = fmaf((float)y + 0.5f, hy, oy);
+#pragma unroll
+                        for (int k = 0; k < VEC; ++k)
+                            lv.vz[k] = fmaf((float)(z0 + k) + 0.5f, hz, oz);
                         while (m) {
                             const int src = __ffs(m) - 1;
                             m &= m - 1;
                             const float sdx = __shfl_sync(0xffffffffu, dx, src);
-                            const float sy = __shfl_sync(0xffffffffu, ay, src);
-                            const float sz = __shfl_sync(0xffffffffu, az, src);
+                            const float sy = __shfl_sync(0xffffffffu, my_y, src);
+                            const float sz = __shfl_sync(0xffffffffu, my_z, src);
                             lv.add(sdx, sy, sz, q, r2, Ly, iLy, Lz, iLz);
                         }
                     }
+                    if (g + lane < nvec) store_lane<T, VEC, HINT>(out, g + lane, lv.acc);
+                    y += y_step;
+                    z0 += z_step;
+                    if (z0 >= G.nz) {
+                        z0 -= G.nz;
+                        ++y;
+                    }
                 }
             }
-            if (v < nvec) {
-                if constexpr (VEC * sizeof(T) == 16) {
-                    store16<HINT>(out + (long long)v * VEC, pack16<T, VEC>(lv.acc));
-                } else {
-                    out[v] = from_float<T>(lv.acc[0]);
+        } else {
+            // Large molecule: cull and stage this channel's atoms near the plane, in order.
+            int count = 0;
+            for (int base = a0; base < a1; base += 32) {
+                const int ai = base + lane;
+                bool ok = false;
+                float dx = 0.0f, ay = 0.0f, az = 0.0f;
+                if (ai < a1) {
+                    const int e = __ldg(A.in.elem + ai);
+                    if ((unsigned)e >= (unsigned)G.C) {
+                        if (c == 0 && x == 0) atomicOr(A.err, PG_DEVERR_ELEMENT);
+                    } else if (e == c) {
+                        const float ax = __ldg(A.in.coords + 3 * ai);
+                        ay = __ldg(A.in.coords + 3 * ai + 1);
+                        az = __ldg(A.in.coords + 3 * ai + 2);
+                        dx = vx - ax;
+                        if (PER) dx = wrap(dx, Lx, iLx);
+                        ok = (CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc);
+                    }
+                }
+                const unsigned m = __ballot_sync(0xffffffffu, ok);
+                if (ok) {
+                    const int pos = count + __popc(m & lt_mask);
+                    if (pos < kStageCap) stage[pos] = make_float4(dx, ay, az, 0.0f);
+                }
+                count += __popc(m);
+            }
+            __syncwarp();
+            if (count == 0) {
+                zero_plane<T, VEC, HINT>(out, nvec, lane);
+            } else {
+                int y = y_start, z0 = z_start;
+                for (int g = 0; g < nvec; g += 32) {
+                    const int v = g + lane;
+                    LaneVoxels<VEC, CUT, PER> lv;
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) lv.acc[k] = 0.0f;
+                    const int last = min(31, nvec - 1 - g);
+                    const int y_lo = __shfl_sync(0xffffffffu, y, 0);
+                    const int y_hi = __shfl_sync(0xffffffffu, y, last);
+                    int z_lo = 0, z_hi = G.nz - 1;
+                    if (y_lo == y_hi) {
+                        z_lo = __shfl_sync(0xffffffffu, z0, 0);
+                        z_hi = __shfl_sync(0xffffffffu, z0, last) + VEC - 1;
+                    }
+                    const float cy = fmaf(0.5f * (float)(y_lo + y_hi) + 0.5f, hy, oy);
+                    const float wy = 0.5f * (float)(y_hi - y_lo) * hy;
+                    const float cz = fmaf(0.5f * (float)(z_lo + z_hi) + 0.5f, hz, oz);
+                    const float wz = 0.5f * (float)(z_hi - z_lo) * hz;
+                    lv.vy = fmaf((float)y + 0.5f, hy, oy);
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) lv.vz[k] = fmaf((float)(z0 + k) + 0.5f, hz, oz);
+
+                    if (count <= kStageCap) {
+                        for (int cb = 0; cb < count; cb += 32) {
+                            const int j = cb + lane;
+                            bool ok = false;
+                            if (j < count) {
+                                const float4 st = stage[j];
+                                ok = reaches<CUT, PER>(st.x, st.y, st.z, cy, wy, cz, wz, rc, Ly,
+                                                       iLy, Lz, iLz);
+                            }
+                            unsigned m = __ballot_sync(0xffffffffu, ok);
+                            while (m) {
+                                const int src = __ffs(m) - 1;
+                                m &= m - 1;
+                                const float4 st = stage[cb + src];
+                                lv.add(st.x, st.y, st.z, q, r2, Ly, iLy, Lz, iLz);
+                            }
+                        }
+                    } else {
+                        // Unstaged fallback: the same atoms in the same order, from global.
+                        for (int base = a0; base < a1; base += 32) {
+                            const int ai = base + lane;
+                            bool ok = false;
+                            float dx = 0.0f, ay = 0.0f, az = 0.0f;
+                            if (ai < a1 && __ldg(A.in.elem + ai) == c) {
+                                const float ax = __ldg(A.in.coords + 3 * ai);
+                                ay = __ldg(A.in.coords + 3 * ai + 1);
+                                az = __ldg(A.in.coords + 3 * ai + 2);
+                                dx = vx - ax;
+                                if (PER) dx = wrap(dx, Lx, iLx);
+                                ok = ((CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc)) &&
+                                     reaches<CUT, PER>(dx, ay, az, cy, wy, cz, wz, rc, Ly, iLy,
+                                                       Lz, iLz);
+                            }
+                            unsigned m = __ballot_sync(0xffffffffu, ok);
+                            while (m) {
+                                const int src = __ffs(m) - 1;
+                                m &= m - 1;
+                                const float sdx = __shfl_sync(0xffffffffu, dx, src);
+                                const float sy = __shfl_sync(0xffffffffu, ay, src);
+                                const float sz = __shfl_sync(0xffffffffu, az, src);
+                                lv.add(sdx, sy, sz, q, r2, Ly, iLy, Lz, iLz);
+                            }
+                        }
+                    }
+                    if (v < nvec) store_lane<T, VEC, HINT>(out, v, lv.acc);
+                    y += y_step;
+                    z0 += z_step;
+                    if (z0 >= G.nz) {
+                        z0 -= G.nz;
+                        ++y;
+                    }
                 }
             }
-            y += y_step;
-            z0 += z_step;
-            if (z0 >= G.nz) {
-                z0 -= G.nz;
-                ++y;
+            __syncwarp();
+        }
+
+        // Next plane: x, then channel, then molecule.
+        if (++x == G.nx) {
+            x = 0;
+            if (++c == G.C) {
+                c = 0;
+                ++b;
             }
         }
-        __syncwarp();
     }
 }
 

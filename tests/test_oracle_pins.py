@@ -253,11 +253,20 @@ def test_brute_force_equals_support_box_bitwise(oracle_lib, cutoff, periodic):
                                rtol=1e-12, atol=1e-14)
 
 
-def test_band_split_sums_to_grid(oracle_lib):
+def test_band_split_brackets_the_grid(oracle_lib):
     wl = synth.plain_small(n_mol=3)
     p = oracle.Problem.from_workload(wl)
+    G = oracle.voxelize(p)
     g_in, g_band = oracle.voxelize_band(p, 1e-5)
-    np.testing.assert_allclose(g_in + g_band, oracle.voxelize(p), rtol=1e-14, atol=1e-16)
+    assert np.all(g_in <= G + 1e-15) and np.all(G <= g_in + g_band + 1e-15)
+    # Lattice-point case: sigma = 0.5, r = 1.5 = 3 voxels exactly.  The 30 voxels with
+    # p^2 + q^2 + s^2 = 9 (6 axial, 24 of type (2,2,1)) sit exactly on the cutoff surface:
+    # all of them land in the band and none counts as strictly inside.
+    x = [[8.25, 8.25, 8.25]]
+    p2 = make(x, [0], (33, 33, 33), 1, 0.5, cutoff="sphere")
+    gi, gb = oracle.voxelize_band(p2, 1e-9)
+    assert int((gb > 0).sum()) == 30
+    assert np.all(gi[gb > 0] == 0.0)
 
 
 def test_invalid_element_is_rejected(oracle_lib):
