@@ -51,7 +51,7 @@ typedef enum {
     PG_ERR_UNSUPPORTED = 2,       /* valid but not implemented (e.g. separable + sphere) */
     PG_ERR_CUDA = 3,              /* a CUDA runtime call failed; message has the detail */
     PG_ERR_DEVICE_VALIDATION = 4, /* the device error word was set (see pg_sync_status) */
-    PG_ERR_TIMEOUT = 5            /* reserved: a bounded device wait gave up */
+    PG_ERR_TIMEOUT = 5            /* a bounded device wait gave up (PG_DEVERR_TIMEOUT) */
 } pg_status;
 
 typedef enum { PG_F32 = 0, PG_F16 = 1, PG_BF16 = 2 } pg_dtype;
@@ -69,6 +69,7 @@ typedef enum {
 #define PG_DEVERR_OFFSETS 0x2u   /* mol_off not monotone, negative, or > n_atoms */
 #define PG_DEVERR_SPACING 0x4u   /* spacing <= 0 or not finite */
 #define PG_DEVERR_PERIODIC 0x8u  /* periodic cell with r_c >= L/2 on some axis */
+#define PG_DEVERR_TIMEOUT 0x10u  /* a bounded wait on tensor-core completion gave up */
 
 /*
  * A batch of B molecules in CSR form (Sec. V: points carry (channel, x, y, z); Sec. III-A:

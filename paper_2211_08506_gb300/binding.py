@@ -27,6 +27,7 @@ PG_DEVERR_ELEMENT = 0x1
 PG_DEVERR_OFFSETS = 0x2
 PG_DEVERR_SPACING = 0x4
 PG_DEVERR_PERIODIC = 0x8
+PG_DEVERR_TIMEOUT = 0x10
 
 EXPORTED = (
     "pg_version", "pg_last_error", "pg_status_string", "pg_voxelize", "pg_voxelize_tuned",

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdint>
@@ -53,8 +54,16 @@ pg_status cuda_fail(cudaError_t e, const char *what)
 struct Device {
     int id = -1;
     int sms = 0;
-    unsigned *err = nullptr;  // device error word (PG_DEVERR_* bits)
+    unsigned *err = nullptr;                // device error word (PG_DEVERR_* bits)
+    unsigned long long *sched = nullptr;    // kSchedSlots work counters, 4 words apart
+    std::atomic<unsigned> *next_slot = nullptr;
     std::string name;
+
+    unsigned long long *take_slot()
+    {
+        const unsigned i = next_slot->fetch_add(1u, std::memory_order_relaxed) % kSchedSlots;
+        return sched + 4 * (size_t)i;
+    }
 };
 
 std::mutex g_mu;
@@ -78,6 +87,10 @@ pg_status get_device(Device **out)
             if (ch == ' ') ch = '_';
         PG_CUDA(cudaMalloc(&d.err, sizeof(unsigned)), "cudaMalloc(error word)");
         PG_CUDA(cudaMemset(d.err, 0, sizeof(unsigned)), "cudaMemset(error word)");
+        const size_t sched_bytes = sizeof(unsigned long long) * 4 * kSchedSlots;
+        PG_CUDA(cudaMalloc(&d.sched, sched_bytes), "cudaMalloc(work counters)");
+        PG_CUDA(cudaMemset(d.sched, 0, sched_bytes), "cudaMemset(work counters)");
+        d.next_slot = new std::atomic<unsigned>(0u);
         PG_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize(setup)");
         it = g_devices.emplace(id, d).first;
     }
@@ -183,7 +196,8 @@ bool vec_stores_ok(const void *out, const pg_grid *g, int dtype)
 
 // Resolve one forward launch without issuing it.
 pg_status plan_forward(const pg_batch *b, const pg_grid *g, int dtype, void *out,
-                       const pg_tuning &t, const Device &d, unsigned *err, KernelLaunch *kl)
+                       const pg_tuning &t, const Device &d, unsigned *err,
+                       unsigned long long *sched, KernelLaunch *kl)
 {
     Geometry G;
     make_geometry(b, g, &G);
@@ -212,6 +226,7 @@ pg_status plan_forward(const pg_batch *b, const pg_grid *g, int dtype, void *out
     a.in = make_inputs(b);
     a.out = out;
     a.err = err;
+    a.sched = sched;
     a.geo = G;
     cudaError_t e = direct_plan(a, dtype, vec_stores_ok(out, g, dtype) ? 1 : 0, t, d.sms, kl);
     if (e != cudaSuccess) return cuda_fail(e, "direct_plan");
@@ -233,7 +248,7 @@ pg_status forward(const pg_batch *b, const pg_grid *g, int dtype, void *out, con
     if ((st = get_device(&d))) return st;
     if (b->n_mol == 0) return PG_OK;
     KernelLaunch kl;
-    if ((st = plan_forward(b, g, dtype, out, t, *d, d->err, &kl))) return st;
+    if ((st = plan_forward(b, g, dtype, out, t, *d, d->err, d->take_slot(), &kl))) return st;
     PG_CUDA(launch(kl, s), "voxelize launch");
     return PG_OK;
 }
@@ -289,6 +304,7 @@ struct pg_plan {
     float *d_origin = nullptr;
     float *d_spacing = nullptr;
     unsigned *d_err = nullptr;
+    unsigned long long *d_sched = nullptr;
     unsigned char *h_stage = nullptr;
     size_t stage_off[5] = {0, 0, 0, 0, 0};
     unsigned *h_err = nullptr;
@@ -310,6 +326,7 @@ void plan_free(pg_plan *p)
     cudaFree(p->d_origin);
     cudaFree(p->d_spacing);
     cudaFree(p->d_err);
+    cudaFree(p->d_sched);
     if (p->h_stage) cudaFreeHost(p->h_stage);
     if (p->h_err) cudaFreeHost(p->h_err);
     delete p;
@@ -390,12 +407,13 @@ pg_status plan_update_graph(pg_plan *p, const void *const src[5], const size_t b
 pg_status report_bits(unsigned bits)
 {
     if (!bits) return PG_OK;
-    return fail(PG_ERR_DEVICE_VALIDATION,
-                "device validation failed (bits 0x%x:%s%s%s%s)", bits,
+    return fail((bits & PG_DEVERR_TIMEOUT) ? PG_ERR_TIMEOUT : PG_ERR_DEVICE_VALIDATION,
+                "device validation failed (bits 0x%x:%s%s%s%s%s)", bits,
                 (bits & PG_DEVERR_ELEMENT) ? " element id outside [0, C)" : "",
                 (bits & PG_DEVERR_OFFSETS) ? " bad CSR offsets" : "",
                 (bits & PG_DEVERR_SPACING) ? " non-positive spacing" : "",
-                (bits & PG_DEVERR_PERIODIC) ? " periodic cutoff >= half a cell edge" : "");
+                (bits & PG_DEVERR_PERIODIC) ? " periodic cutoff >= half a cell edge" : "",
+                (bits & PG_DEVERR_TIMEOUT) ? " tensor-core wait timed out" : "");
 }
 
 }  // namespace
@@ -582,7 +600,8 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
     int ref_index = -1;
     for (size_t i = 0; i < cands.size(); ++i) {
         KernelLaunch kl;
-        if (plan_forward(batch, grid, out_dtype, out, cands[i], *d, d->err, &kl) != PG_OK) {
+        if (plan_forward(batch, grid, out_dtype, out, cands[i], *d, d->err, d->take_slot(),
+                         &kl) != PG_OK) {
             t_last_error.clear();
             continue;
         }
@@ -745,6 +764,11 @@ pg_status pg_plan_create(pg_plan **plan, const pg_grid *grid, int32_t out_dtype,
     if ((e = cudaMalloc(&p->d_origin, sizes[3])) != cudaSuccess) return bad(e, "cudaMalloc");
     if ((e = cudaMalloc(&p->d_spacing, sizes[4])) != cudaSuccess) return bad(e, "cudaMalloc");
     if ((e = cudaMalloc(&p->d_err, sizeof(unsigned))) != cudaSuccess) return bad(e, "cudaMalloc");
+    if ((e = cudaMalloc(&p->d_sched, 4 * sizeof(unsigned long long))) != cudaSuccess)
+        return bad(e, "cudaMalloc");
+    if ((e = cudaMemset(p->d_sched, 0, 4 * sizeof(unsigned long long))) != cudaSuccess)
+        return bad(e, "cudaMemset");
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return bad(e, "cudaDeviceSynchronize");
     if ((e = cudaHostAlloc((void **)&p->h_stage, total, cudaHostAllocDefault)) != cudaSuccess)
         return bad(e, "cudaHostAlloc");
     if ((e = cudaHostAlloc((void **)&p->h_err, sizeof(unsigned), cudaHostAllocDefault)) !=
@@ -804,7 +828,8 @@ pg_status pg_plan_run(pg_plan *p, const pg_batch *hb, void *out, void *stream)
     db.origin = p->d_origin;
     db.spacing = p->d_spacing;
     KernelLaunch kl;
-    if ((st = plan_forward(&db, &p->grid, p->dtype, out, p->tuning, *d, p->d_err, &kl)))
+    if ((st = plan_forward(&db, &p->grid, p->dtype, out, p->tuning, *d, p->d_err, p->d_sched,
+                           &kl)))
         return st;
     if ((st = plan_update_graph(p, src, cnt, dst, kl))) return st;
     cudaStream_t s = (cudaStream_t)stream;
@@ -830,6 +855,8 @@ void pg_shutdown(void)
             cudaSetDevice(kv.first);
             cudaDeviceSynchronize();
             cudaFree(kv.second.err);
+            cudaFree(kv.second.sched);
+            delete kv.second.next_slot;
         }
         g_devices.clear();
         if (cur >= 0) cudaSetDevice(cur);

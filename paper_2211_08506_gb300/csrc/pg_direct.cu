@@ -6,8 +6,8 @@
 // Work decomposition.  The output is a dense [B][C][nx][ny][nz] array and, with ~1% of
 // voxels non-zero, writing it is the whole cost: the kernel is a write-bandwidth-bound
 // fill with sparse splats.  One work item is one contiguous (y, z) plane of one
-// (molecule b, channel c, x index) triple; item index == plane index, so consecutive items
-// are consecutive memory.  Persistent warps walk the items with a fixed stride.
+// (molecule b, channel c, x index) triple.  Persistent warps take whole (b, c) grids (nx
+// consecutive planes) from a per-launch atomic counter, so uneven molecules balance out.
 //
 // Per item, one warp
 //   1. culls the molecule's atoms 32 at a time with a warp ballot: an atom survives if it
@@ -182,25 +182,19 @@ __global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
     float4 *stage = stage_all + warp * kStageCap;
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    // Each warp owns a contiguous range of items (planes), so consecutive items share the
-    // molecule and, for molecules of at most 32 atoms, the atoms stay in registers.
-    const long long n_items = (long long)G.n_mol * G.C * G.nx;
-    const long long n_warps = (long long)gridDim.x * warps_per_block;
-    const long long gw = (long long)blockIdx.x * warps_per_block + warp;
-    long long item = n_items * gw / n_warps;
-    const long long item_end = n_items * (gw + 1) / n_warps;
-    if (item >= item_end) return;
+    // Work is handed out dynamically in chunks of one (molecule, channel) grid = nx planes:
+    // lane 0 takes the next chunk index from a per-launch counter.  The molecule's header
+    // and, for molecules of at most 32 atoms, the atoms themselves stay in registers across
+    // the chunk's planes.  The last warp to finish resets the counter for the next launch.
+    const unsigned long long n_chunks = (unsigned long long)G.n_mol * G.C;
+    const unsigned long long total_warps = (unsigned long long)gridDim.x * warps_per_block;
 
     const int plane = G.ny * G.nz;
     const int nvec = plane / VEC;
     const int y_start = (lane * VEC) / G.nz, z_start = (lane * VEC) % G.nz;
     const int y_step = (32 * VEC) / G.nz, z_step = (32 * VEC) % G.nz;
 
-    int x = (int)(item % G.nx);
-    int c = (int)((item / G.nx) % G.C);
-    int b = (int)(item / ((long long)G.nx * G.C));
     int cur_b = -1;
-
     int a0 = 0, a1 = 0;
     float ox = 0.f, oy = 0.f, oz = 0.f, hx = 1.f, hy = 1.f, hz = 1.f;
     float Lx = 1.f, Ly = 1.f, Lz = 1.f, iLx = 1.f, iLy = 1.f, iLz = 1.f;
@@ -209,8 +203,13 @@ __global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
     float my_x = 0.f, my_y = 0.f, my_z = 0.f;
     int my_e = -1;
 
-    for (; item < item_end; ++item) {
-        T *out = reinterpret_cast<T *>(A.out) + item * (long long)plane;
+    while (true) {
+        unsigned long long chunk = 0;
+        if (lane == 0) chunk = atomicAdd(A.sched, 1ull);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        if (chunk >= n_chunks) break;
+        const int b = (int)(chunk / (unsigned)G.C);
+        const int c = (int)(chunk - (unsigned long long)b * G.C);
         if (b != cur_b) {
             cur_b = b;
             a0 = __ldg(A.in.mol_off + b);
@@ -252,182 +251,189 @@ __global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
             }
             if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(A.err, PG_DEVERR_ELEMENT);
         }
+        for (int x = 0; x < G.nx; ++x) {
+            const long long item = (long long)chunk * G.nx + x;
+            T *out = reinterpret_cast<T *>(A.out) + item * (long long)plane;
+            const float q = G.q[c], r2 = G.r2[c], rc = G.rcull[c];
+            if (PER && CUT != PG_CUTOFF_NONE && lane == 0 && x == 0 && a1 > a0 &&
+                (2.0f * rc >= fminf(Lx, fminf(Ly, Lz))))
+                atomicOr(A.err, PG_DEVERR_PERIODIC);
+            const float vx = fmaf((float)x + 0.5f, hx, ox);
 
-        const float q = G.q[c], r2 = G.r2[c], rc = G.rcull[c];
-        if (PER && CUT != PG_CUTOFF_NONE && lane == 0 && x == 0 && a1 > a0 &&
-            (2.0f * rc >= fminf(Lx, fminf(Ly, Lz))))
-            atomicOr(A.err, PG_DEVERR_PERIODIC);
-        const float vx = fmaf((float)x + 0.5f, hx, ox);
-
-        if (small) {
-            // Candidates of this plane: the lane's own atom if it has channel c and lies
-            // within the cutoff of the plane in x.
-            float dx = vx - my_x;
-            if (PER) dx = wrap(dx, Lx, iLx);
-            const bool cand = (my_e == c) && ((CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc));
-            const unsigned cmask = __ballot_sync(0xffffffffu, cand);
-            if (cmask == 0u) {
-                zero_plane<T, VEC, HINT>(out, nvec, lane);
-            } else {
-                int y = y_start, z0 = z_start;
-                for (int g = 0; g < nvec; g += 32) {
-                    const int last = min(31, nvec - 1 - g);
-                    const int y_lo = __shfl_sync(0xffffffffu, y, 0);
-                    const int y_hi = __shfl_sync(0xffffffffu, y, last);
-                    int z_lo = 0, z_hi = G.nz - 1;
-                    if (y_lo == y_hi) {
-                        z_lo = __shfl_sync(0xffffffffu, z0, 0);
-                        z_hi = __shfl_sync(0xffffffffu, z0, last) + VEC - 1;
-                    }
-                    const float cy = fmaf(0.5f * (float)(y_lo + y_hi) + 0.5f, hy, oy);
-                    const float wy = 0.5f * (float)(y_hi - y_lo) * hy;
-                    const float cz = fmaf(0.5f * (float)(z_lo + z_hi) + 0.5f, hz, oz);
-                    const float wz = 0.5f * (float)(z_hi - z_lo) * hz;
-                    const bool hit = cand && reaches<CUT, PER>(dx, my_y, my_z, cy, wy, cz, wz,
-                                                               rc, Ly, iLy, Lz, iLz);
-                    unsigned m = __ballot_sync(0xffffffffu, hit);
-                    LaneVoxels<VEC, CUT, PER> lv;
-#pragma unroll
-                    for (int k = 0; k < VEC; ++k) lv.acc[k] = 0.0f;
-                    if (m) {
-                        lv.vy = fmaf((float)y + 0.5f, hy, oy);
-#pragma unroll
-                        for (int k = 0; k < VEC; ++k)
-                            lv.vz[k] = fmaf((float)(z0 + k) + 0.5f, hz, oz);
-                        while (m) {
-                            const int src = __ffs(m) - 1;
-                            m &= m - 1;
-                            const float sdx = __shfl_sync(0xffffffffu, dx, src);
-                            const float sy = __shfl_sync(0xffffffffu, my_y, src);
-                            const float sz = __shfl_sync(0xffffffffu, my_z, src);
-                            lv.add(sdx, sy, sz, q, r2, Ly, iLy, Lz, iLz);
+            if (small) {
+                // Candidates of this plane: the lane's own atom if it has channel c and lies
+                // within the cutoff of the plane in x.
+                float dx = vx - my_x;
+                if (PER) dx = wrap(dx, Lx, iLx);
+                const bool cand = (my_e == c) && ((CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc));
+                const unsigned cmask = __ballot_sync(0xffffffffu, cand);
+                if (cmask == 0u) {
+                    zero_plane<T, VEC, HINT>(out, nvec, lane);
+                } else {
+                    int y = y_start, z0 = z_start;
+                    for (int g = 0; g < nvec; g += 32) {
+                        const int last = min(31, nvec - 1 - g);
+                        const int y_lo = __shfl_sync(0xffffffffu, y, 0);
+                        const int y_hi = __shfl_sync(0xffffffffu, y, last);
+                        int z_lo = 0, z_hi = G.nz - 1;
+                        if (y_lo == y_hi) {
+                            z_lo = __shfl_sync(0xffffffffu, z0, 0);
+                            z_hi = __shfl_sync(0xffffffffu, z0, last) + VEC - 1;
                         }
-                    }
-                    if (g + lane < nvec) store_lane<T, VEC, HINT>(out, g + lane, lv.acc);
-                    y += y_step;
-                    z0 += z_step;
-                    if (z0 >= G.nz) {
-                        z0 -= G.nz;
-                        ++y;
-                    }
-                }
-            }
-        } else {
-            // Large molecule: cull and stage this channel's atoms near the plane, in order.
-            int count = 0;
-            for (int base = a0; base < a1; base += 32) {
-                const int ai = base + lane;
-                bool ok = false;
-                float dx = 0.0f, ay = 0.0f, az = 0.0f;
-                if (ai < a1) {
-                    const int e = __ldg(A.in.elem + ai);
-                    if ((unsigned)e >= (unsigned)G.C) {
-                        if (c == 0 && x == 0) atomicOr(A.err, PG_DEVERR_ELEMENT);
-                    } else if (e == c) {
-                        const float ax = __ldg(A.in.coords + 3 * ai);
-                        ay = __ldg(A.in.coords + 3 * ai + 1);
-                        az = __ldg(A.in.coords + 3 * ai + 2);
-                        dx = vx - ax;
-                        if (PER) dx = wrap(dx, Lx, iLx);
-                        ok = (CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc);
-                    }
-                }
-                const unsigned m = __ballot_sync(0xffffffffu, ok);
-                if (ok) {
-                    const int pos = count + __popc(m & lt_mask);
-                    if (pos < kStageCap) stage[pos] = make_float4(dx, ay, az, 0.0f);
-                }
-                count += __popc(m);
-            }
-            __syncwarp();
-            if (count == 0) {
-                zero_plane<T, VEC, HINT>(out, nvec, lane);
-            } else {
-                int y = y_start, z0 = z_start;
-                for (int g = 0; g < nvec; g += 32) {
-                    const int v = g + lane;
-                    LaneVoxels<VEC, CUT, PER> lv;
-#pragma unroll
-                    for (int k = 0; k < VEC; ++k) lv.acc[k] = 0.0f;
-                    const int last = min(31, nvec - 1 - g);
-                    const int y_lo = __shfl_sync(0xffffffffu, y, 0);
-                    const int y_hi = __shfl_sync(0xffffffffu, y, last);
-                    int z_lo = 0, z_hi = G.nz - 1;
-                    if (y_lo == y_hi) {
-                        z_lo = __shfl_sync(0xffffffffu, z0, 0);
-                        z_hi = __shfl_sync(0xffffffffu, z0, last) + VEC - 1;
-                    }
-                    const float cy = fmaf(0.5f * (float)(y_lo + y_hi) + 0.5f, hy, oy);
-                    const float wy = 0.5f * (float)(y_hi - y_lo) * hy;
-                    const float cz = fmaf(0.5f * (float)(z_lo + z_hi) + 0.5f, hz, oz);
-                    const float wz = 0.5f * (float)(z_hi - z_lo) * hz;
-                    lv.vy = fmaf((float)y + 0.5f, hy, oy);
-#pragma unroll
-                    for (int k = 0; k < VEC; ++k) lv.vz[k] = fmaf((float)(z0 + k) + 0.5f, hz, oz);
-
-                    if (count <= kStageCap) {
-                        for (int cb = 0; cb < count; cb += 32) {
-                            const int j = cb + lane;
-                            bool ok = false;
-                            if (j < count) {
-                                const float4 st = stage[j];
-                                ok = reaches<CUT, PER>(st.x, st.y, st.z, cy, wy, cz, wz, rc, Ly,
-                                                       iLy, Lz, iLz);
-                            }
-                            unsigned m = __ballot_sync(0xffffffffu, ok);
-                            while (m) {
-                                const int src = __ffs(m) - 1;
-                                m &= m - 1;
-                                const float4 st = stage[cb + src];
-                                lv.add(st.x, st.y, st.z, q, r2, Ly, iLy, Lz, iLz);
-                            }
-                        }
-                    } else {
-                        // Unstaged fallback: the same atoms in the same order, from global.
-                        for (int base = a0; base < a1; base += 32) {
-                            const int ai = base + lane;
-                            bool ok = false;
-                            float dx = 0.0f, ay = 0.0f, az = 0.0f;
-                            if (ai < a1 && __ldg(A.in.elem + ai) == c) {
-                                const float ax = __ldg(A.in.coords + 3 * ai);
-                                ay = __ldg(A.in.coords + 3 * ai + 1);
-                                az = __ldg(A.in.coords + 3 * ai + 2);
-                                dx = vx - ax;
-                                if (PER) dx = wrap(dx, Lx, iLx);
-                                ok = ((CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc)) &&
-                                     reaches<CUT, PER>(dx, ay, az, cy, wy, cz, wz, rc, Ly, iLy,
-                                                       Lz, iLz);
-                            }
-                            unsigned m = __ballot_sync(0xffffffffu, ok);
+                        const float cy = fmaf(0.5f * (float)(y_lo + y_hi) + 0.5f, hy, oy);
+                        const float wy = 0.5f * (float)(y_hi - y_lo) * hy;
+                        const float cz = fmaf(0.5f * (float)(z_lo + z_hi) + 0.5f, hz, oz);
+                        const float wz = 0.5f * (float)(z_hi - z_lo) * hz;
+                        const bool hit = cand && reaches<CUT, PER>(dx, my_y, my_z, cy, wy, cz, wz,
+                                                                   rc, Ly, iLy, Lz, iLz);
+                        unsigned m = __ballot_sync(0xffffffffu, hit);
+                        LaneVoxels<VEC, CUT, PER> lv;
+    #pragma unroll
+                        for (int k = 0; k < VEC; ++k) lv.acc[k] = 0.0f;
+                        if (m) {
+                            lv.vy = fmaf((float)y + 0.5f, hy, oy);
+    #pragma unroll
+                            for (int k = 0; k < VEC; ++k)
+                                lv.vz[k] = fmaf((float)(z0 + k) + 0.5f, hz, oz);
                             while (m) {
                                 const int src = __ffs(m) - 1;
                                 m &= m - 1;
                                 const float sdx = __shfl_sync(0xffffffffu, dx, src);
-                                const float sy = __shfl_sync(0xffffffffu, ay, src);
-                                const float sz = __shfl_sync(0xffffffffu, az, src);
+                                const float sy = __shfl_sync(0xffffffffu, my_y, src);
+                                const float sz = __shfl_sync(0xffffffffu, my_z, src);
                                 lv.add(sdx, sy, sz, q, r2, Ly, iLy, Lz, iLz);
                             }
                         }
-                    }
-                    if (v < nvec) store_lane<T, VEC, HINT>(out, v, lv.acc);
-                    y += y_step;
-                    z0 += z_step;
-                    if (z0 >= G.nz) {
-                        z0 -= G.nz;
-                        ++y;
+                        if (g + lane < nvec) store_lane<T, VEC, HINT>(out, g + lane, lv.acc);
+                        y += y_step;
+                        z0 += z_step;
+                        if (z0 >= G.nz) {
+                            z0 -= G.nz;
+                            ++y;
+                        }
                     }
                 }
-            }
-            __syncwarp();
-        }
+            } else {
+                // Large molecule: cull and stage this channel's atoms near the plane, in order.
+                int count = 0;
+                for (int base = a0; base < a1; base += 32) {
+                    const int ai = base + lane;
+                    bool ok = false;
+                    float dx = 0.0f, ay = 0.0f, az = 0.0f;
+                    if (ai < a1) {
+                        const int e = __ldg(A.in.elem + ai);
+                        if ((unsigned)e >= (unsigned)G.C) {
+                            if (c == 0 && x == 0) atomicOr(A.err, PG_DEVERR_ELEMENT);
+                        } else if (e == c) {
+                            const float ax = __ldg(A.in.coords + 3 * ai);
+                            ay = __ldg(A.in.coords + 3 * ai + 1);
+                            az = __ldg(A.in.coords + 3 * ai + 2);
+                            dx = vx - ax;
+                            if (PER) dx = wrap(dx, Lx, iLx);
+                            ok = (CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc);
+                        }
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, ok);
+                    if (ok) {
+                        const int pos = count + __popc(m & lt_mask);
+                        if (pos < kStageCap) stage[pos] = make_float4(dx, ay, az, 0.0f);
+                    }
+                    count += __popc(m);
+                }
+                __syncwarp();
+                if (count == 0) {
+                    zero_plane<T, VEC, HINT>(out, nvec, lane);
+                } else {
+                    int y = y_start, z0 = z_start;
+                    for (int g = 0; g < nvec; g += 32) {
+                        const int v = g + lane;
+                        LaneVoxels<VEC, CUT, PER> lv;
+    #pragma unroll
+                        for (int k = 0; k < VEC; ++k) lv.acc[k] = 0.0f;
+                        const int last = min(31, nvec - 1 - g);
+                        const int y_lo = __shfl_sync(0xffffffffu, y, 0);
+                        const int y_hi = __shfl_sync(0xffffffffu, y, last);
+                        int z_lo = 0, z_hi = G.nz - 1;
+                        if (y_lo == y_hi) {
+                            z_lo = __shfl_sync(0xffffffffu, z0, 0);
+                            z_hi = __shfl_sync(0xffffffffu, z0, last) + VEC - 1;
+                        }
+                        const float cy = fmaf(0.5f * (float)(y_lo + y_hi) + 0.5f, hy, oy);
+                        const float wy = 0.5f * (float)(y_hi - y_lo) * hy;
+                        const float cz = fmaf(0.5f * (float)(z_lo + z_hi) + 0.5f, hz, oz);
+                        const float wz = 0.5f * (float)(z_hi - z_lo) * hz;
+                        lv.vy = fmaf((float)y + 0.5f, hy, oy);
+    #pragma unroll
+                        for (int k = 0; k < VEC; ++k) lv.vz[k] = fmaf((float)(z0 + k) + 0.5f, hz, oz);
 
-        // Next plane: x, then channel, then molecule.
-        if (++x == G.nx) {
-            x = 0;
-            if (++c == G.C) {
-                c = 0;
-                ++b;
+                        if (count <= kStageCap) {
+                            for (int cb = 0; cb < count; cb += 32) {
+                                const int j = cb + lane;
+                                bool ok = false;
+                                if (j < count) {
+                                    const float4 st = stage[j];
+                                    ok = reaches<CUT, PER>(st.x, st.y, st.z, cy, wy, cz, wz, rc, Ly,
+                                                           iLy, Lz, iLz);
+                                }
+                                unsigned m = __ballot_sync(0xffffffffu, ok);
+                                while (m) {
+                                    const int src = __ffs(m) - 1;
+                                    m &= m - 1;
+                                    const float4 st = stage[cb + src];
+                                    lv.add(st.x, st.y, st.z, q, r2, Ly, iLy, Lz, iLz);
+                                }
+                            }
+                        } else {
+                            // Unstaged fallback: the same atoms in the same order, from global.
+                            for (int base = a0; base < a1; base += 32) {
+                                const int ai = base + lane;
+                                bool ok = false;
+                                float dx = 0.0f, ay = 0.0f, az = 0.0f;
+                                if (ai < a1 && __ldg(A.in.elem + ai) == c) {
+                                    const float ax = __ldg(A.in.coords + 3 * ai);
+                                    ay = __ldg(A.in.coords + 3 * ai + 1);
+                                    az = __ldg(A.in.coords + 3 * ai + 2);
+                                    dx = vx - ax;
+                                    if (PER) dx = wrap(dx, Lx, iLx);
+                                    ok = ((CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc)) &&
+                                         reaches<CUT, PER>(dx, ay, az, cy, wy, cz, wz, rc, Ly, iLy,
+                                                           Lz, iLz);
+                                }
+                                unsigned m = __ballot_sync(0xffffffffu, ok);
+                                while (m) {
+                                    const int src = __ffs(m) - 1;
+                                    m &= m - 1;
+                                    const float sdx = __shfl_sync(0xffffffffu, dx, src);
+                                    const float sy = __shfl_sync(0xffffffffu, ay, src);
+                                    const float sz = __shfl_sync(0xffffffffu, az, src);
+                                    lv.add(sdx, sy, sz, q, r2, Ly, iLy, Lz, iLz);
+                                }
+                            }
+                        }
+                        if (v < nvec) store_lane<T, VEC, HINT>(out, v, lv.acc);
+                        y += y_step;
+                        z0 += z_step;
+                        if (z0 >= G.nz) {
+                            z0 -= G.nz;
+                            ++y;
+                        }
+                    }
+                }
+                __syncwarp();
             }
+
+        }  // planes of the chunk
+    }
+
+    // Retire: the final failed grab above is ordered before this arrival, so when the last
+    // warp arrives no other warp touches the counter again and it can be reset.
+    if (lane == 0) {
+        __threadfence();
+        const unsigned long long done = atomicAdd(A.sched + 1, 1ull);
+        if (done == total_warps - 1) {
+            __threadfence();
+            atomicExch(A.sched, 0ull);
+            atomicExch(A.sched + 1, 0ull);
         }
     }
 }

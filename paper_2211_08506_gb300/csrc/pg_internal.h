@@ -39,8 +39,13 @@ struct DirectArgs {
     Inputs in;
     void *out;
     unsigned *err;
+    unsigned long long *sched;  // {next chunk, retired warps}; zero between launches
     Geometry geo;
 };
+
+// Work counters for dynamically scheduled kernels: a small pool per device, handed out
+// round-robin to launches so that launches in flight on different streams do not share one.
+constexpr int kSchedSlots = 64;
 
 struct BackwardArgs {
     Inputs in;

@@ -1,13 +1,565 @@
-// Separable tcgen05 contraction (sm_103a) - placeholder until the tensor-core kernel lands.
+// Separable tcgen05 contraction for batched Gaussian-density voxelization (sm_103a).
+//
+// With a per-axis cutoff (none, or the box |d_axis| <= r_c) the point-sampled Gaussian of
+// Sec. III-A factors per axis, which is the separability the paper exploits with per-axis
+// tables (Sec. III-A after Eq. 5; Sec. VI-A).  For one molecule the grid is then a matrix
+// product over atoms a:
+//
+//     G[(c,x), (y,z)] = sum_a A[(c,x), a] * B[a, (y,z)],
+//     A[(c,x), a] = [elem a == c] g_x(a, x),   B[a, (y,z)] = g_y(a, y) g_z(a, z),
+//     g_axis(a, i) = chi_axis(d) 2^(-q_c d^2),  d = voxel centre - atom (nearest image),
+//
+// M = C nx rows, N = ny nz columns (the output [C][nx][ny][nz] is this matrix, row-major),
+// K = the molecule's atoms.  The operands are generated in shared memory and never touch
+// HBM: A is rounded once from FP32 g_x, B once from the FP32 product g_y g_z (BF16, round
+// to nearest even); the tensor cores accumulate in FP32 in tensor memory.
+//
+// One CTA of 128 threads owns one 128-row M tile of one molecule at a time (persistent loop
+// over (molecule, M tile) items).  Thread t is accumulator row t (TMEM lane t).  Per item the
+// CTA builds per-axis tables and the A tile once, then for each N tile of n_tile columns:
+//   builds B (n_tile x 32 atoms, BF16) -> one thread issues two K=16 tcgen05.mma into a TMEM
+//   accumulator of n_tile FP32 columns and commits to an mbarrier -> every thread loads its
+//   row with tcgen05.ld, converts to the output type, writes it to a padded shared staging
+//   row and sends it to global memory with one cp.async.bulk (bulk-async store).
+// Molecules with more than 32 atoms loop over 32-atom K chunks, accumulating in TMEM.
+// Both operands use the K-major, no-swizzle canonical layout: 8-row x 16-byte core matrices,
+// 128 bytes apart along K (leading byte offset) and 512 bytes apart along M/N (stride byte
+// offset).
+//
+// Every mbarrier wait is bounded; on expiry the kernel sets PG_DEVERR_TIMEOUT, drains its
+// own bulk stores, frees its tensor memory and returns.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "pg_internal.h"
 
 namespace pgi {
 
-bool separable_supported(const Geometry &, int) { return false; }
+namespace {
 
-cudaError_t separable_plan(const SeparableArgs &, int, const pg_tuning &, int, KernelLaunch *)
+constexpr int kKC = 32;         // atoms per K chunk (two K=16 MMA steps)
+constexpr int kTab = 36;        // floats per table row: 32 atoms + 4 pad (conflict-free reads)
+constexpr int kRows = 128;      // M tile = CTA threads = TMEM lanes
+constexpr unsigned kWaitLimit = 1u << 24;
+
+struct SepLayout {
+    int bar, tmem, atoms, a, b, gy, gz, stage, stage_stride, total;
+};
+
+__host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline SepLayout sep_layout(int ny, int nz, int n_tile, int esz)
 {
-    return cudaErrorNotSupported;
+    SepLayout L;
+    int o = 0;
+    L.bar = o;
+    o += 8;
+    L.tmem = o;
+    o += 8;
+    o = align_up(o, 128);
+    L.atoms = o;
+    o += kKC * 2 * 16;
+    o = align_up(o, 1024);
+    L.a = o;
+    o += kRows * kKC * 2;
+    o = align_up(o, 1024);
+    L.b = o;
+    o += n_tile * kKC * 2;
+    o = align_up(o, 128);
+    L.gy = o;
+    o += ny * kTab * 4;
+    o = align_up(o, 128);
+    L.gz = o;
+    o += nz * kTab * 4;
+    o = align_up(o, 128);
+    L.stage = o;
+    L.stage_stride = n_tile * esz + 16;
+    o += kRows * L.stage_stride;
+    L.total = align_up(o, 128);
+    return L;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float wrap(float d, float L, float invL)
+{
+    return fmaf(-L, rintf(d * invL), d);
+}
+
+// ---- mbarrier, tcgen05 and bulk-copy wrappers (inline PTX) ----
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0u;
+}
+
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     dst_smem),
+                 "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_relinquish()
+{
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr),
+                 "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mma_bf16_f32(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                             uint32_t idesc, uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+        "[%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait()
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void *gdst, uint32_t ssrc, uint32_t bytes)
+{
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
+                 "r"(ssrc), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit()
+{
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_read_all()
+{
+    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all()
+{
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version of the tcgen05 family
+    return d;                // base offset 0, absolute LBO mode, layout type 0 (no swizzle)
+}
+
+// Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, both K-major, M = 128.
+__device__ __forceinline__ uint32_t instr_desc(int n)
+{
+    return (1u << 4)                        // D format: F32
+           | (1u << 7)                      // A format: BF16
+           | (1u << 10)                     // B format: BF16
+           | ((uint32_t)(n >> 3) << 17)     // N / 8
+           | ((uint32_t)(kRows >> 4) << 24);  // M / 16
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
+{
+    __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// Per-axis factor chi_axis(d) 2^(-q d^2).
+template <int CUT>
+__device__ __forceinline__ float axis_factor(float d, float q, float r2)
+{
+    const float d2 = d * d;
+    const float v = ex2_approx(-q * d2);
+    return (CUT == PG_CUTOFF_BOX && d2 > r2) ? 0.0f : v;
+}
+
+template <typename T>
+__device__ __forceinline__ void store_row_chunk(unsigned char *dst, const uint32_t (&r)[32]);
+
+template <>
+__device__ __forceinline__ void store_row_chunk<float>(unsigned char *dst, const uint32_t (&r)[32])
+{
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) d[i] = make_uint4(r[4 * i], r[4 * i + 1], r[4 * i + 2], r[4 * i + 3]);
+}
+
+template <>
+__device__ __forceinline__ void store_row_chunk<__half>(unsigned char *dst, const uint32_t (&r)[32])
+{
+    uint32_t p[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+        __half2 h = __floats2half2_rn(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+        p[i] = *reinterpret_cast<uint32_t *>(&h);
+    }
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d[i] = make_uint4(p[4 * i], p[4 * i + 1], p[4 * i + 2], p[4 * i + 3]);
+}
+
+template <>
+__device__ __forceinline__ void store_row_chunk<__nv_bfloat16>(unsigned char *dst,
+                                                               const uint32_t (&r)[32])
+{
+    uint32_t p[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+        p[i] = pack_bf16x2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+    uint4 *d = reinterpret_cast<uint4 *>(dst);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d[i] = make_uint4(p[4 * i], p[4 * i + 1], p[4 * i + 2], p[4 * i + 3]);
+}
+
+template <typename T, int CUT, bool PER>
+__global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const Geometry &G = A.geo;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int n_tile = A.n_tile;
+    const SepLayout L = sep_layout(G.ny, G.nz, n_tile, (int)sizeof(T));
+    float4 *atom_pos = reinterpret_cast<float4 *>(smem + L.atoms);  // {x, y, z, q}
+    float4 *atom_aux = atom_pos + kKC;                               // {r2, elem, -, -}
+    unsigned char *sa = smem + L.a;
+    unsigned char *sb = smem + L.b;
+    float *tgy = reinterpret_cast<float *>(smem + L.gy);
+    float *tgz = reinterpret_cast<float *>(smem + L.gz);
+    unsigned char *srow = smem + L.stage + tid * L.stage_stride;
+    const uint32_t bar = smem_u32(smem + L.bar);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L.tmem);
+
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(tmem_slot), (uint32_t)n_tile);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+    const uint32_t idesc = instr_desc(n_tile);
+    const uint32_t sa_addr = smem_u32(sa), sb_addr = smem_u32(sb);
+    uint32_t phase = 0;
+    bool timed_out = false;
+
+    const int M = G.C * G.nx;
+    const int N = G.ny * G.nz;
+    const int n_chunks = (N + n_tile - 1) / n_tile;
+    const long long n_items = (long long)G.n_mol * A.m_tiles;
+    T *out = reinterpret_cast<T *>(A.out);
+
+    for (long long item = blockIdx.x; item < n_items && !timed_out; item += gridDim.x) {
+        const int b = (int)(item / A.m_tiles);
+        const int m0 = (int)(item % A.m_tiles) * kRows;
+        int a0 = __ldg(A.in.mol_off + b), a1 = __ldg(A.in.mol_off + b + 1);
+        const float ox = __ldg(A.in.origin + 3 * b), oy = __ldg(A.in.origin + 3 * b + 1),
+                    oz = __ldg(A.in.origin + 3 * b + 2);
+        const float hx = __ldg(A.in.spacing + 3 * b), hy = __ldg(A.in.spacing + 3 * b + 1),
+                    hz = __ldg(A.in.spacing + 3 * b + 2);
+        const bool off_ok = (a0 >= 0) && (a0 <= a1) && (a1 <= G.n_atoms);
+        const bool sp_ok = (hx > 0.0f) && (hy > 0.0f) && (hz > 0.0f) && (hx < INFINITY) &&
+                           (hy < INFINITY) && (hz < INFINITY);
+        if (!off_ok || !sp_ok) {
+            if (tid == 0 && m0 == 0)
+                atomicOr(A.err, (off_ok ? 0u : PG_DEVERR_OFFSETS) | (sp_ok ? 0u : PG_DEVERR_SPACING));
+            a0 = a1 = 0;
+        }
+        const float Lx = G.nx * hx, Ly = G.ny * hy, Lz = G.nz * hz;
+        const float iLx = 1.0f / Lx, iLy = 1.0f / Ly, iLz = 1.0f / Lz;
+        const int n_atoms = a1 - a0;
+        const int n_kc = n_atoms > 0 ? (n_atoms + kKC - 1) / kKC : 1;
+        const int R = m0 + tid;
+        const bool row_ok = R < M;
+        const int row_c = row_ok ? R / G.nx : -2;
+        const int row_x = row_ok ? R - (R / G.nx) * G.nx : 0;
+        const float vx = fmaf((float)row_x + 0.5f, hx, ox);
+
+        for (int nc = 0; nc < n_chunks && !timed_out; ++nc) {
+            const int n0 = nc * n_tile;
+            for (int kc = 0; kc < n_kc && !timed_out; ++kc) {
+                if (n_kc > 1 || nc == 0) {
+                    // Atoms of this K chunk, their per-axis tables and the A tile.
+                    if (tid < kKC) {
+                        const int ai = a0 + kc * kKC + tid;
+                        float4 pos = make_float4(0.f, 0.f, 0.f, 0.f);
+                        float4 aux = make_float4(0.f, -1.f, 0.f, 0.f);
+                        if (ai < a1) {
+                            const int e = __ldg(A.in.elem + ai);
+                            if ((unsigned)e < (unsigned)G.C) {
+                                pos = make_float4(__ldg(A.in.coords + 3 * ai),
+                                                  __ldg(A.in.coords + 3 * ai + 1),
+                                                  __ldg(A.in.coords + 3 * ai + 2), G.q[e]);
+                                aux = make_float4(G.r2[e], (float)e, 0.f, 0.f);
+                            } else if (m0 == 0) {
+                                atomicOr(A.err, PG_DEVERR_ELEMENT);
+                            }
+                        }
+                        atom_pos[tid] = pos;
+                        atom_aux[tid] = aux;
+                    }
+                    __syncthreads();
+                    for (int i = tid; i < G.ny * kKC; i += kRows) {
+                        const int y = i / kKC, j = i - (i / kKC) * kKC;
+                        const float4 p = atom_pos[j];
+                        float v = 0.0f;
+                        if (atom_aux[j].y >= 0.0f) {
+                            float d = fmaf((float)y + 0.5f, hy, oy) - p.y;
+                            if (PER) d = wrap(d, Ly, iLy);
+                            v = axis_factor<CUT>(d, p.w, atom_aux[j].x);
+                        }
+                        tgy[y * kTab + j] = v;
+                    }
+                    for (int i = tid; i < G.nz * kKC; i += kRows) {
+                        const int z = i / kKC, j = i - (i / kKC) * kKC;
+                        const float4 p = atom_pos[j];
+                        float v = 0.0f;
+                        if (atom_aux[j].y >= 0.0f) {
+                            float d = fmaf((float)z + 0.5f, hz, oz) - p.z;
+                            if (PER) d = wrap(d, Lz, iLz);
+                            v = axis_factor<CUT>(d, p.w, atom_aux[j].x);
+                        }
+                        tgz[z * kTab + j] = v;
+                    }
+                    // A row `tid`: [elem a == c] g_x(a, x), 4 core-matrix chunks of 8 atoms.
+#pragma unroll
+                    for (int jg = 0; jg < kKC / 8; ++jg) {
+                        float v[8];
+#pragma unroll
+                        for (int t = 0; t < 8; ++t) {
+                            const int j = jg * 8 + t;
+                            const float4 p = atom_pos[j];
+                            const float4 aux = atom_aux[j];
+                            v[t] = 0.0f;
+                            if (row_ok && (int)aux.y == row_c) {
+                                float d = vx - p.x;
+                                if (PER) d = wrap(d, Lx, iLx);
+                                v[t] = axis_factor<CUT>(d, p.w, aux.x);
+                            }
+                        }
+                        const uint4 w = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                                                   pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+                        *reinterpret_cast<uint4 *>(sa + (tid >> 3) * 512 + jg * 128 +
+                                                   (tid & 7) * 16) = w;
+                    }
+                    __syncthreads();
+                }
+                // B tile: column n = n0 + nl of B is (y, z); 16-byte chunk qi holds atoms
+                // kg*8 .. kg*8+7 of column nl at byte qi*16 of the canonical layout.
+                for (int qi = tid; qi < n_tile * (kKC / 8); qi += kRows) {
+                    const int nl = (qi >> 5) * 8 + (qi & 7);
+                    const int kg = (qi >> 3) & 3;
+                    const int n = n0 + nl;
+                    uint4 w = make_uint4(0u, 0u, 0u, 0u);
+                    if (n < N) {
+                        const int y = n / G.nz, z = n - (n / G.nz) * G.nz;
+                        const float4 *gy4 = reinterpret_cast<const float4 *>(tgy + y * kTab + kg * 8);
+                        const float4 *gz4 = reinterpret_cast<const float4 *>(tgz + z * kTab + kg * 8);
+                        const float4 y0 = gy4[0], y1 = gy4[1], z0 = gz4[0], z1 = gz4[1];
+                        w = make_uint4(pack_bf16x2(y0.x * z0.x, y0.y * z0.y),
+                                       pack_bf16x2(y0.z * z0.z, y0.w * z0.w),
+                                       pack_bf16x2(y1.x * z1.x, y1.y * z1.y),
+                                       pack_bf16x2(y1.z * z1.z, y1.w * z1.w));
+                    }
+                    *reinterpret_cast<uint4 *>(sb + qi * 16) = w;
+                }
+                fence_proxy_async_smem();
+                tc_fence_before();
+                __syncthreads();
+                if (tid == 0) {
+                    tc_fence_after();
+#pragma unroll
+                    for (int s = 0; s < kKC / 16; ++s) {
+                        const uint64_t ad = smem_desc(sa_addr + s * 256, 128, 512);
+                        const uint64_t bd = smem_desc(sb_addr + s * 256, 128, 512);
+                        mma_bf16_f32(tmem, ad, bd, idesc, (kc > 0 || s > 0) ? 1u : 0u);
+                    }
+                    mma_commit(bar);
+                }
+                bool done = false;
+                for (unsigned it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(bar, phase);
+                phase ^= 1u;
+                timed_out = __syncthreads_or(!done) != 0;
+                tc_fence_after();
+            }
+            if (timed_out) break;
+            // Epilogue: TMEM row -> registers -> output type -> staging row -> bulk store.
+            bulk_wait_read_all();
+            for (int cb = 0; cb < n_tile; cb += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem_row + cb, r);
+                tmem_ld_wait();
+                store_row_chunk<T>(srow + cb * (int)sizeof(T), r);
+            }
+            tc_fence_before();
+            if (row_ok) {
+                fence_proxy_async_smem();
+                const int cols = min(n_tile, N - n0);
+                T *dst = out + ((long long)b * M + R) * (long long)N + n0;
+                bulk_store(dst, smem_u32(srow), (uint32_t)(cols * (int)sizeof(T)));
+                bulk_commit();
+            }
+        }
+    }
+    if (timed_out && tid == 0) atomicOr(A.err, PG_DEVERR_TIMEOUT);
+    bulk_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, (uint32_t)n_tile);
+    }
+}
+
+template <typename T, int CUT>
+const void *pick_per(int periodic)
+{
+    return periodic ? (const void *)separable_kernel<T, CUT, true>
+                    : (const void *)separable_kernel<T, CUT, false>;
+}
+
+template <typename T>
+const void *pick_cut(int cutoff, int periodic)
+{
+    return cutoff == PG_CUTOFF_BOX ? pick_per<T, PG_CUTOFF_BOX>(periodic)
+                                   : pick_per<T, PG_CUTOFF_NONE>(periodic);
+}
+
+}  // namespace
+
+bool separable_supported(const Geometry &g, int dtype)
+{
+    (void)dtype;
+    if (g.cutoff == PG_CUTOFF_SPHERE) return false;
+    const long long N = (long long)g.ny * g.nz;
+    // Row segments go out as bulk copies: 16-byte multiples; tables must fit shared memory.
+    if (N % 16 != 0) return false;
+    if (g.ny > 256 || g.nz > 256) return false;
+    return true;
+}
+
+cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &t, int sm_count,
+                           KernelLaunch *kl)
+{
+    if (!separable_supported(a0.geo, dtype)) return cudaErrorNotSupported;
+    SeparableArgs a = a0;
+    int n_tile = t.n_tile;
+    if (n_tile != 64 && n_tile != 128 && n_tile != 256) n_tile = 128;
+    const int esz = dtype == PG_F32 ? 4 : 2;
+    // Largest requested tile whose shared-memory footprint fits one SM's 227 KB.
+    while (n_tile > 64 && sep_layout(a.geo.ny, a.geo.nz, n_tile, esz).total > 227 * 1024)
+        n_tile /= 2;
+    const SepLayout L = sep_layout(a.geo.ny, a.geo.nz, n_tile, esz);
+    if (L.total > 227 * 1024) return cudaErrorNotSupported;
+    a.n_tile = n_tile;
+    a.m_tiles = (a.geo.C * a.geo.nx + kRows - 1) / kRows;
+    const void *f = dtype == PG_F32   ? pick_cut<float>(a.geo.cutoff, a.geo.periodic)
+                    : dtype == PG_F16 ? pick_cut<__half>(a.geo.cutoff, a.geo.periodic)
+                                      : pick_cut<__nv_bfloat16>(a.geo.cutoff, a.geo.periodic);
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kRows, L.total);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorNotSupported;
+    // Tensor memory: 512 columns per SM shared by the resident CTAs.
+    per_sm = per_sm < 512 / n_tile ? per_sm : 512 / n_tile;
+    if (t.blocks_per_sm > 0 && t.blocks_per_sm < per_sm) per_sm = t.blocks_per_sm;
+    const long long items = (long long)a.geo.n_mol * a.m_tiles;
+    long long blocks = (long long)sm_count * per_sm;
+    if (blocks > items) blocks = items;
+    if (blocks < 1) blocks = 1;
+    kl->func = f;
+    kl->grid = dim3((unsigned)blocks);
+    kl->block = dim3(kRows);
+    kl->smem = (size_t)L.total;
+    set_args(kl, a);
+    return cudaSuccess;
 }
 
 }  // namespace pgi
