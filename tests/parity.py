@@ -19,12 +19,17 @@ import numpy as np
 import oracle
 
 TOL = {"f32": 1e-5, "f16": 1e-3, "bf16": 5e-3}
+# Absolute floor: the spacing of the output format near zero.  FP16 cannot represent values
+# below its smallest subnormal 2^-24; FP32/BF16 kernels flush results below 2^-126 to zero.
+ABS_TOL = {"f32": 2.0 ** -120, "f16": 2.0 ** -24, "bf16": 2.0 ** -120}
 SEPARABLE_TOL = 1e-2  # BF16 operands (2 x 2^-9 relative per term) + FP16 store
 GRAD_TOL = 1e-4       # GPU gradient vs oracle, relative to max |g| per molecule
 
 
-def grid_check(G_gpu, prob: "oracle.Problem", rel_tol: float, eps: float = 1e-5):
-    """Assert the CUDA grids lie within tolerance of the oracle; return error stats."""
+def grid_check(G_gpu, prob: "oracle.Problem", rel_tol: float, eps: float = 1e-5,
+               abs_tol: float = 2.0 ** -120):
+    """Assert the CUDA grids lie within rel_tol * max + abs_tol of the oracle; return error
+    stats."""
     G = np.asarray(G_gpu, dtype=np.float64).reshape(prob.shape)
     if prob.c.cutoff == oracle.CUTOFFS["none"]:
         g_in = oracle.voxelize(prob)
@@ -38,7 +43,7 @@ def grid_check(G_gpu, prob: "oracle.Problem", rel_tol: float, eps: float = 1e-5)
         if m == 0.0:
             assert np.all(G[b] == 0.0), f"molecule {b}: oracle grid is zero, CUDA is not"
             continue
-        tol = rel_tol * m
+        tol = rel_tol * m + abs_tol
         lo = g_in[b] - tol
         hi = g_in[b] + g_band[b] + tol
         bad = (G[b] < lo) | (G[b] > hi) | ~np.isfinite(G[b])

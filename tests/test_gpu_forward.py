@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synth
-from tests.parity import TOL, grid_check
+from tests.parity import ABS_TOL, TOL, grid_check
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -45,7 +45,8 @@ def run(pg, wl, dtype=None, path="direct", batch=None, grid=None, tuning=None):
 def test_plain_small_f32_matches_oracle(pg):
     wl = synth.plain_small()
     G = run(pg, wl)
-    stats = grid_check(G, oracle.Problem.from_workload(wl), TOL["f32"])
+    stats = grid_check(G, oracle.Problem.from_workload(wl), TOL["f32"],
+               abs_tol=ABS_TOL["f32"])
     assert stats["max_abs_rel"] < 1e-5
 
 
@@ -58,7 +59,8 @@ def test_dtypes_cutoffs_and_boundaries(pg, dtype, cutoff, periodic):
     if periodic:
         wl.cutoff_k = 2.5  # r_c = 1.5 A < L/2 = 8 A
     G = run(pg, wl, dtype=dtype)
-    grid_check(G, oracle.Problem.from_workload(wl), TOL[dtype])
+    grid_check(G, oracle.Problem.from_workload(wl), TOL[dtype],
+               abs_tol=ABS_TOL[dtype])
 
 
 @pytest.mark.parametrize("shape,dtype", [((17, 19, 23), "f32"), ((9, 5, 31), "f16"),
@@ -71,7 +73,8 @@ def test_ragged_and_odd_shapes(pg, shape, dtype):
     b = wl.batch
     b.spacing = np.tile(np.array([0.55, 0.45, 0.6], np.float32), (b.n_mol, 1))
     G = run(pg, wl, dtype=dtype)
-    grid_check(G, oracle.Problem.from_workload(wl), TOL[dtype])
+    grid_check(G, oracle.Problem.from_workload(wl), TOL[dtype],
+               abs_tol=ABS_TOL[dtype])
 
 
 def test_empty_molecules_atoms_outside_and_empty_batch(pg):
@@ -84,7 +87,8 @@ def test_empty_molecules_atoms_outside_and_empty_batch(pg):
              b.elem[b.atoms_of(3)]]
     nb = synth._pack(coords, elems, b.origin, b.spacing)
     G = run(pg, wl, batch=nb)
-    grid_check(G, oracle.Problem.from_workload(wl, batch=nb), TOL["f32"])
+    grid_check(G, oracle.Problem.from_workload(wl, batch=nb), TOL["f32"],
+               abs_tol=ABS_TOL["f32"])
     assert np.all(G[1] == 0.0)
     # No molecules at all, and molecules without atoms.
     empty = synth._pack([], [], np.zeros((0, 3)), np.zeros((0, 3)))
@@ -102,7 +106,8 @@ def test_dense_items_take_unstaged_fallback_bitwise(pg):
     wl = synth.plain_small(n_mol=1)
     for dtype in ("f32", "f16"):
         G = run(pg, wl, batch=nb, dtype=dtype)
-        grid_check(G, oracle.Problem.from_workload(wl, batch=nb), TOL[dtype])
+        grid_check(G, oracle.Problem.from_workload(wl, batch=nb), TOL[dtype],
+               abs_tol=ABS_TOL[dtype])
 
 
 def test_deterministic_across_runs_and_launch_shapes(pg):
@@ -132,7 +137,8 @@ def test_outputs_stay_in_bounds(pg):
         pg.voxelize(db, grid, dtype=dtype, path="direct", out=out)
         pg.sync_status()
         assert torch.all(buf[:pad] == 7.0) and torch.all(buf[pad + n:] == 7.0)
-        grid_check(out.float().cpu().numpy(), oracle.Problem.from_workload(wl), TOL[dtype])
+        grid_check(out.float().cpu().numpy(), oracle.Problem.from_workload(wl), TOL[dtype],
+               abs_tol=ABS_TOL[dtype])
 
 
 def test_misaligned_output_uses_scalar_stores(pg):
@@ -143,7 +149,8 @@ def test_misaligned_output_uses_scalar_stores(pg):
     out = buf[1:].view(2, 5, 32, 32, 32)  # 4-byte but not 16-byte aligned
     pg.voxelize(pg.DeviceBatch.from_numpy(wl.batch), grid, dtype="f32", path="direct", out=out)
     pg.sync_status()
-    grid_check(out.cpu().numpy(), oracle.Problem.from_workload(wl), TOL["f32"])
+    grid_check(out.cpu().numpy(), oracle.Problem.from_workload(wl), TOL["f32"],
+               abs_tol=ABS_TOL["f32"])
 
 
 def test_device_validation_flags_without_faulting(pg):
@@ -162,7 +169,8 @@ def test_device_validation_flags_without_faulting(pg):
     keep[2] = False
     ok = synth.Batch(b.coords[keep], b.elem[keep], b.mol_off.copy(), b.origin, b.spacing)
     ok.mol_off[1:] -= 1
-    grid_check(G.cpu().numpy(), oracle.Problem.from_workload(wl, batch=ok), TOL["f32"])
+    grid_check(G.cpu().numpy(), oracle.Problem.from_workload(wl, batch=ok), TOL["f32"],
+               abs_tol=ABS_TOL["f32"])
     # Offsets past n_atoms and non-positive spacing: flagged, zeros written, no fault.
     bad2 = synth.Batch(b.coords.copy(), b.elem.copy(), b.mol_off.copy(), b.origin.copy(),
                        b.spacing.copy())
@@ -194,7 +202,7 @@ def _sampled(pg, wl, dtype, n_sample, seed, path="auto", tune=True):
     idx = np.sort(np.random.default_rng(seed).choice(wl.batch.n_mol, n_sample, replace=False))
     sub = G[torch.as_tensor(idx, device="cuda")].float().cpu().numpy()
     return grid_check(sub, oracle.Problem.from_workload(wl, batch=wl.batch.subset(idx)),
-                      TOL[dtype])
+                      TOL[dtype], abs_tol=ABS_TOL[dtype])
 
 
 def test_qm9_shaped_full_batch_sampled_parity(pg):
