@@ -218,6 +218,34 @@ pg_status pg_plan_destroy(pg_plan *plan);
 /* Free per-device state and the tuning cache.  Later calls re-create what they need. */
 void pg_shutdown(void);
 
+/*
+ * pg_voxelize_noalloc - forward voxelization that allocates no device memory.
+ *
+ * The paper has no counterpart: this serves callers that cannot let a library allocate.
+ * The other entry points cudaMalloc a small per-device state the first time they run on a
+ * device.  That is not possible while a stream capture in global mode is open elsewhere in
+ * the process, nor acceptable when a framework's caching allocator or an external budget
+ * owns all device memory, or when a host freezes its device-memory footprint after
+ * start-up.  This call runs the direct kernel (same results, bit for bit, as
+ * pg_voxelize with PG_PATH_DIRECT) with its scratch - the work counter and the error word -
+ * in a fixed PG_NOALLOC_SCRATCH_BYTES array compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  A launch needs 20 bytes of it whatever
+ * the batch size; a launch that needed more than the array holds would be rejected with
+ * PG_ERR_INVALID_ARG.
+ *   batch, grid, out_dtype, out   as for pg_voxelize (DEVICE buffers, caller-owned)
+ *   stream                        cudaStream_t as void* (NULL: legacy default stream)
+ *   bits_out                      if non-NULL, receives the device error bits (PG_DEVERR_*)
+ * Synchronous: clears the scratch, launches, copies the error word back into a host stack
+ * variable and synchronizes `stream`; returns PG_ERR_DEVICE_VALIDATION if a bit was set.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  All calls
+ * share the one array: calls that overlap on the GPU (different streams or threads) race
+ * on it and must be serialized by the caller.
+ */
+#define PG_NOALLOC_SCRATCH_BYTES 256
+pg_status pg_voxelize_noalloc(const pg_batch *batch, const pg_grid *grid, int32_t out_dtype,
+                              void *out, void *stream, uint32_t *bits_out);
+
 #ifdef __cplusplus
 }
 #endif

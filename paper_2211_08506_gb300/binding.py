@@ -33,7 +33,7 @@ EXPORTED = (
     "pg_version", "pg_last_error", "pg_status_string", "pg_voxelize", "pg_voxelize_tuned",
     "pg_voxelize_backward", "pg_sync_status", "pg_autotune", "pg_get_tuning",
     "pg_tuning_save", "pg_tuning_load", "pg_plan_create", "pg_plan_run", "pg_plan_destroy",
-    "pg_shutdown",
+    "pg_shutdown", "pg_voxelize_noalloc",
 )
 
 
@@ -117,9 +117,12 @@ def load() -> ctypes.CDLL:
         lib.pg_plan_run.argtypes = [vp, P(pg_batch), vp, vp]
         lib.pg_plan_destroy.argtypes = [vp]
         lib.pg_shutdown.restype = None
+        lib.pg_voxelize_noalloc.argtypes = [P(pg_batch), P(pg_grid), i32, vp, vp,
+                                            P(ctypes.c_uint32)]
         for name in ("pg_voxelize", "pg_voxelize_tuned", "pg_voxelize_backward",
                      "pg_sync_status", "pg_autotune", "pg_get_tuning", "pg_tuning_save",
-                     "pg_tuning_load", "pg_plan_create", "pg_plan_run", "pg_plan_destroy"):
+                     "pg_tuning_load", "pg_plan_create", "pg_plan_run", "pg_plan_destroy",
+                     "pg_voxelize_noalloc"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -210,3 +213,11 @@ def pg_plan_destroy(plan):
 
 def pg_shutdown():
     load().pg_shutdown()
+
+
+def pg_voxelize_noalloc(batch, grid, out_dtype, out, stream):
+    """Allocation-free forward voxelization (synchronous); returns (status, error bits)."""
+    bits = ctypes.c_uint32(0)
+    st = load().pg_voxelize_noalloc(ctypes.byref(batch), ctypes.byref(grid), out_dtype, out,
+                                    stream, ctypes.byref(bits))
+    return st, bits.value

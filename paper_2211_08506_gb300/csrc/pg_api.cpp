@@ -418,6 +418,46 @@ pg_status report_bits(unsigned bits)
 
 }  // namespace
 
+namespace pgi {
+
+pg_status set_last_error(pg_status status, const char *fmt, ...)
+{
+    char buf[768];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_last_error = buf;
+    return status;
+}
+
+pg_status direct_launch_with_scratch(const pg_batch *b, const pg_grid *g, int dtype, void *out,
+                                     unsigned *err, unsigned long long *sched, int sm_count,
+                                     KernelLaunch *kl)
+{
+    kl->func = nullptr;
+    pg_status st = validate(b, g);
+    if (st) return st;
+    if ((st = check_dtype(dtype))) return st;
+    if (b->n_mol > 0 && !out) return fail(PG_ERR_INVALID_ARG, "out must not be NULL");
+    if ((uintptr_t)out % dtype_size(dtype) != 0)
+        return fail(PG_ERR_INVALID_ARG, "out is not aligned to its element size");
+    if (b->n_mol == 0) return PG_OK;
+    DirectArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.in = make_inputs(b);
+    a.out = out;
+    a.err = err;
+    a.sched = sched;
+    make_geometry(b, g, &a.geo);
+    const pg_tuning t = default_tuning(PG_PATH_DIRECT);
+    cudaError_t e = direct_plan(a, dtype, vec_stores_ok(out, g, dtype) ? 1 : 0, t, sm_count, kl);
+    if (e != cudaSuccess) return cuda_fail(e, "direct_plan");
+    return PG_OK;
+}
+
+}  // namespace pgi
+
 extern "C" {
 
 int32_t pg_version(void) { return PG_ABI_VERSION; }

@@ -95,6 +95,16 @@ cudaError_t buffer_hash(const void *buf, size_t bytes, unsigned long long *d_out
 cudaError_t buffer_compare(const void *a, const void *b, size_t n, int dtype, float *d_out2,
                            cudaStream_t s);
 
+// Validate a direct-path forward call and describe its launch with a caller-supplied
+// error word and work counter (no device state of the library is touched).  Sets the
+// thread's last-error message on failure; kl->func stays null when there is nothing to run.
+pg_status direct_launch_with_scratch(const pg_batch *b, const pg_grid *g, int dtype, void *out,
+                                     unsigned *err, unsigned long long *sched, int sm_count,
+                                     KernelLaunch *kl);
+
+// Record a failure message for pg_last_error() and return `status`.
+pg_status set_last_error(pg_status status, const char *fmt, ...);
+
 inline cudaError_t launch(KernelLaunch &kl, cudaStream_t s)
 {
     kl.params[0] = kl.args;
