@@ -9,6 +9,7 @@
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <fstream>
 #include <map>
@@ -419,6 +420,17 @@ pg_status report_bits(unsigned bits)
 }  // namespace
 
 namespace pgi {
+
+void debug_launch(const KernelLaunch &kl)
+{
+    static const bool on = [] {
+        const char *v = std::getenv("PG_DEBUG_LAUNCH");
+        return v && v[0] == '1';
+    }();
+    if (on)
+        std::fprintf(stderr, "[pg] launch func=%p grid=%u block=%u smem=%zu\n", kl.func,
+                     kl.grid.x, kl.block.x, kl.smem);
+}
 
 pg_status set_last_error(pg_status status, const char *fmt, ...)
 {

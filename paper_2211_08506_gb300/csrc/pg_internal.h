@@ -105,9 +105,13 @@ pg_status direct_launch_with_scratch(const pg_batch *b, const pg_grid *g, int dt
 // Record a failure message for pg_last_error() and return `status`.
 pg_status set_last_error(pg_status status, const char *fmt, ...);
 
+// PG_DEBUG_LAUNCH=1 in the environment prints every launch shape to stderr.
+void debug_launch(const KernelLaunch &kl);
+
 inline cudaError_t launch(KernelLaunch &kl, cudaStream_t s)
 {
     kl.params[0] = kl.args;
+    debug_launch(kl);
     return cudaLaunchKernel(kl.func, kl.grid, kl.block, kl.params, kl.smem, s);
 }
 

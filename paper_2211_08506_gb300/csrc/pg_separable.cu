@@ -543,12 +543,26 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
                                       : pick_cut<__nv_bfloat16>(a.geo.cutoff, a.geo.periodic);
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, kRows, L.total);
+    e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
+    // Resident CTAs per SM from the three limits that bind here: shared memory (with the
+    // per-block reservation), registers, and the SM's 512 tensor-memory columns.
+    int dev = 0, smem_sm = 0, smem_reserved = 0, regs_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)))
+        return e;
+    if ((e = cudaDeviceGetAttribute(&smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev)))
+        return e;
+    if ((e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)))
+        return e;
+    cudaFuncAttributes fa;
+    if ((e = cudaFuncGetAttributes(&fa, f)) != cudaSuccess) return e;
+    const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * kRows;
+    int per_sm = smem_sm / (L.total + smem_reserved);
+    if (regs_cta > 0 && regs_sm / regs_cta < per_sm) per_sm = regs_sm / regs_cta;
+    if (512 / n_tile < per_sm) per_sm = 512 / n_tile;
     if (per_sm < 1) return cudaErrorNotSupported;
-    // Tensor memory: 512 columns per SM shared by the resident CTAs.
-    per_sm = per_sm < 512 / n_tile ? per_sm : 512 / n_tile;
     if (t.blocks_per_sm > 0 && t.blocks_per_sm < per_sm) per_sm = t.blocks_per_sm;
     const long long items = (long long)a.geo.n_mol * a.m_tiles;
     long long blocks = (long long)sm_count * per_sm;
