@@ -291,14 +291,28 @@ def run_ours(args):
     out = torch.empty(grid.out_shape(B), dtype=api.DTYPES[dtype][1], device="cuda")
     stream = torch.cuda.Stream()
 
-    # Untimed: autotune the launch for this bucket, then capture one step in a graph.
+    # Differentiation: a step is the forward pass plus the adjoint for L = <W, G>.
+    W = grad = None
+    if wl.name == "differentiation":
+        W = torch.from_numpy(synth.loss_weights(wl, shard=rank if world > 1 else None)).cuda()
+        grad = torch.empty((wl.batch.n_atoms, 3), dtype=torch.float32, device="cuda")
+
+    # Untimed: autotune the launch for this bucket, then capture the step in graphs (forward,
+    # and adjoint if any, so the forward kernel's own time is visible between them).
     with torch.cuda.stream(stream):
         tuning = api.autotune(db, grid, dtype=dtype, path=path, out=out)
         api.voxelize(db, grid, dtype=dtype, path=path, out=out)
+        if W is not None:
+            api.voxelize_backward(db, grid, W, grad_coords=grad)
     api.sync_status(stream)
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
         api.voxelize(db, grid, dtype=dtype, path=path, out=out)
+    graph_bwd = None
+    if W is not None:
+        graph_bwd = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph_bwd, stream=stream):
+            api.voxelize_backward(db, grid, W, grad_coords=grad)
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
@@ -307,22 +321,30 @@ def run_ours(args):
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             graph.replay()
+            if graph_bwd is not None:
+                graph_bwd.replay()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev_mid = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     sampler.mark("start")
     with torch.cuda.stream(stream):
         ev[0].record(stream)
         for i in range(args.steps):
             graph.replay()
+            ev_mid[i].record(stream)
+            if graph_bwd is not None:
+                graph_bwd.replay()
             ev[i + 1].record(stream)
     torch.cuda.synchronize()
     sampler.mark("stop")
     if dist:
         dist.barrier()
-    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    # Forward kernel time per launch (the step's dominant kernel) and the adjoint's.
+    per_step = [ev[i].elapsed_time(ev_mid[i]) for i in range(args.steps)]
+    per_bwd = [ev_mid[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     if dist:
         t = torch.tensor([total_ms], device="cuda")
@@ -403,6 +425,8 @@ def run_ours(args):
             "cuda_graph": True,
         },
         "voxels_per_sec": voxels,
+        "step": "forward + adjoint" if graph_bwd is not None else "forward",
+        "adjoint_ms_per_step": statistics.mean(per_bwd) if graph_bwd is not None else None,
         "roofline": {
             "bound": "hbm",
             "achieved": achieved,
@@ -424,7 +448,7 @@ def run_ours(args):
             "d2h_bytes_per_step": 4,
             "api": "pg_plan_run (pinned host CSR batch -> graph: H2D + kernel -> error word D2H)",
         },
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (2 if graph_bwd is not None else 1),
         "clocks": sampler.summary(),
         "cpu_baseline": base,
     }

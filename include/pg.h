@@ -121,6 +121,8 @@ typedef struct {
  *   blocks_per_sm  persistent CTAs per SM (0 = as many as fit)
  *   store_hint     0: default global stores; 1: streaming (evict-first) stores
  *   n_tile         separable path: output columns per tensor-core tile (64, 128 or 256)
+ *   gather_only    direct path: 0 lets dense planes accumulate atom by atom in shared memory
+ *                  (scatter mode); 1 gathers every plane.  Both give identical bits.
  */
 typedef struct {
     int32_t path;
@@ -128,7 +130,8 @@ typedef struct {
     int32_t blocks_per_sm;
     int32_t store_hint;
     int32_t n_tile;
-    int32_t reserved[3];
+    int32_t gather_only;
+    int32_t reserved[2];
 } pg_tuning;
 
 /* Library ABI version (PG_ABI_VERSION). */

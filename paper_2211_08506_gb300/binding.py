@@ -69,13 +69,14 @@ class pg_tuning(ctypes.Structure):
         ("blocks_per_sm", ctypes.c_int32),
         ("store_hint", ctypes.c_int32),
         ("n_tile", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("gather_only", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
     def as_dict(self):
         return {"path": self.path, "block_threads": self.block_threads,
                 "blocks_per_sm": self.blocks_per_sm, "store_hint": self.store_hint,
-                "n_tile": self.n_tile}
+                "n_tile": self.n_tile, "gather_only": self.gather_only}
 
 
 _lock = threading.Lock()

@@ -190,6 +190,15 @@ pg_tuning default_tuning(int path)
     return t;
 }
 
+// Floats of per-warp shared memory for the direct kernel's scatter mode (dense planes), or 0
+// where it does not apply: no cutoff, or planes above 16 KB of FP32 accumulators.
+int direct_plane_stride(const pg_grid *g)
+{
+    const long long plane = (long long)g->ny * g->nz;
+    if (g->cutoff == PG_CUTOFF_NONE || plane * 4 > 16384) return 0;
+    return (int)((plane + 3) / 4 * 4);
+}
+
 bool vec_stores_ok(const void *out, const pg_grid *g, int dtype)
 {
     return ((uintptr_t)out % 16 == 0) && (((size_t)g->nz * dtype_size(dtype)) % 16 == 0);
@@ -228,6 +237,7 @@ pg_status plan_forward(const pg_batch *b, const pg_grid *g, int dtype, void *out
     a.out = out;
     a.err = err;
     a.sched = sched;
+    a.plane_stride = t.gather_only ? 0 : direct_plane_stride(g);
     a.geo = G;
     cudaError_t e = direct_plan(a, dtype, vec_stores_ok(out, g, dtype) ? 1 : 0, t, d.sms, kl);
     if (e != cudaSuccess) return cuda_fail(e, "direct_plan");
@@ -461,6 +471,7 @@ pg_status direct_launch_with_scratch(const pg_batch *b, const pg_grid *g, int dt
     a.out = out;
     a.err = err;
     a.sched = sched;
+    a.plane_stride = direct_plane_stride(g);
     make_geometry(b, g, &a.geo);
     const pg_tuning t = default_tuning(PG_PATH_DIRECT);
     cudaError_t e = direct_plan(a, dtype, vec_stores_ok(out, g, dtype) ? 1 : 0, t, sm_count, kl);
@@ -601,6 +612,15 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
                     t.store_hint = hint;
                     cands.push_back(t);
                 }
+        if (grid->cutoff != PG_CUTOFF_NONE)
+            for (int threads : {256, 512})
+                for (int hint : {0, 1}) {
+                    pg_tuning t = default_tuning(PG_PATH_DIRECT);
+                    t.block_threads = threads;
+                    t.store_hint = hint;
+                    t.gather_only = 1;
+                    cands.push_back(t);
+                }
     }
     Geometry G;
     make_geometry(batch, grid, &G);
@@ -738,7 +758,7 @@ pg_status pg_tuning_save(const char *file)
     for (auto &kv : g_tune)
         f << kv.first << ' ' << kv.second.path << ' ' << kv.second.block_threads << ' '
           << kv.second.blocks_per_sm << ' ' << kv.second.store_hint << ' ' << kv.second.n_tile
-          << '\n';
+          << ' ' << kv.second.gather_only << '\n';
     return PG_OK;
 }
 
@@ -759,6 +779,7 @@ pg_status pg_tuning_load(const char *file)
         if (!(is >> key >> t.path >> t.block_threads >> t.blocks_per_sm >> t.store_hint >>
               t.n_tile))
             return fail(PG_ERR_INVALID_ARG, "malformed tuning line: %s", line.c_str());
+        if (!(is >> t.gather_only)) t.gather_only = 0;
         add[key] = t;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -6,8 +6,8 @@
 // Work decomposition.  The output is a dense [B][C][nx][ny][nz] array and, with ~1% of
 // voxels non-zero, writing it is the whole cost: the kernel is a write-bandwidth-bound
 // fill with sparse splats.  One work item is one contiguous (y, z) plane of one
-// (molecule b, channel c, x index) triple.  Persistent warps take whole (b, c) grids (nx
-// consecutive planes) from a per-launch atomic counter, so uneven molecules balance out.
+// (molecule b, channel c, x index) triple.  Persistent warps take chunks of consecutive
+// planes from a per-launch atomic counter, so uneven molecules balance out.
 //
 // Per item, one warp
 //   1. culls the molecule's atoms 32 at a time with a warp ballot: an atom survives if it
@@ -32,6 +32,11 @@
 namespace pgi {
 
 namespace {
+
+// x-planes per dynamically scheduled chunk.
+constexpr int kChunkPlanes = 8;
+// Staged candidates from which a plane is accumulated in scatter mode instead of gathered.
+constexpr int kScatterMin = 6;
 
 __device__ __forceinline__ float ex2_approx(float x)
 {
@@ -171,22 +176,117 @@ __device__ __forceinline__ void store_lane(T *out, int v, const float (&acc)[VEC
         out[v] = from_float<T>(acc[0]);
 }
 
+__device__ __forceinline__ int wrap_index(int i, int n)
+{
+    const int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// Index range [lo, hi] of voxel centres o + (i+1/2)h within rho of a (widened by one voxel
+// each side): clamped to the grid, or for periodic cells at most n consecutive (unwrapped)
+// indices so that no voxel is visited twice.
+template <bool PER>
+__device__ __forceinline__ void disc_range(float a, float rho, float o, float inv_h, int n,
+                                           int &lo, int &hi)
+{
+    lo = (int)fmaxf(floorf((a - rho - o) * inv_h - 0.5f), -1e8f) - 1;
+    hi = (int)fminf(ceilf((a + rho - o) * inv_h - 0.5f), 1e8f) + 1;
+    if (PER) {
+        if (hi - lo + 1 > n) hi = lo + n - 1;
+    } else {
+        lo = max(lo, 0);
+        hi = min(hi, n - 1);
+    }
+}
+
+// Scatter mode for dense planes.  The warp accumulates the plane in its shared-memory buffer
+// atom by atom, in atom order; each atom visits only the bounding square of its disc in this
+// plane, and every lane owns distinct voxels within one atom.  Then the plane is converted and
+// stored.  Per voxel the same non-zero terms, computed by the same operations, are added in
+// the same order as in the gather mode, so both modes give identical bits.
+template <typename T, int VEC, int CUT, bool PER, int HINT>
+__device__ __noinline__ void scatter_plane(T *out, float *acc_s, const float4 *stage, int count,
+                                           int ny, int nz, int lane, float q, float r2,
+                                           float rc, float oy, float oz, float hy, float hz,
+                                           float Ly, float iLy, float Lz, float iLz)
+{
+    const int plane = ny * nz;
+    const int nvec = plane / VEC;
+    for (int i = lane; i < plane; i += 32) acc_s[i] = 0.0f;
+    __syncwarp();
+    const float inv_hy = 1.0f / hy, inv_hz = 1.0f / hz;
+    for (int j = 0; j < count; ++j) {
+        const float4 st = stage[j];
+        const float dx = st.x, ay = st.y, az = st.z;
+        const float dx2 = dx * dx;
+        float rho = rc;
+        if (CUT == PG_CUTOFF_SPHERE) {
+            const float t = fmaf(-dx, dx, rc * rc);
+            if (t < 0.0f) continue;
+            rho = sqrtf(t);
+        }
+        int ylo, yhi, zlo, zhi;
+        disc_range<PER>(ay, rho, oy, inv_hy, ny, ylo, yhi);
+        disc_range<PER>(az, rho, oz, inv_hz, nz, zlo, zhi);
+        const int ny_s = yhi - ylo + 1, nz_s = zhi - zlo + 1;
+        if (ny_s <= 0 || nz_s <= 0) continue;
+        auto voxel = [&](int yu, int zu) {
+            const int y = PER ? wrap_index(yu, ny) : yu;
+            const int z = PER ? wrap_index(zu, nz) : zu;
+            float dy = fmaf((float)y + 0.5f, hy, oy) - ay;
+            float dz = fmaf((float)z + 0.5f, hz, oz) - az;
+            if (PER) {
+                dy = wrap(dy, Ly, iLy);
+                dz = wrap(dz, Lz, iLz);
+            }
+            const float dxy2 = fmaf(dy, dy, dx2);
+            const float d2 = fmaf(dz, dz, dxy2);
+            const bool in = (CUT == PG_CUTOFF_SPHERE)
+                                ? (d2 <= r2)
+                                : (fmaxf(fmaxf(dx2, dy * dy), dz * dz) <= r2);
+            if (in) acc_s[y * nz + z] += ex2_approx(-q * d2);
+        };
+        if (nz_s <= 32) {
+            const int rows = 32 / nz_s;
+            const int ry = lane / nz_s, rz = lane - (lane / nz_s) * nz_s;
+            if (ry < rows)
+                for (int r0 = 0; r0 < ny_s; r0 += rows)
+                    if (r0 + ry < ny_s) voxel(ylo + r0 + ry, zlo + rz);
+        } else {
+            for (int fy = 0; fy < ny_s; ++fy)
+                for (int fz = lane; fz < nz_s; fz += 32) voxel(ylo + fy, zlo + fz);
+        }
+        __syncwarp();
+    }
+    for (int v = lane; v < nvec; v += 32) {
+        float a[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) a[k] = acc_s[v * VEC + k];
+        store_lane<T, VEC, HINT>(out, v, a);
+    }
+    __syncwarp();
+}
+
 template <typename T, int VEC, int CUT, bool PER, int HINT>
 __global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
 {
-    extern __shared__ float4 stage_all[];
+    extern __shared__ float4 smem_all[];
     const Geometry &G = A.geo;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int warps_per_block = blockDim.x >> 5;
-    float4 *stage = stage_all + warp * kStageCap;
+    // Per warp: kStageCap staged atoms, then (scatter mode) a plane of A.plane_stride floats.
+    float4 *stage = smem_all + (size_t)warp * (kStageCap + A.plane_stride / 4);
+    float *acc_s = reinterpret_cast<float *>(stage + kStageCap);
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    // Work is handed out dynamically in chunks of one (molecule, channel) grid = nx planes:
-    // lane 0 takes the next chunk index from a per-launch counter.  The molecule's header
-    // and, for molecules of at most 32 atoms, the atoms themselves stay in registers across
-    // the chunk's planes.  The last warp to finish resets the counter for the next launch.
-    const unsigned long long n_chunks = (unsigned long long)G.n_mol * G.C;
+    // Work is handed out dynamically in chunks of up to kChunkPlanes consecutive x-planes of
+    // one (molecule, channel) grid: lane 0 takes the next chunk index from a per-launch
+    // counter.  The molecule's header and, for molecules of at most 32 atoms, the atoms
+    // themselves stay in registers across the chunk's planes (and across chunks of the same
+    // molecule).  The last warp to finish resets the counter for the next launch.
+    const int x_chunks = (G.nx + kChunkPlanes - 1) / kChunkPlanes;
+    const unsigned long long n_chunks = (unsigned long long)G.n_mol * G.C * x_chunks;
     const unsigned long long total_warps = (unsigned long long)gridDim.x * warps_per_block;
 
     const int plane = G.ny * G.nz;
@@ -208,8 +308,12 @@ __global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
         if (lane == 0) chunk = atomicAdd(A.sched, 1ull);
         chunk = __shfl_sync(0xffffffffu, chunk, 0);
         if (chunk >= n_chunks) break;
-        const int b = (int)(chunk / (unsigned)G.C);
-        const int c = (int)(chunk - (unsigned long long)b * G.C);
+        const unsigned long long bc = chunk / (unsigned)x_chunks;
+        const int xc = (int)(chunk - bc * x_chunks);
+        const int b = (int)(bc / (unsigned)G.C);
+        const int c = (int)(bc - (unsigned long long)b * G.C);
+        const int x_begin = xc * kChunkPlanes;
+        const int x_end = min(G.nx, x_begin + kChunkPlanes);
         if (b != cur_b) {
             cur_b = b;
             a0 = __ldg(A.in.mol_off + b);
@@ -251,8 +355,8 @@ __global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
             }
             if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(A.err, PG_DEVERR_ELEMENT);
         }
-        for (int x = 0; x < G.nx; ++x) {
-            const long long item = (long long)chunk * G.nx + x;
+        for (int x = x_begin; x < x_end; ++x) {
+            const long long item = (long long)bc * G.nx + x;
             T *out = reinterpret_cast<T *>(A.out) + item * (long long)plane;
             const float q = G.q[c], r2 = G.r2[c], rc = G.rcull[c];
             if (PER && CUT != PG_CUTOFF_NONE && lane == 0 && x == 0 && a1 > a0 &&
@@ -343,6 +447,11 @@ __global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
                 __syncwarp();
                 if (count == 0) {
                     zero_plane<T, VEC, HINT>(out, nvec, lane);
+                } else if (CUT != PG_CUTOFF_NONE && A.plane_stride > 0 && count >= kScatterMin &&
+                           count <= kStageCap) {
+                    scatter_plane<T, VEC, CUT, PER, HINT>(out, acc_s, stage, count, G.ny, G.nz,
+                                                         lane, q, r2, rc, oy, oz, hy, hz, Ly,
+                                                         iLy, Lz, iLz);
                 } else {
                     int y = y_start, z0 = z_start;
                     for (int g = 0; g < nvec; g += 32) {
@@ -477,9 +586,13 @@ cudaError_t direct_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tun
 
     int threads = t.block_threads;
     if (threads != 128 && threads != 256 && threads != 512) threads = 256;
-    const size_t smem = (size_t)(threads / 32) * kStageCap * sizeof(float4);
+    const size_t per_warp = kStageCap * sizeof(float4) + (size_t)a.plane_stride * sizeof(float);
+    while (threads > 128 && (size_t)(threads / 32) * per_warp > 200 * 1024) threads /= 2;
+    const size_t smem = (size_t)(threads / 32) * per_warp;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (t.blocks_per_sm > 0 && t.blocks_per_sm < per_sm) per_sm = t.blocks_per_sm;

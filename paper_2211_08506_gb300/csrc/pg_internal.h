@@ -40,6 +40,7 @@ struct DirectArgs {
     void *out;
     unsigned *err;
     unsigned long long *sched;  // {next chunk, retired warps}; zero between launches
+    int plane_stride;           // floats of per-warp plane buffer for scatter mode (0: off)
     Geometry geo;
 };
 

@@ -237,3 +237,16 @@ def test_register_and_staged_paths_agree_bitwise(pg):
         G1 = run(pg, wl, dtype=dtype)
         G2 = run(pg, wl, dtype=dtype, batch=padded)
         assert np.array_equal(G1, G2)
+
+
+def test_scatter_and_gather_modes_agree_bitwise_on_dense_cells(pg):
+    # Dense periodic cells: planes with many candidates take the shared-memory scatter mode
+    # unless gather_only is set; both must produce identical bits, and match the oracle.
+    wl = synth.crystal_shaped(n_cells=24)
+    for dtype in ("f32", "f16"):
+        auto = run(pg, wl, dtype=dtype, tuning={"path": 1, "block_threads": 256})
+        gather = run(pg, wl, dtype=dtype,
+                     tuning={"path": 1, "block_threads": 256, "gather_only": 1})
+        assert np.array_equal(auto, gather)
+    grid_check(auto[:6], oracle.Problem.from_workload(wl, batch=wl.batch.subset(range(6))),
+               TOL["f16"], abs_tol=ABS_TOL["f16"])
