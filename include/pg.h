@@ -123,6 +123,7 @@ typedef struct {
  *   n_tile         separable path: output columns per tensor-core tile (64, 128 or 256)
  *   gather_only    direct path: 0 lets dense planes accumulate atom by atom in shared memory
  *                  (scatter mode); 1 gathers every plane.  Both give identical bits.
+ *   chunk_planes   direct path: x-planes per dynamically scheduled work chunk (1..64; 0 = 8)
  */
 typedef struct {
     int32_t path;
@@ -131,7 +132,8 @@ typedef struct {
     int32_t store_hint;
     int32_t n_tile;
     int32_t gather_only;
-    int32_t reserved[2];
+    int32_t chunk_planes;
+    int32_t reserved[1];
 } pg_tuning;
 
 /* Library ABI version (PG_ABI_VERSION). */

@@ -70,13 +70,15 @@ class pg_tuning(ctypes.Structure):
         ("store_hint", ctypes.c_int32),
         ("n_tile", ctypes.c_int32),
         ("gather_only", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("chunk_planes", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 1),
     ]
 
     def as_dict(self):
         return {"path": self.path, "block_threads": self.block_threads,
                 "blocks_per_sm": self.blocks_per_sm, "store_hint": self.store_hint,
-                "n_tile": self.n_tile, "gather_only": self.gather_only}
+                "n_tile": self.n_tile, "gather_only": self.gather_only,
+                "chunk_planes": self.chunk_planes}
 
 
 _lock = threading.Lock()

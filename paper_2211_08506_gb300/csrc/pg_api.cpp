@@ -187,6 +187,7 @@ pg_tuning default_tuning(int path)
     t.blocks_per_sm = 0;
     t.store_hint = 0;
     t.n_tile = 128;
+    t.chunk_planes = 8;
     return t;
 }
 
@@ -238,6 +239,7 @@ pg_status plan_forward(const pg_batch *b, const pg_grid *g, int dtype, void *out
     a.err = err;
     a.sched = sched;
     a.plane_stride = t.gather_only ? 0 : direct_plane_stride(g);
+    a.chunk_planes = (t.chunk_planes >= 1 && t.chunk_planes <= 64) ? t.chunk_planes : 8;
     a.geo = G;
     cudaError_t e = direct_plan(a, dtype, vec_stores_ok(out, g, dtype) ? 1 : 0, t, d.sms, kl);
     if (e != cudaSuccess) return cuda_fail(e, "direct_plan");
@@ -472,6 +474,7 @@ pg_status direct_launch_with_scratch(const pg_batch *b, const pg_grid *g, int dt
     a.err = err;
     a.sched = sched;
     a.plane_stride = direct_plane_stride(g);
+    a.chunk_planes = 8;
     make_geometry(b, g, &a.geo);
     const pg_tuning t = default_tuning(PG_PATH_DIRECT);
     cudaError_t e = direct_plan(a, dtype, vec_stores_ok(out, g, dtype) ? 1 : 0, t, sm_count, kl);
@@ -603,24 +606,23 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
 
     std::vector<pg_tuning> cands;
     if (path != PG_PATH_SEPARABLE) {
-        for (int threads : {256, 128, 512})
+        // Full product of the direct kernel's launch knobs; the default comes first and is
+        // the reference every other candidate must match bit for bit.
+        cands.push_back(default_tuning(PG_PATH_DIRECT));
+        const int go_max = grid->cutoff != PG_CUTOFF_NONE ? 1 : 0;
+        for (int threads : {256, 512})
             for (int bps : {0, 1, 2})
-                for (int hint : {0, 1}) {
-                    pg_tuning t = default_tuning(PG_PATH_DIRECT);
-                    t.block_threads = threads;
-                    t.blocks_per_sm = bps;
-                    t.store_hint = hint;
-                    cands.push_back(t);
-                }
-        if (grid->cutoff != PG_CUTOFF_NONE)
-            for (int threads : {256, 512})
-                for (int hint : {0, 1}) {
-                    pg_tuning t = default_tuning(PG_PATH_DIRECT);
-                    t.block_threads = threads;
-                    t.store_hint = hint;
-                    t.gather_only = 1;
-                    cands.push_back(t);
-                }
+                for (int hint : {0, 1})
+                    for (int cp : {1, 2, 4, 8})
+                        for (int go = 0; go <= go_max; ++go) {
+                            pg_tuning t = default_tuning(PG_PATH_DIRECT);
+                            t.block_threads = threads;
+                            t.blocks_per_sm = bps;
+                            t.store_hint = hint;
+                            t.chunk_planes = cp;
+                            t.gather_only = go;
+                            cands.push_back(t);
+                        }
     }
     Geometry G;
     make_geometry(batch, grid, &G);
@@ -758,7 +760,7 @@ pg_status pg_tuning_save(const char *file)
     for (auto &kv : g_tune)
         f << kv.first << ' ' << kv.second.path << ' ' << kv.second.block_threads << ' '
           << kv.second.blocks_per_sm << ' ' << kv.second.store_hint << ' ' << kv.second.n_tile
-          << ' ' << kv.second.gather_only << '\n';
+          << ' ' << kv.second.gather_only << ' ' << kv.second.chunk_planes << '\n';
     return PG_OK;
 }
 
@@ -780,6 +782,7 @@ pg_status pg_tuning_load(const char *file)
               t.n_tile))
             return fail(PG_ERR_INVALID_ARG, "malformed tuning line: %s", line.c_str());
         if (!(is >> t.gather_only)) t.gather_only = 0;
+        if (!(is >> t.chunk_planes)) t.chunk_planes = 8;
         add[key] = t;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -140,46 +140,82 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
             axis_support<CUT, PER>(ax, ox, hx, G.nx, rc, ilo, ni);
             axis_support<CUT, PER>(ay, oy, hy, G.ny, rc, jlo, nj);
             axis_support<CUT, PER>(az, oz, hz, G.nz, rc, klo, nk);
+            const GT *g = gout + ((long long)b * G.C + c) * grid_elems;
+            // Each lane starts at flat voxel `lane` of the (ni x nj x nk) box, z fastest, and
+            // advances 32 voxels per step with carries (no division in the loop).  For periodic
+            // cells the box start is first brought into [0, n) so one conditional wrap suffices.
+            if (PER) {
+                ilo = wrap_index(ilo, G.nx);
+                jlo = wrap_index(jlo, G.ny);
+                klo = wrap_index(klo, G.nz);
+            }
             const int njk = nj * nk;
             const long long total = (long long)ni * njk;
-            const GT *g = gout + ((long long)b * G.C + c) * grid_elems;
+            int fi = 0, fj = 0, fk = 0, si = 0, sj = 0, sk = 0;
+            if (total > 0) {
+                fi = lane / njk;
+                fj = (lane - fi * njk) / nk;
+                fk = lane - fi * njk - fj * nk;
+                si = 32 / njk;
+                sj = (32 - si * njk) / nk;
+                sk = 32 - si * njk - sj * nk;
+            }
             float sx = 0.0f, sy = 0.0f, sz = 0.0f;
-#pragma unroll 4
-            for (long long f = lane; f < total; f += 32) {
-                const int fi = (int)(f / njk);
-                const int rem = (int)(f - (long long)fi * njk);
-                const int fj = rem / nk;
-                const int fk = rem - fj * nk;
-                int i = ilo + fi, j = jlo + fj, k = klo + fk;
-                if (PER) {
-                    i = wrap_index(i, G.nx);
-                    j = wrap_index(j, G.ny);
-                    k = wrap_index(k, G.nz);
+            constexpr int U = 4;  // voxels in flight per lane
+            for (long long f0 = lane; f0 < total; f0 += 32 * U) {
+                float gv[U], dxv[U], dyv[U], dzv[U];
+                bool inv[U];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const bool valid = f0 + 32LL * u < total;
+                    int i = ilo + fi, j = jlo + fj, k = klo + fk;
+                    if (PER) {
+                        if (i >= G.nx) i -= G.nx;
+                        if (j >= G.ny) j -= G.ny;
+                        if (k >= G.nz) k -= G.nz;
+                    }
+                    float dx = fmaf((float)i + 0.5f, hx, ox) - ax;
+                    float dy = fmaf((float)j + 0.5f, hy, oy) - ay;
+                    float dz = fmaf((float)k + 0.5f, hz, oz) - az;
+                    if (PER) {
+                        dx = wrap(dx, Lx, iLx);
+                        dy = wrap(dy, Ly, iLy);
+                        dz = wrap(dz, Lz, iLz);
+                    }
+                    dxv[u] = dx;
+                    dyv[u] = dy;
+                    dzv[u] = dz;
+                    const float dx2 = dx * dx;
+                    const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx2));
+                    bool in;
+                    if (CUT == PG_CUTOFF_SPHERE)
+                        in = d2 <= r2;
+                    else if (CUT == PG_CUTOFF_BOX)
+                        in = fmaxf(dx2, fmaxf(dy * dy, dz * dz)) <= r2;
+                    else
+                        in = true;
+                    inv[u] = valid && in;
+                    gv[u] = valid ? to_float<GT>(g[(long long)i * plane + (long long)j * G.nz + k])
+                                  : 0.0f;
+                    gv[u] *= inv[u] ? ex2_approx(-q * d2) : 0.0f;
+                    // advance this lane by 32 voxels
+                    fk += sk;
+                    if (fk >= nk) {
+                        fk -= nk;
+                        ++fj;
+                    }
+                    fj += sj;
+                    if (fj >= nj) {
+                        fj -= nj;
+                        ++fi;
+                    }
+                    fi += si;
                 }
-                float dx = fmaf((float)i + 0.5f, hx, ox) - ax;
-                float dy = fmaf((float)j + 0.5f, hy, oy) - ay;
-                float dz = fmaf((float)k + 0.5f, hz, oz) - az;
-                if (PER) {
-                    dx = wrap(dx, Lx, iLx);
-                    dy = wrap(dy, Ly, iLy);
-                    dz = wrap(dz, Lz, iLz);
-                }
-                const float dx2 = dx * dx;
-                const float d2 = fmaf(dz, dz, fmaf(dy, dy, dx2));
-                bool in;
-                if (CUT == PG_CUTOFF_SPHERE)
-                    in = d2 <= r2;
-                else if (CUT == PG_CUTOFF_BOX)
-                    in = fmaxf(dx2, fmaxf(dy * dy, dz * dz)) <= r2;
-                else
-                    in = true;
-                if (in) {
-                    const float w =
-                        to_float<GT>(g[(long long)i * plane + (long long)j * G.nz + k]) *
-                        ex2_approx(-q * d2);
-                    sx = fmaf(w, dx, sx);
-                    sy = fmaf(w, dy, sy);
-                    sz = fmaf(w, dz, sz);
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    sx = fmaf(gv[u], dxv[u], sx);
+                    sy = fmaf(gv[u], dyv[u], sy);
+                    sz = fmaf(gv[u], dzv[u], sz);
                 }
             }
 #pragma unroll

@@ -33,8 +33,6 @@ namespace pgi {
 
 namespace {
 
-// x-planes per dynamically scheduled chunk.
-constexpr int kChunkPlanes = 8;
 // Staged candidates from which a plane is accumulated in scatter mode instead of gathered.
 constexpr int kScatterMin = 6;
 
@@ -230,15 +228,11 @@ __device__ __noinline__ void scatter_plane(T *out, float *acc_s, const float4 *s
         disc_range<PER>(az, rho, oz, inv_hz, nz, zlo, zhi);
         const int ny_s = yhi - ylo + 1, nz_s = zhi - zlo + 1;
         if (ny_s <= 0 || nz_s <= 0) continue;
-        auto voxel = [&](int yu, int zu) {
-            const int y = PER ? wrap_index(yu, ny) : yu;
-            const int z = PER ? wrap_index(zu, nz) : zu;
-            float dy = fmaf((float)y + 0.5f, hy, oy) - ay;
-            float dz = fmaf((float)z + 0.5f, hz, oz) - az;
-            if (PER) {
-                dy = wrap(dy, Ly, iLy);
-                dz = wrap(dz, Lz, iLz);
-            }
+        if (PER) {  // start inside [0, n): one conditional wrap per voxel suffices
+            ylo = wrap_index(ylo, ny);
+            zlo = wrap_index(zlo, nz);
+        }
+        auto add = [&](int y, float dy, int z, float dz) {
             const float dxy2 = fmaf(dy, dy, dx2);
             const float d2 = fmaf(dz, dz, dxy2);
             const bool in = (CUT == PG_CUTOFF_SPHERE)
@@ -246,15 +240,42 @@ __device__ __noinline__ void scatter_plane(T *out, float *acc_s, const float4 *s
                                 : (fmaxf(fmaxf(dx2, dy * dy), dz * dz) <= r2);
             if (in) acc_s[y * nz + z] += ex2_approx(-q * d2);
         };
+        auto row = [&](int fy, int &y, float &dy) {
+            y = ylo + fy;
+            if (PER && y >= ny) y -= ny;
+            dy = fmaf((float)y + 0.5f, hy, oy) - ay;
+            if (PER) dy = wrap(dy, Ly, iLy);
+        };
         if (nz_s <= 32) {
-            const int rows = 32 / nz_s;
+            // Lane -> (row offset ry, column rz) with rows_per_step rows per step: the lane's
+            // column, and so its z displacement, is fixed for the whole atom.
+            const int rows_per_step = 32 / nz_s;
             const int ry = lane / nz_s, rz = lane - (lane / nz_s) * nz_s;
-            if (ry < rows)
-                for (int r0 = 0; r0 < ny_s; r0 += rows)
-                    if (r0 + ry < ny_s) voxel(ylo + r0 + ry, zlo + rz);
+            if (ry < rows_per_step) {
+                int z = zlo + rz;
+                if (PER && z >= nz) z -= nz;
+                float dz = fmaf((float)z + 0.5f, hz, oz) - az;
+                if (PER) dz = wrap(dz, Lz, iLz);
+                for (int fy = ry; fy < ny_s; fy += rows_per_step) {
+                    int y;
+                    float dy;
+                    row(fy, y, dy);
+                    add(y, dy, z, dz);
+                }
+            }
         } else {
-            for (int fy = 0; fy < ny_s; ++fy)
-                for (int fz = lane; fz < nz_s; fz += 32) voxel(ylo + fy, zlo + fz);
+            for (int fy = 0; fy < ny_s; ++fy) {
+                int y;
+                float dy;
+                row(fy, y, dy);
+                for (int fz = lane; fz < nz_s; fz += 32) {
+                    int z = zlo + fz;
+                    if (PER && z >= nz) z -= nz;
+                    float dz = fmaf((float)z + 0.5f, hz, oz) - az;
+                    if (PER) dz = wrap(dz, Lz, iLz);
+                    add(y, dy, z, dz);
+                }
+            }
         }
         __syncwarp();
     }
@@ -280,12 +301,13 @@ __global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
     float *acc_s = reinterpret_cast<float *>(stage + kStageCap);
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    // Work is handed out dynamically in chunks of up to kChunkPlanes consecutive x-planes of
+    // Work is handed out dynamically in chunks of up to chunk_planes consecutive x-planes of
     // one (molecule, channel) grid: lane 0 takes the next chunk index from a per-launch
     // counter.  The molecule's header and, for molecules of at most 32 atoms, the atoms
     // themselves stay in registers across the chunk's planes (and across chunks of the same
     // molecule).  The last warp to finish resets the counter for the next launch.
-    const int x_chunks = (G.nx + kChunkPlanes - 1) / kChunkPlanes;
+    const int chunk_planes = A.chunk_planes;
+    const int x_chunks = (G.nx + chunk_planes - 1) / chunk_planes;
     const unsigned long long n_chunks = (unsigned long long)G.n_mol * G.C * x_chunks;
     const unsigned long long total_warps = (unsigned long long)gridDim.x * warps_per_block;
 
@@ -312,8 +334,8 @@ __global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
         const int xc = (int)(chunk - bc * x_chunks);
         const int b = (int)(bc / (unsigned)G.C);
         const int c = (int)(bc - (unsigned long long)b * G.C);
-        const int x_begin = xc * kChunkPlanes;
-        const int x_end = min(G.nx, x_begin + kChunkPlanes);
+        const int x_begin = xc * chunk_planes;
+        const int x_end = min(G.nx, x_begin + chunk_planes);
         if (b != cur_b) {
             cur_b = b;
             a0 = __ldg(A.in.mol_off + b);

@@ -41,6 +41,7 @@ struct DirectArgs {
     unsigned *err;
     unsigned long long *sched;  // {next chunk, retired warps}; zero between launches
     int plane_stride;           // floats of per-warp plane buffer for scatter mode (0: off)
+    int chunk_planes;           // x-planes per dynamically scheduled chunk (>= 1)
     Geometry geo;
 };
 

@@ -19,14 +19,29 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
     return z ^ (z >> 31);
 }
 
-__global__ void hash_kernel(const unsigned *words, size_t n, unsigned long long *out)
+__global__ void hash_kernel(const uint4 *words4, size_t n4, const unsigned *tail, size_t n_tail,
+                            unsigned long long *out)
 {
     unsigned long long s = 0;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x)
-        s += mix64(((unsigned long long)i << 32) ^ words[i]);
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const uint4 w = words4[i];
+        const unsigned long long base = (unsigned long long)(4 * i) << 32;
+        s += mix64(base ^ w.x) + mix64((base + (1ull << 32)) ^ w.y) +
+             mix64((base + (2ull << 32)) ^ w.z) + mix64((base + (3ull << 32)) ^ w.w);
+    }
+    if (blockIdx.x == 0)
+        for (size_t i = threadIdx.x; i < n_tail; i += blockDim.x)
+            s += mix64(((unsigned long long)(4 * n4 + i) << 32) ^ tail[i]);
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+    __shared__ unsigned long long part[32];
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        atomicAdd(out, t);
+    }
 }
 
 template <typename T>
@@ -67,7 +82,12 @@ cudaError_t buffer_hash(const void *buf, size_t bytes, unsigned long long *d_out
     if (e != cudaSuccess) return e;
     const size_t n = bytes / 4;
     if (n == 0) return cudaSuccess;
-    hash_kernel<<<1024, 256, 0, s>>>(reinterpret_cast<const unsigned *>(buf), n, d_out);
+    // 16-byte words where the buffer is 16-byte aligned, the remainder word by word.
+    const bool aligned = ((uintptr_t)buf % 16) == 0;
+    const size_t n4 = aligned ? n / 4 : 0;
+    const unsigned *tail = reinterpret_cast<const unsigned *>(buf) + 4 * n4;
+    hash_kernel<<<2048, 256, 0, s>>>(reinterpret_cast<const uint4 *>(buf), n4, tail, n - 4 * n4,
+                                     d_out);
     return cudaGetLastError();
 }
 

@@ -121,6 +121,9 @@ def test_deterministic_across_runs_and_launch_shapes(pg):
                      "store_hint": hint}
                 G = run(pg, wl, tuning=t)
                 assert np.array_equal(G.view(np.uint32), ref.view(np.uint32)), t
+    for cp in (1, 3, 8, 64):
+        G = run(pg, wl, tuning={"path": 1, "chunk_planes": cp})
+        assert np.array_equal(G.view(np.uint32), ref.view(np.uint32)), cp
 
 
 def test_outputs_stay_in_bounds(pg):
@@ -248,5 +251,8 @@ def test_scatter_and_gather_modes_agree_bitwise_on_dense_cells(pg):
         gather = run(pg, wl, dtype=dtype,
                      tuning={"path": 1, "block_threads": 256, "gather_only": 1})
         assert np.array_equal(auto, gather)
+        one = run(pg, wl, dtype=dtype,
+                  tuning={"path": 1, "block_threads": 512, "chunk_planes": 1})
+        assert np.array_equal(auto, one)
     grid_check(auto[:6], oracle.Problem.from_workload(wl, batch=wl.batch.subset(range(6))),
                TOL["f16"], abs_tol=ABS_TOL["f16"])
