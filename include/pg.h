@@ -124,6 +124,8 @@ typedef struct {
  *   gather_only    direct path: 0 lets dense planes accumulate atom by atom in shared memory
  *                  (scatter mode); 1 gathers every plane.  Both give identical bits.
  *   chunk_planes   direct path: x-planes per dynamically scheduled work chunk (1..64; 0 = 8)
+ *   separable_simple  separable path: 0 = warp-specialized pipeline (default), 1 = one-stage
+ *                  kernel.  Both accumulate the same BF16 products in the same order.
  */
 typedef struct {
     int32_t path;
@@ -133,7 +135,7 @@ typedef struct {
     int32_t n_tile;
     int32_t gather_only;
     int32_t chunk_planes;
-    int32_t reserved[1];
+    int32_t separable_simple;
 } pg_tuning;
 
 /* Library ABI version (PG_ABI_VERSION). */

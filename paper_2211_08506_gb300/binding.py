@@ -71,14 +71,14 @@ class pg_tuning(ctypes.Structure):
         ("n_tile", ctypes.c_int32),
         ("gather_only", ctypes.c_int32),
         ("chunk_planes", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 1),
+        ("separable_simple", ctypes.c_int32),
     ]
 
     def as_dict(self):
         return {"path": self.path, "block_threads": self.block_threads,
                 "blocks_per_sm": self.blocks_per_sm, "store_hint": self.store_hint,
                 "n_tile": self.n_tile, "gather_only": self.gather_only,
-                "chunk_planes": self.chunk_planes}
+                "chunk_planes": self.chunk_planes, "separable_simple": self.separable_simple}
 
 
 _lock = threading.Lock()

@@ -628,11 +628,11 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
     make_geometry(batch, grid, &G);
     const bool sep_ok = grid->cutoff != PG_CUTOFF_SPHERE && separable_supported(G, out_dtype);
     if (path != PG_PATH_DIRECT && sep_ok) {
-        for (int nt : {128, 256, 64})
-            for (int hint : {0, 1}) {
+        for (int simple : {0, 1})
+            for (int nt : {128, 256, 64}) {
                 pg_tuning t = default_tuning(PG_PATH_SEPARABLE);
                 t.n_tile = nt;
-                t.store_hint = hint;
+                t.separable_simple = simple;
                 cands.push_back(t);
             }
     }
@@ -712,16 +712,24 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
             pass = cmp[0] <= 1e-2f * cmp[1];
         }
         if (!pass) continue;
-        // Time: median of 5 launches.
+        // Time: median over 5 batches of back-to-back launches, each batch >= ~0.5 ms.
+        float first = 0.0f;
+        if ((st = cu(cudaEventRecord(e0, s), "event"))) return st;
+        if ((st = cu(launch(kl, s), "tune launch"))) return st;
+        if ((st = cu(cudaEventRecord(e1, s), "event"))) return st;
+        if ((st = cu(cudaEventSynchronize(e1), "event sync"))) return st;
+        if ((st = cu(cudaEventElapsedTime(&first, e0, e1), "elapsed"))) return st;
+        const int per_batch = std::max(1, std::min(64, (int)(0.5f / std::max(first, 1e-3f))));
         std::vector<float> ms;
         for (int r = 0; r < 5; ++r) {
             if ((st = cu(cudaEventRecord(e0, s), "event"))) return st;
-            if ((st = cu(launch(kl, s), "tune launch"))) return st;
+            for (int k = 0; k < per_batch; ++k)
+                if ((st = cu(launch(kl, s), "tune launch"))) return st;
             if ((st = cu(cudaEventRecord(e1, s), "event"))) return st;
             if ((st = cu(cudaEventSynchronize(e1), "event sync"))) return st;
             float t = 0;
             if ((st = cu(cudaEventElapsedTime(&t, e0, e1), "elapsed"))) return st;
-            ms.push_back(t);
+            ms.push_back(t / per_batch);
         }
         std::sort(ms.begin(), ms.end());
         times[i] = ms[ms.size() / 2];
@@ -760,7 +768,8 @@ pg_status pg_tuning_save(const char *file)
     for (auto &kv : g_tune)
         f << kv.first << ' ' << kv.second.path << ' ' << kv.second.block_threads << ' '
           << kv.second.blocks_per_sm << ' ' << kv.second.store_hint << ' ' << kv.second.n_tile
-          << ' ' << kv.second.gather_only << ' ' << kv.second.chunk_planes << '\n';
+          << ' ' << kv.second.gather_only << ' ' << kv.second.chunk_planes << ' '
+          << kv.second.separable_simple << '\n';
     return PG_OK;
 }
 
@@ -783,6 +792,7 @@ pg_status pg_tuning_load(const char *file)
             return fail(PG_ERR_INVALID_ARG, "malformed tuning line: %s", line.c_str());
         if (!(is >> t.gather_only)) t.gather_only = 0;
         if (!(is >> t.chunk_planes)) t.chunk_planes = 8;
+        if (!(is >> t.separable_simple)) t.separable_simple = 0;
         add[key] = t;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);

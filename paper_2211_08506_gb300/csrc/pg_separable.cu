@@ -40,7 +40,8 @@ namespace {
 constexpr int kKC = 32;         // atoms per K chunk (two K=16 MMA steps)
 constexpr int kTab = 36;        // floats per table row: 32 atoms + 4 pad (conflict-free reads)
 constexpr int kRows = 128;      // M tile = CTA threads = TMEM lanes
-constexpr unsigned kWaitLimit = 1u << 24;
+constexpr unsigned kWaitLimit = 1u << 24;         // polls of one mbarrier wait, at most
+constexpr unsigned long long kWaitNs = 2000000000ull;  // and at most 2 s of wall time
 
 struct SepLayout {
     int bar, tmem, atoms, a, b, gy, gz, stage, stage_stride, total;
@@ -97,6 +98,13 @@ __device__ __forceinline__ float wrap(float d, float L, float invL)
 }
 
 // ---- mbarrier, tcgen05 and bulk-copy wrappers (inline PTX) ----
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
@@ -462,7 +470,11 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                     mma_commit(bar);
                 }
                 bool done = false;
-                for (unsigned it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(bar, phase);
+                const unsigned long long t0 = global_ns();
+                for (unsigned it = 0; it < kWaitLimit && !done; ++it) {
+                    done = mbar_try_wait(bar, phase);
+                    if (!done && (it & 63u) == 63u && global_ns() - t0 > kWaitNs) break;
+                }
                 phase ^= 1u;
                 timed_out = __syncthreads_or(!done) != 0;
                 tc_fence_after();
@@ -496,18 +508,398 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
     }
 }
 
-template <typename T, int CUT>
-const void *pick_per(int periodic)
+// ---------------------------------------------------------------------------------------
+// Pipelined variant.  Three warp roles overlap the work of consecutive N tiles:
+//   warps 0-3  epilogue: thread t owns accumulator row t; drains one of two TMEM accumulators
+//              (tcgen05.ld -> output type -> staging row -> cp.async.bulk) while the other fills;
+//   warps 4-7  producer: per item builds atoms and per-axis tables, then for every step
+//              (N tile, K chunk) writes the A and B operands of one of two shared-memory stages;
+//   warp 8     MMA: one thread issues the tcgen05.mma pair of each step and commits to the
+//              stage's "empty" barrier and, after a tile's last K chunk, to the accumulator's
+//              "full" barrier.
+// All three walk the same (item, N tile, K chunk) sequence, so every handoff is a
+// full/empty mbarrier pair with phase parities derived from a step counter.  Waits are
+// bounded: a role that gives up raises a shared flag the others poll, then all drain and
+// the CTA frees its tensor memory.
+constexpr int kPipeStages = 2;
+constexpr int kPipeThreads = 288;  // 9 warps
+
+struct PipeLayout {
+    int bars, tmem, flag, atoms, stage0, stage_bytes, a_bytes, gy, gz, out, out_stride, total;
+};
+
+__host__ __device__ inline PipeLayout pipe_layout(int ny, int nz, int n_tile, int esz)
 {
+    PipeLayout L;
+    int o = 0;
+    L.bars = o;  // b_full[2], b_empty[2], acc_full[2], acc_empty[2]
+    o += 8 * 8;
+    L.tmem = o;
+    o += 8;
+    L.flag = o;
+    o += 8;
+    o = align_up(o, 128);
+    L.atoms = o;
+    o += kKC * 2 * 16;
+    o = align_up(o, 1024);
+    L.a_bytes = kRows * kKC * 2;
+    L.stage_bytes = align_up(L.a_bytes + n_tile * kKC * 2, 1024);
+    L.stage0 = o;
+    o += kPipeStages * L.stage_bytes;
+    L.gy = o;
+    o += ny * kTab * 4;
+    o = align_up(o, 128);
+    L.gz = o;
+    o += nz * kTab * 4;
+    o = align_up(o, 128);
+    L.out = o;
+    L.out_stride = n_tile * esz + 16;
+    o += kRows * L.out_stride;
+    L.total = align_up(o, 128);
+    return L;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void producer_sync()
+{
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+}
+
+// True for every producer thread iff it is true for all of them (named barrier 1, 128
+// threads), so the producers always take the same branch after a bounded wait.
+__device__ __forceinline__ bool producers_all(bool v)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.and.pred q, 1, 128, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v)
+        : "memory");
+    return r != 0u;
+}
+
+// Bounded wait on `parity`; false if it gave up or another role already did.
+__device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatile int *flag)
+{
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0; it < kWaitLimit; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 63u) == 63u && (*flag || global_ns() - t0 > kWaitNs)) break;
+    }
+    *flag = 1;
+    return false;
+}
+
+struct PipeItem {
+    int b, m0, a0, a1, n_kc;
+    float ox, oy, oz, hx, hy, hz;
+    unsigned bad;  // PG_DEVERR_* bits of this molecule (its grid is then all zeros)
+};
+
+__device__ __forceinline__ PipeItem pipe_item(const SeparableArgs &A, long long item)
+{
+    const Geometry &G = A.geo;
+    PipeItem it;
+    it.b = (int)(item / A.m_tiles);
+    it.m0 = (int)(item % A.m_tiles) * kRows;
+    it.a0 = __ldg(A.in.mol_off + it.b);
+    it.a1 = __ldg(A.in.mol_off + it.b + 1);
+    it.ox = __ldg(A.in.origin + 3 * it.b);
+    it.oy = __ldg(A.in.origin + 3 * it.b + 1);
+    it.oz = __ldg(A.in.origin + 3 * it.b + 2);
+    it.hx = __ldg(A.in.spacing + 3 * it.b);
+    it.hy = __ldg(A.in.spacing + 3 * it.b + 1);
+    it.hz = __ldg(A.in.spacing + 3 * it.b + 2);
+    const bool off_ok = (it.a0 >= 0) && (it.a0 <= it.a1) && (it.a1 <= G.n_atoms);
+    const bool sp_ok = (it.hx > 0.0f) && (it.hy > 0.0f) && (it.hz > 0.0f) &&
+                       (it.hx < INFINITY) && (it.hy < INFINITY) && (it.hz < INFINITY);
+    it.bad = (off_ok ? 0u : PG_DEVERR_OFFSETS) | (sp_ok ? 0u : PG_DEVERR_SPACING);
+    if (it.bad) it.a0 = it.a1 = 0;
+    const int n = it.a1 - it.a0;
+    it.n_kc = n > 0 ? (n + kKC - 1) / kKC : 1;
+    return it;
+}
+
+template <typename T, int CUT, bool PER>
+__global__ void __launch_bounds__(kPipeThreads, 2) separable_pipe_kernel(const SeparableArgs A)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const Geometry &G = A.geo;
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5;
+    const int lane = tid & 31;
+    const int n_tile = A.n_tile;
+    const PipeLayout L = pipe_layout(G.ny, G.nz, n_tile, (int)sizeof(T));
+    const uint32_t bars = smem_u32(smem + L.bars);
+    auto b_full = [&](int s) { return bars + 8u * s; };
+    auto b_empty = [&](int s) { return bars + 8u * (2 + s); };
+    auto acc_full = [&](int s) { return bars + 8u * (4 + s); };
+    auto acc_empty = [&](int s) { return bars + 8u * (6 + s); };
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L.tmem);
+    volatile int *flag = reinterpret_cast<volatile int *>(smem + L.flag);
+
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(b_full(s), 128);
+            mbar_init(b_empty(s), 1);
+            mbar_init(acc_full(s), 1);
+            mbar_init(acc_empty(s), 128);
+        }
+        *flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(smem_u32(tmem_slot), (uint32_t)(2 * n_tile));
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int M = G.C * G.nx;
+    const int N = G.ny * G.nz;
+    const int n_chunks = (N + n_tile - 1) / n_tile;
+    const long long n_items = (long long)G.n_mol * A.m_tiles;
+
+    if (warp >= 4 && warp < 8) {
+        // ------------------------------------------------------------------ producer
+        const int p = tid - 128;
+        float4 *atom_pos = reinterpret_cast<float4 *>(smem + L.atoms);
+        float4 *atom_aux = atom_pos + kKC;
+        float *tgy = reinterpret_cast<float *>(smem + L.gy);
+        float *tgz = reinterpret_cast<float *>(smem + L.gz);
+        long long stage_item[kPipeStages] = {-1, -1};
+        unsigned step = 0;
+        bool ok = true;
+        for (long long item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+            const PipeItem it = pipe_item(A, item);
+            if (it.bad && p == 0 && it.m0 == 0) atomicOr(A.err, it.bad);
+            const float Lx = G.nx * it.hx, Ly = G.ny * it.hy, Lz = G.nz * it.hz;
+            const float iLx = 1.0f / Lx, iLy = 1.0f / Ly, iLz = 1.0f / Lz;
+            const int R = it.m0 + p;
+            const bool row_ok = R < M;
+            const int row_c = row_ok ? R / G.nx : -2;
+            const int row_x = row_ok ? R - (R / G.nx) * G.nx : 0;
+            const float vx = fmaf((float)row_x + 0.5f, it.hx, it.ox);
+            for (int nc = 0; nc < n_chunks && ok; ++nc) {
+                const int n0 = nc * n_tile;
+                for (int kc = 0; kc < it.n_kc && ok; ++kc, ++step) {
+                    const int s = (int)(step % kPipeStages);
+                    const uint32_t ph = (step / kPipeStages) & 1u;
+                    const bool got = pipe_wait(b_empty(s), ph ^ 1u, flag);
+                    if (!producers_all(got)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *sa = smem + L.stage0 + s * L.stage_bytes;
+                    unsigned char *sb = sa + L.a_bytes;
+                    const bool new_atoms = (nc == 0 && kc == 0) || it.n_kc > 1;
+                    if (new_atoms) {
+                        producer_sync();  // every producer is done reading the old tables
+                        if (p < kKC) {
+                            const int ai = it.a0 + kc * kKC + p;
+                            float4 pos = make_float4(0.f, 0.f, 0.f, 0.f);
+                            float4 aux = make_float4(0.f, -1.f, 0.f, 0.f);
+                            if (ai < it.a1) {
+                                const int e = __ldg(A.in.elem + ai);
+                                if ((unsigned)e < (unsigned)G.C) {
+                                    pos = make_float4(__ldg(A.in.coords + 3 * ai),
+                                                      __ldg(A.in.coords + 3 * ai + 1),
+                                                      __ldg(A.in.coords + 3 * ai + 2), G.q[e]);
+                                    aux = make_float4(G.r2[e], (float)e, 0.f, 0.f);
+                                } else if (it.m0 == 0) {
+                                    atomicOr(A.err, PG_DEVERR_ELEMENT);
+                                }
+                            }
+                            atom_pos[p] = pos;
+                            atom_aux[p] = aux;
+                        }
+                        producer_sync();
+                        for (int i = p; i < G.ny * kKC; i += 128) {
+                            const int y = i / kKC, j = i - (i / kKC) * kKC;
+                            const float4 q4 = atom_pos[j];
+                            float v = 0.0f;
+                            if (atom_aux[j].y >= 0.0f) {
+                                float d = fmaf((float)y + 0.5f, it.hy, it.oy) - q4.y;
+                                if (PER) d = wrap(d, Ly, iLy);
+                                v = axis_factor<CUT>(d, q4.w, atom_aux[j].x);
+                            }
+                            tgy[y * kTab + j] = v;
+                        }
+                        for (int i = p; i < G.nz * kKC; i += 128) {
+                            const int z = i / kKC, j = i - (i / kKC) * kKC;
+                            const float4 q4 = atom_pos[j];
+                            float v = 0.0f;
+                            if (atom_aux[j].y >= 0.0f) {
+                                float d = fmaf((float)z + 0.5f, it.hz, it.oz) - q4.z;
+                                if (PER) d = wrap(d, Lz, iLz);
+                                v = axis_factor<CUT>(d, q4.w, atom_aux[j].x);
+                            }
+                            tgz[z * kTab + j] = v;
+                        }
+                        producer_sync();
+                    }
+                    // A tile: rewritten unless this stage already holds this item's A (one
+                    // K chunk per item).
+                    if (it.n_kc > 1 || stage_item[s] != item) {
+#pragma unroll
+                        for (int jg = 0; jg < kKC / 8; ++jg) {
+                            float v[8];
+#pragma unroll
+                            for (int t = 0; t < 8; ++t) {
+                                const int j = jg * 8 + t;
+                                const float4 q4 = atom_pos[j];
+                                const float4 aux = atom_aux[j];
+                                v[t] = 0.0f;
+                                if (row_ok && (int)aux.y == row_c) {
+                                    float d = vx - q4.x;
+                                    if (PER) d = wrap(d, Lx, iLx);
+                                    v[t] = axis_factor<CUT>(d, q4.w, aux.x);
+                                }
+                            }
+                            *reinterpret_cast<uint4 *>(sa + (p >> 3) * 512 + jg * 128 +
+                                                       (p & 7) * 16) =
+                                make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                                           pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+                        }
+                        stage_item[s] = it.n_kc > 1 ? -1 : item;
+                    }
+                    // B tile (see the single-stage kernel for the layout).
+                    for (int qi = p; qi < n_tile * (kKC / 8); qi += 128) {
+                        const int nl = (qi >> 5) * 8 + (qi & 7);
+                        const int kg = (qi >> 3) & 3;
+                        const int n = n0 + nl;
+                        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+                        if (n < N) {
+                            const int y = n / G.nz, z = n - (n / G.nz) * G.nz;
+                            const float4 *gy4 =
+                                reinterpret_cast<const float4 *>(tgy + y * kTab + kg * 8);
+                            const float4 *gz4 =
+                                reinterpret_cast<const float4 *>(tgz + z * kTab + kg * 8);
+                            const float4 y0 = gy4[0], y1 = gy4[1], z0 = gz4[0], z1 = gz4[1];
+                            w = make_uint4(pack_bf16x2(y0.x * z0.x, y0.y * z0.y),
+                                           pack_bf16x2(y0.z * z0.z, y0.w * z0.w),
+                                           pack_bf16x2(y1.x * z1.x, y1.y * z1.y),
+                                           pack_bf16x2(y1.z * z1.z, y1.w * z1.w));
+                        }
+                        *reinterpret_cast<uint4 *>(sb + qi * 16) = w;
+                    }
+                    fence_proxy_async_smem();
+                    mbar_arrive(b_full(s));
+                }
+            }
+        }
+    } else if (warp == 8) {
+        // ------------------------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            const uint32_t idesc = instr_desc(n_tile);
+            unsigned step = 0, tile = 0;
+            bool ok = true;
+            for (long long item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+                const PipeItem it = pipe_item(A, item);
+                for (int nc = 0; nc < n_chunks && ok; ++nc, ++tile) {
+                    const int buf = (int)(tile & 1u);
+                    const uint32_t aph = (tile >> 1) & 1u;
+                    for (int kc = 0; kc < it.n_kc && ok; ++kc, ++step) {
+                        const int s = (int)(step % kPipeStages);
+                        const uint32_t ph = (step / kPipeStages) & 1u;
+                        if (!pipe_wait(b_full(s), ph, flag)) {
+                            ok = false;
+                            break;
+                        }
+                        if (kc == 0 && !pipe_wait(acc_empty(buf), aph ^ 1u, flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(smem + L.stage0 + s * L.stage_bytes);
+                        const uint32_t sb = sa + L.a_bytes;
+#pragma unroll
+                        for (int k = 0; k < kKC / 16; ++k)
+                            mma_bf16_f32(tmem + buf * n_tile, smem_desc(sa + k * 256, 128, 512),
+                                         smem_desc(sb + k * 256, 128, 512), idesc,
+                                         (kc > 0 || k > 0) ? 1u : 0u);
+                        mma_commit(b_empty(s));
+                        if (kc == it.n_kc - 1) mma_commit(acc_full(buf));
+                    }
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------------------------ epilogue
+        T *out = reinterpret_cast<T *>(A.out);
+        unsigned char *srow = smem + L.out + tid * L.out_stride;
+        const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
+        unsigned tile = 0;
+        bool ok = true;
+        for (long long item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
+            const PipeItem it = pipe_item(A, item);
+            const int R = it.m0 + tid;
+            const bool row_ok = R < M;
+            for (int nc = 0; nc < n_chunks && ok; ++nc, ++tile) {
+                const int buf = (int)(tile & 1u);
+                const uint32_t ph = (tile >> 1) & 1u;
+                // tcgen05.ld is warp-collective: the whole warp continues or stops together.
+                if (!__all_sync(0xffffffffu, pipe_wait(acc_full(buf), ph, flag))) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                bulk_wait_read_all();
+                for (int cb = 0; cb < n_tile; cb += 32) {
+                    uint32_t r[32];
+                    tmem_ld32(tmem_row + buf * n_tile + cb, r);
+                    tmem_ld_wait();
+                    store_row_chunk<T>(srow + cb * (int)sizeof(T), r);
+                }
+                tc_fence_before();
+                mbar_arrive(acc_empty(buf));
+                if (row_ok) {
+                    fence_proxy_async_smem();
+                    const int n0 = nc * n_tile;
+                    const int cols = min(n_tile, N - n0);
+                    T *dst = out + ((long long)it.b * M + R) * (long long)N + n0;
+                    bulk_store(dst, smem_u32(srow), (uint32_t)(cols * (int)sizeof(T)));
+                    bulk_commit();
+                }
+            }
+        }
+        bulk_wait_all();
+    }
+
+    if (tid == 0 && *flag) atomicOr(A.err, PG_DEVERR_TIMEOUT);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem, (uint32_t)(2 * n_tile));
+    }
+}
+
+template <typename T, int CUT>
+const void *pick_per(int periodic, bool pipe)
+{
+    if (pipe)
+        return periodic ? (const void *)separable_pipe_kernel<T, CUT, true>
+                        : (const void *)separable_pipe_kernel<T, CUT, false>;
     return periodic ? (const void *)separable_kernel<T, CUT, true>
                     : (const void *)separable_kernel<T, CUT, false>;
 }
 
 template <typename T>
-const void *pick_cut(int cutoff, int periodic)
+const void *pick_cut(int cutoff, int periodic, bool pipe)
 {
-    return cutoff == PG_CUTOFF_BOX ? pick_per<T, PG_CUTOFF_BOX>(periodic)
-                                   : pick_per<T, PG_CUTOFF_NONE>(periodic);
+    return cutoff == PG_CUTOFF_BOX ? pick_per<T, PG_CUTOFF_BOX>(periodic, pipe)
+                                   : pick_per<T, PG_CUTOFF_NONE>(periodic, pipe);
 }
 
 }  // namespace
@@ -528,20 +920,26 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
 {
     if (!separable_supported(a0.geo, dtype)) return cudaErrorNotSupported;
     SeparableArgs a = a0;
+    const bool pipe = t.separable_simple == 0;
     int n_tile = t.n_tile;
     if (n_tile != 64 && n_tile != 128 && n_tile != 256) n_tile = 128;
     const int esz = dtype == PG_F32 ? 4 : 2;
+    auto bytes = [&](int nt) {
+        return pipe ? pipe_layout(a.geo.ny, a.geo.nz, nt, esz).total
+                    : sep_layout(a.geo.ny, a.geo.nz, nt, esz).total;
+    };
     // Largest requested tile whose shared-memory footprint fits one SM's 227 KB.
-    while (n_tile > 64 && sep_layout(a.geo.ny, a.geo.nz, n_tile, esz).total > 227 * 1024)
-        n_tile /= 2;
-    const SepLayout L = sep_layout(a.geo.ny, a.geo.nz, n_tile, esz);
-    if (L.total > 227 * 1024) return cudaErrorNotSupported;
+    while (n_tile > 64 && bytes(n_tile) > 227 * 1024) n_tile /= 2;
+    const int smem = bytes(n_tile);
+    if (smem > 227 * 1024) return cudaErrorNotSupported;
     a.n_tile = n_tile;
     a.m_tiles = (a.geo.C * a.geo.nx + kRows - 1) / kRows;
-    const void *f = dtype == PG_F32   ? pick_cut<float>(a.geo.cutoff, a.geo.periodic)
-                    : dtype == PG_F16 ? pick_cut<__half>(a.geo.cutoff, a.geo.periodic)
-                                      : pick_cut<__nv_bfloat16>(a.geo.cutoff, a.geo.periodic);
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    const void *f = dtype == PG_F32   ? pick_cut<float>(a.geo.cutoff, a.geo.periodic, pipe)
+                    : dtype == PG_F16 ? pick_cut<__half>(a.geo.cutoff, a.geo.periodic, pipe)
+                                      : pick_cut<__nv_bfloat16>(a.geo.cutoff, a.geo.periodic, pipe);
+    const int threads = pipe ? kPipeThreads : kRows;
+    const int tmem_cols = pipe ? 2 * n_tile : n_tile;
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
@@ -558,10 +956,10 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
         return e;
     cudaFuncAttributes fa;
     if ((e = cudaFuncGetAttributes(&fa, f)) != cudaSuccess) return e;
-    const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * kRows;
-    int per_sm = smem_sm / (L.total + smem_reserved);
+    const int regs_cta = ((fa.numRegs + 7) / 8 * 8) * (threads + 31) / 32 * 32;
+    int per_sm = smem_sm / (smem + smem_reserved);
     if (regs_cta > 0 && regs_sm / regs_cta < per_sm) per_sm = regs_sm / regs_cta;
-    if (512 / n_tile < per_sm) per_sm = 512 / n_tile;
+    if (512 / tmem_cols < per_sm) per_sm = 512 / tmem_cols;
     if (per_sm < 1) return cudaErrorNotSupported;
     if (t.blocks_per_sm > 0 && t.blocks_per_sm < per_sm) per_sm = t.blocks_per_sm;
     const long long items = (long long)a.geo.n_mol * a.m_tiles;
@@ -570,8 +968,8 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
     if (blocks < 1) blocks = 1;
     kl->func = f;
     kl->grid = dim3((unsigned)blocks);
-    kl->block = dim3(kRows);
-    kl->smem = (size_t)L.total;
+    kl->block = dim3(threads);
+    kl->smem = (size_t)smem;
     set_args(kl, a);
     return cudaSuccess;
 }

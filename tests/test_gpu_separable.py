@@ -29,14 +29,15 @@ def pg():
     return api
 
 
-def sep(pg, wl, dtype="f16", batch=None, n_tile=None):
+def sep(pg, wl, dtype="f16", batch=None, n_tile=None, simple=0):
     batch = wl.batch if batch is None else batch
     db = pg.DeviceBatch.from_numpy(batch)
     grid = pg.Grid.from_workload(wl)
-    if n_tile is None:
+    if n_tile is None and not simple:
         G = pg.voxelize(db, grid, dtype=dtype, path="separable")
     else:
-        G = pg.voxelize_tuned(db, grid, {"path": 2, "n_tile": n_tile}, dtype=dtype)
+        G = pg.voxelize_tuned(db, grid, {"path": 2, "n_tile": n_tile or 128,
+                                         "separable_simple": simple}, dtype=dtype)
     assert pg.sync_status() == 0
     return G.float().cpu().numpy()
 
@@ -82,11 +83,26 @@ def test_partial_tiles(pg, shape):
                abs_tol=ABS_TOL["f16"])
 
 
+@pytest.mark.parametrize("simple", [0, 1])
 @pytest.mark.parametrize("n_tile", [64, 128, 256])
-def test_every_tile_width(pg, n_tile):
+def test_every_tile_width_and_variant(pg, n_tile, simple):
     wl = small("box", False, n_mol=3)
-    grid_check(sep(pg, wl, n_tile=n_tile), oracle.Problem.from_workload(wl), SEPARABLE_TOL,
-               abs_tol=ABS_TOL["f16"])
+    grid_check(sep(pg, wl, n_tile=n_tile, simple=simple), oracle.Problem.from_workload(wl),
+               SEPARABLE_TOL, abs_tol=ABS_TOL["f16"])
+
+
+def test_pipelined_and_single_stage_agree_bitwise(pg):
+    # Same BF16 operands, same accumulation order: identical bits from both kernels, also
+    # with K chunks past 32 atoms and partial tiles.
+    rng = np.random.default_rng(23)
+    pos = [8.0 + rng.uniform(-4, 4, (n, 3)) for n in (3, 40, 29, 70)]
+    el = [rng.integers(0, 5, n) for n in (3, 40, 29, 70)]
+    nb = synth._pack(pos, el, np.zeros((4, 3)), np.full((4, 3), 0.5))
+    for shape in ((32, 32, 32), (20, 12, 20)):
+        wl = small("none", False, shape=shape)
+        a = sep(pg, wl, batch=nb, n_tile=128, simple=0)
+        b = sep(pg, wl, batch=nb, n_tile=128, simple=1)
+        assert np.array_equal(a, b)
 
 
 def test_more_than_32_atoms_accumulates_k_chunks(pg):
