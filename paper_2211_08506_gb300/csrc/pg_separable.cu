@@ -589,8 +589,10 @@ __device__ __forceinline__ bool producers_all(bool v)
 // Bounded wait on `parity`; false if it gave up or another role already did.
 __device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatile int *flag)
 {
+    if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned it = 0; it < kWaitLimit; ++it) {
+        __nanosleep(32);  // back off so waiting warps leave issue slots to working ones
         if (mbar_try_wait(bar, parity)) return true;
         if ((it & 63u) == 63u && (*flag || global_ns() - t0 > kWaitNs)) break;
     }
@@ -678,6 +680,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) separable_pipe_kernel(const S
         float *tgy = reinterpret_cast<float *>(smem + L.gy);
         float *tgz = reinterpret_cast<float *>(smem + L.gz);
         long long stage_item[kPipeStages] = {-1, -1};
+        const int dy32 = 32 / G.nz, dz32 = 32 - (32 / G.nz) * G.nz;
         unsigned step = 0;
         bool ok = true;
         for (long long item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
@@ -773,25 +776,35 @@ __global__ void __launch_bounds__(kPipeThreads, 2) separable_pipe_kernel(const S
                         }
                         stage_item[s] = it.n_kc > 1 ? -1 : item;
                     }
-                    // B tile (see the single-stage kernel for the layout).
-                    for (int qi = p; qi < n_tile * (kKC / 8); qi += 128) {
-                        const int nl = (qi >> 5) * 8 + (qi & 7);
-                        const int kg = (qi >> 3) & 3;
-                        const int n = n0 + nl;
-                        uint4 w = make_uint4(0u, 0u, 0u, 0u);
-                        if (n < N) {
-                            const int y = n / G.nz, z = n - (n / G.nz) * G.nz;
-                            const float4 *gy4 =
-                                reinterpret_cast<const float4 *>(tgy + y * kTab + kg * 8);
-                            const float4 *gz4 =
-                                reinterpret_cast<const float4 *>(tgz + z * kTab + kg * 8);
-                            const float4 y0 = gy4[0], y1 = gy4[1], z0 = gz4[0], z1 = gz4[1];
-                            w = make_uint4(pack_bf16x2(y0.x * z0.x, y0.y * z0.y),
-                                           pack_bf16x2(y0.z * z0.z, y0.w * z0.w),
-                                           pack_bf16x2(y1.x * z1.x, y1.y * z1.y),
-                                           pack_bf16x2(y1.z * z1.z, y1.w * z1.w));
+                    // B tile (layout as in the single-stage kernel).  Producer p always
+                    // writes atom group kg = (p/8)%4 of columns nl = (p/32)*8 + p%8 + 32i, so
+                    // its (y, z) advance by a fixed step: no division per chunk.
+                    {
+                        const int kg = (p >> 3) & 3;
+                        int n = n0 + (p >> 5) * 8 + (p & 7);
+                        int y = n / G.nz, z = n - (n / G.nz) * G.nz;
+                        for (int qi = p; qi < n_tile * (kKC / 8); qi += 128) {
+                            uint4 w = make_uint4(0u, 0u, 0u, 0u);
+                            if (n < N) {
+                                const float4 *gy4 =
+                                    reinterpret_cast<const float4 *>(tgy + y * kTab + kg * 8);
+                                const float4 *gz4 =
+                                    reinterpret_cast<const float4 *>(tgz + z * kTab + kg * 8);
+                                const float4 y0 = gy4[0], y1 = gy4[1], z0 = gz4[0], z1 = gz4[1];
+                                w = make_uint4(pack_bf16x2(y0.x * z0.x, y0.y * z0.y),
+                                               pack_bf16x2(y0.z * z0.z, y0.w * z0.w),
+                                               pack_bf16x2(y1.x * z1.x, y1.y * z1.y),
+                                               pack_bf16x2(y1.z * z1.z, y1.w * z1.w));
+                            }
+                            *reinterpret_cast<uint4 *>(sb + qi * 16) = w;
+                            n += 32;
+                            z += dz32;
+                            y += dy32;
+                            if (z >= G.nz) {
+                                z -= G.nz;
+                                ++y;
+                            }
                         }
-                        *reinterpret_cast<uint4 *>(sb + qi * 16) = w;
                     }
                     fence_proxy_async_smem();
                     mbar_arrive(b_full(s));
@@ -855,11 +868,13 @@ __global__ void __launch_bounds__(kPipeThreads, 2) separable_pipe_kernel(const S
                 }
                 tc_fence_after();
                 bulk_wait_read_all();
-                for (int cb = 0; cb < n_tile; cb += 32) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem_row + buf * n_tile + cb, r);
+                for (int cb = 0; cb < n_tile; cb += 64) {
+                    uint32_t r0[32], r1[32];
+                    tmem_ld32(tmem_row + buf * n_tile + cb, r0);
+                    tmem_ld32(tmem_row + buf * n_tile + cb + 32, r1);
                     tmem_ld_wait();
-                    store_row_chunk<T>(srow + cb * (int)sizeof(T), r);
+                    store_row_chunk<T>(srow + cb * (int)sizeof(T), r0);
+                    store_row_chunk<T>(srow + (cb + 32) * (int)sizeof(T), r1);
                 }
                 tc_fence_before();
                 mbar_arrive(acc_empty(buf));
