@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units (not part of the ABI).
 #pragma once
 
+#include <cuda.h>  // CUtensorMap (type only; the encoder is fetched at run time)
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -58,6 +59,7 @@ struct BackwardArgs {
 };
 
 struct SeparableArgs {
+    CUtensorMap out_map;  // 3D [n_mol][C nx][ny nz] view of `out` for TMA stores (pipelined)
     Inputs in;
     void *out;
     unsigned *err;
@@ -73,7 +75,7 @@ struct KernelLaunch {
     dim3 grid, block;
     size_t smem = 0;
     size_t args_size = 0;
-    alignas(16) unsigned char args[2048];
+    alignas(64) unsigned char args[2048];
     void *params[1];
 };
 

@@ -19,17 +19,21 @@
 // CTA builds per-axis tables and the A tile once, then for each N tile of n_tile columns:
 //   builds B (n_tile x 32 atoms, BF16) -> one thread issues two K=16 tcgen05.mma into a TMEM
 //   accumulator of n_tile FP32 columns and commits to an mbarrier -> every thread loads its
-//   row with tcgen05.ld, converts to the output type, writes it to a padded shared staging
-//   row and sends it to global memory with one cp.async.bulk (bulk-async store).
+//   row with tcgen05.ld, converts to the output type and writes it to a padded shared
+//   staging row -> each warp then writes its 32 rows to global memory with coalesced
+//   16-byte stores (one bulk copy per row was measured to be limited by the rate at which
+//   the copy engine accepts requests).
 // Molecules with more than 32 atoms loop over 32-atom K chunks, accumulating in TMEM.
 // Both operands use the K-major, no-swizzle canonical layout: 8-row x 16-byte core matrices,
 // 128 bytes apart along K (leading byte offset) and 512 bytes apart along M/N (stride byte
 // offset).
 //
-// Every mbarrier wait is bounded; on expiry the kernel sets PG_DEVERR_TIMEOUT, drains its
-// own bulk stores, frees its tensor memory and returns.
+// Every mbarrier wait is bounded; on expiry the kernel sets PG_DEVERR_TIMEOUT, frees its
+// tensor memory and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
+
+#include <type_traits>
 
 #include "pg_internal.h"
 
@@ -203,11 +207,15 @@ __device__ __forceinline__ void tmem_ld_wait()
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void bulk_store(void *gdst, uint32_t ssrc, uint32_t bytes)
+// TMA tensor store of one box from shared memory; coordinates innermost first.
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, uint32_t src, int x, int y,
+                                             int z)
 {
-    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst),
-                 "r"(ssrc), "r"(bytes)
-                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(src), "r"(x), "r"(y), "r"(z)
+        : "memory");
 }
 
 __device__ __forceinline__ void bulk_commit()
@@ -297,6 +305,78 @@ __device__ __forceinline__ void store_row_chunk<__nv_bfloat16>(unsigned char *ds
     uint4 *d = reinterpret_cast<uint4 *>(dst);
 #pragma unroll
     for (int i = 0; i < 4; ++i) d[i] = make_uint4(p[4 * i], p[4 * i + 1], p[4 * i + 2], p[4 * i + 3]);
+}
+
+// Staging of 32 accumulator columns [cb, cb+32) of row `lane` for a TMA store box of
+// 32 rows x 128 bytes with the 128-byte swizzle: 16-byte chunk j of a row sits at chunk
+// j ^ (row % 8), so the 8 rows sharing a bank group write to 8 different chunks.
+template <typename T>
+__device__ __forceinline__ void stage_swizzled(unsigned char *warp_stage, int lane, int cb,
+                                               const uint32_t (&r)[32])
+{
+    constexpr int chunks = 32 * (int)sizeof(T) / 16;  // 16-byte chunks in 32 columns
+    uint32_t p[4 * chunks];
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int i = 0; i < 32; ++i) p[i] = r[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if constexpr (std::is_same<T, __half>::value) {
+                __half2 h = __floats2half2_rn(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+                p[i] = *reinterpret_cast<uint32_t *>(&h);
+            } else {
+                p[i] = pack_bf16x2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+            }
+        }
+    }
+    const int c0 = cb * (int)sizeof(T) / 16;  // first 16-byte chunk of this column block
+#pragma unroll
+    for (int i = 0; i < chunks; ++i) {
+        const int c = c0 + i;
+        const int slab = c >> 3, j = c & 7;
+        *reinterpret_cast<uint4 *>(warp_stage + slab * 4096 + lane * 128 + ((j ^ (lane & 7)) << 4)) =
+            make_uint4(p[4 * i], p[4 * i + 1], p[4 * i + 2], p[4 * i + 3]);
+    }
+}
+
+// Coalesced write-out of one warp's 32 staged rows: row segment bytes are spread over lanes
+// 16 bytes each (several rows per step when a segment is shorter than 512 bytes), so every
+// store instruction covers whole 32-byte sectors.  Rows at or past M and columns at or past
+// N are skipped.  `stage` is the warp's first staging row, `stride` the staging row pitch.
+template <typename T>
+__device__ __forceinline__ void store_warp_rows(T *out, const unsigned char *stage, int stride,
+                                                int row0, int M, long long row_base, int N,
+                                                int n0, int n_tile, int lane)
+{
+    const int seg16 = n_tile * (int)sizeof(T) / 16;  // 16-byte pieces per row segment
+    const int cols = min(n_tile, N - n0);
+    const int valid16 = cols * (int)sizeof(T) / 16;
+    constexpr int per16 = 16 / (int)sizeof(T);      // elements per 16-byte piece
+    if (seg16 <= 32) {
+        const int rows_per_step = 32 / seg16;
+        const int rr = lane / seg16, c16 = lane - (lane / seg16) * seg16;
+        for (int r = rr; r < 32; r += rows_per_step) {
+            const int R = row0 + r;
+            if (R < M && c16 < valid16) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(stage + r * stride + c16 * 16);
+                __stcs(reinterpret_cast<uint4 *>(out + (row_base + R) * (long long)N + n0 +
+                                                 c16 * per16),
+                       v);
+            }
+        }
+    } else {
+        for (int r = 0; r < 32; ++r) {
+            const int R = row0 + r;
+            if (R >= M) break;
+            for (int c16 = lane; c16 < valid16; c16 += 32) {
+                const uint4 v = *reinterpret_cast<const uint4 *>(stage + r * stride + c16 * 16);
+                __stcs(reinterpret_cast<uint4 *>(out + (row_base + R) * (long long)N + n0 +
+                                                 c16 * per16),
+                       v);
+            }
+        }
+    }
 }
 
 template <typename T, int CUT, bool PER>
@@ -480,8 +560,8 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                 tc_fence_after();
             }
             if (timed_out) break;
-            // Epilogue: TMEM row -> registers -> output type -> staging row -> bulk store.
-            bulk_wait_read_all();
+            // Epilogue: TMEM row -> registers -> output type -> staging row, then the warp
+            // writes its 32 rows out with coalesced stores.
             for (int cb = 0; cb < n_tile; cb += 32) {
                 uint32_t r[32];
                 tmem_ld32(tmem_row + cb, r);
@@ -489,17 +569,13 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                 store_row_chunk<T>(srow + cb * (int)sizeof(T), r);
             }
             tc_fence_before();
-            if (row_ok) {
-                fence_proxy_async_smem();
-                const int cols = min(n_tile, N - n0);
-                T *dst = out + ((long long)b * M + R) * (long long)N + n0;
-                bulk_store(dst, smem_u32(srow), (uint32_t)(cols * (int)sizeof(T)));
-                bulk_commit();
-            }
+            __syncwarp();
+            store_warp_rows<T>(out, smem + L.stage + warp * 32 * L.stage_stride, L.stage_stride,
+                               m0 + warp * 32, M, (long long)b * M, N, n0, n_tile, tid & 31);
+            __syncwarp();
         }
     }
     if (timed_out && tid == 0) atomicOr(A.err, PG_DEVERR_TIMEOUT);
-    bulk_wait_all();
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
@@ -511,7 +587,8 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
 // ---------------------------------------------------------------------------------------
 // Pipelined variant.  Three warp roles overlap the work of consecutive N tiles:
 //   warps 0-3  epilogue: thread t owns accumulator row t; drains one of two TMEM accumulators
-//              (tcgen05.ld -> output type -> staging row -> cp.async.bulk) while the other fills;
+//              (tcgen05.ld -> output type -> staging row -> coalesced stores) while the other
+//              fills;
 //   warps 4-7  producer: per item builds atoms and per-axis tables, then for every step
 //              (N tile, K chunk) writes the A and B operands of one of two shared-memory stages;
 //   warp 8     MMA: one thread issues the tcgen05.mma pair of each step and commits to the
@@ -551,11 +628,11 @@ __host__ __device__ inline PipeLayout pipe_layout(int ny, int nz, int n_tile, in
     o = align_up(o, 128);
     L.gz = o;
     o += nz * kTab * 4;
-    o = align_up(o, 128);
+    o = align_up(o, 1024);
     L.out = o;
-    L.out_stride = n_tile * esz + 16;
-    o += kRows * L.out_stride;
-    L.total = align_up(o, 128);
+    L.out_stride = (n_tile * esz / 128) * 4096;  // per warp: slabs of 32 rows x 128 bytes
+    o += 4 * L.out_stride;
+    L.total = align_up(o, 1024);
     return L;
 }
 
@@ -600,6 +677,23 @@ __device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatil
     return false;
 }
 
+// One lane of the warp polls the barrier; __syncwarp then orders the other lanes after its
+// acquire.  Returns the same value on every lane.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *flag)
+{
+    bool got = true;
+    if ((threadIdx.x & 31) == 0) got = pipe_wait(bar, parity, flag);
+    return __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+}
+
+// Every lane's prior shared-memory writes (and tcgen05 loads, fenced by the caller) are
+// ordered before one arrival made by lane 0.
+__device__ __forceinline__ void warp_arrive(uint32_t bar)
+{
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+}
+
 struct PipeItem {
     int b, m0, a0, a1, n_kc;
     float ox, oy, oz, hx, hy, hz;
@@ -631,7 +725,8 @@ __device__ __forceinline__ PipeItem pipe_item(const SeparableArgs &A, long long 
 }
 
 template <typename T, int CUT, bool PER>
-__global__ void __launch_bounds__(kPipeThreads, 2) separable_pipe_kernel(const SeparableArgs A)
+__global__ void __launch_bounds__(kPipeThreads, 2)
+    separable_pipe_kernel(const __grid_constant__ SeparableArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     const Geometry &G = A.geo;
@@ -650,10 +745,10 @@ __global__ void __launch_bounds__(kPipeThreads, 2) separable_pipe_kernel(const S
 
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
-            mbar_init(b_full(s), 128);
-            mbar_init(b_empty(s), 1);
-            mbar_init(acc_full(s), 1);
-            mbar_init(acc_empty(s), 128);
+            mbar_init(b_full(s), 4);     // one elected lane per producer warp
+            mbar_init(b_empty(s), 1);    // tcgen05.commit
+            mbar_init(acc_full(s), 1);   // tcgen05.commit
+            mbar_init(acc_empty(s), 4);  // one elected lane per epilogue warp
         }
         *flag = 0;
         fence_barrier_init();
@@ -698,7 +793,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) separable_pipe_kernel(const S
                 for (int kc = 0; kc < it.n_kc && ok; ++kc, ++step) {
                     const int s = (int)(step % kPipeStages);
                     const uint32_t ph = (step / kPipeStages) & 1u;
-                    const bool got = pipe_wait(b_empty(s), ph ^ 1u, flag);
+                    const bool got = warp_wait(b_empty(s), ph ^ 1u, flag);
                     if (!producers_all(got)) {
                         ok = false;
                         break;
@@ -807,7 +902,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2) separable_pipe_kernel(const S
                         }
                     }
                     fence_proxy_async_smem();
-                    mbar_arrive(b_full(s));
+                    warp_arrive(b_full(s));
                 }
             }
         }
@@ -849,46 +944,52 @@ __global__ void __launch_bounds__(kPipeThreads, 2) separable_pipe_kernel(const S
         }
     } else {
         // ------------------------------------------------------------------ epilogue
-        T *out = reinterpret_cast<T *>(A.out);
-        unsigned char *srow = smem + L.out + tid * L.out_stride;
+        unsigned char *wstage = smem + L.out + warp * L.out_stride;
+        const int slabs = n_tile * (int)sizeof(T) / 128;
+        const int slab_cols = 128 / (int)sizeof(T);
         const uint32_t tmem_row = tmem + ((uint32_t)(warp * 32) << 16);
         unsigned tile = 0;
         bool ok = true;
         for (long long item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
             const PipeItem it = pipe_item(A, item);
-            const int R = it.m0 + tid;
-            const bool row_ok = R < M;
             for (int nc = 0; nc < n_chunks && ok; ++nc, ++tile) {
                 const int buf = (int)(tile & 1u);
                 const uint32_t ph = (tile >> 1) & 1u;
-                // tcgen05.ld is warp-collective: the whole warp continues or stops together.
-                if (!__all_sync(0xffffffffu, pipe_wait(acc_full(buf), ph, flag))) {
+                // tcgen05.ld is warp-collective: the whole warp continues or stops together
+                // (warp_wait returns the same value on every lane).
+                if (!warp_wait(acc_full(buf), ph, flag)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                bulk_wait_read_all();
+                // The previous tile's TMA stores must have read this warp's staging.
+                if (lane == 0) bulk_wait_read_all();
+                __syncwarp();
                 for (int cb = 0; cb < n_tile; cb += 64) {
                     uint32_t r0[32], r1[32];
                     tmem_ld32(tmem_row + buf * n_tile + cb, r0);
                     tmem_ld32(tmem_row + buf * n_tile + cb + 32, r1);
                     tmem_ld_wait();
-                    store_row_chunk<T>(srow + cb * (int)sizeof(T), r0);
-                    store_row_chunk<T>(srow + (cb + 32) * (int)sizeof(T), r1);
+                    stage_swizzled<T>(wstage, lane, cb, r0);
+                    stage_swizzled<T>(wstage, lane, cb + 32, r1);
                 }
                 tc_fence_before();
-                mbar_arrive(acc_empty(buf));
-                if (row_ok) {
-                    fence_proxy_async_smem();
-                    const int n0 = nc * n_tile;
-                    const int cols = min(n_tile, N - n0);
-                    T *dst = out + ((long long)it.b * M + R) * (long long)N + n0;
-                    bulk_store(dst, smem_u32(srow), (uint32_t)(cols * (int)sizeof(T)));
+                fence_proxy_async_smem();
+                warp_arrive(acc_empty(buf));  // includes __syncwarp: the warp's rows are staged
+                // One TMA tensor store per 32-row x 128-byte slab; the tensor map clips rows
+                // past M and columns past N.  Boxes lying wholly outside are skipped.
+                const int row0 = it.m0 + warp * 32;
+                if (lane == 0 && row0 < M) {
+                    for (int sl = 0; sl < slabs; ++sl) {
+                        const int x = nc * n_tile + sl * slab_cols;
+                        if (x < N)
+                            tma_store_3d(&A.out_map, smem_u32(wstage + sl * 4096), x, row0, it.b);
+                    }
                     bulk_commit();
                 }
             }
         }
-        bulk_wait_all();
+        if (lane == 0) bulk_wait_all();
     }
 
     if (tid == 0 && *flag) atomicOr(A.err, PG_DEVERR_TIMEOUT);
@@ -930,10 +1031,45 @@ bool separable_supported(const Geometry &g, int dtype)
     return true;
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// 3D tensor map over the output, dims innermost first {N = ny nz, M = C nx, n_mol}; boxes of
+// 128 bytes x 32 rows x 1 molecule with the 128-byte swizzle.
+cudaError_t encode_out_map(SeparableArgs &a, int dtype)
+{
+    static EncodeTiledFn encode = nullptr;
+    if (!encode) {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return e != cudaSuccess ? e : cudaErrorNotSupported;
+        encode = reinterpret_cast<EncodeTiledFn>(fn);
+    }
+    const int esz = dtype == PG_F32 ? 4 : 2;
+    const CUtensorMapDataType dt = dtype == PG_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : dtype == PG_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t N = (cuuint64_t)a.geo.ny * a.geo.nz, M = (cuuint64_t)a.geo.C * a.geo.nx;
+    const cuuint64_t dims[3] = {N, M, (cuuint64_t)a.geo.n_mol};
+    const cuuint64_t strides[2] = {N * esz, N * M * esz};
+    const cuuint32_t box[3] = {(cuuint32_t)(128 / esz), 32, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode(&a.out_map, dt, 3, a.out, dims, strides, box, estr,
+                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorNotSupported;
+}
+
 cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &t, int sm_count,
                            KernelLaunch *kl)
 {
     if (!separable_supported(a0.geo, dtype)) return cudaErrorNotSupported;
+    if ((uintptr_t)a0.out % 16 != 0) return cudaErrorNotSupported;
     SeparableArgs a = a0;
     const bool pipe = t.separable_simple == 0;
     int n_tile = t.n_tile;
@@ -949,6 +1085,10 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
     if (smem > 227 * 1024) return cudaErrorNotSupported;
     a.n_tile = n_tile;
     a.m_tiles = (a.geo.C * a.geo.nx + kRows - 1) / kRows;
+    if (pipe) {
+        cudaError_t em = encode_out_map(a, dtype);
+        if (em != cudaSuccess) return em;
+    }
     const void *f = dtype == PG_F32   ? pick_cut<float>(a.geo.cutoff, a.geo.periodic, pipe)
                     : dtype == PG_F16 ? pick_cut<__half>(a.geo.cutoff, a.geo.periodic, pipe)
                                       : pick_cut<__nv_bfloat16>(a.geo.cutoff, a.geo.periodic, pipe);
