@@ -461,6 +461,8 @@ def run_profile(args, wl, dtype):
     """Plain launches for profiler captures: no tuning, no graph, no host-side extras.
     Prints a line marked "profile" (it is not a benchmark result)."""
     import torch
+
+    import synth
     from paper_2211_08506_gb300 import api
 
     grid = api.Grid.from_workload(wl)
@@ -469,8 +471,14 @@ def run_profile(args, wl, dtype):
     tuning = {"path": 2 if args.path == "separable" else 1, "block_threads": args.threads,
               "blocks_per_sm": 0, "store_hint": args.store_hint, "n_tile": args.n_tile,
               "chunk_planes": args.chunk_planes, "gather_only": args.gather_only}
+    W = grad = None
+    if wl.name == "differentiation":
+        W = torch.from_numpy(synth.loss_weights(wl)).cuda()
+        grad = torch.empty((wl.batch.n_atoms, 3), dtype=torch.float32, device="cuda")
     for _ in range(args.warmup + args.steps):
         api.voxelize_tuned(db, grid, tuning, dtype=dtype, out=out)
+        if W is not None:
+            api.voxelize_backward(db, grid, W, grad_coords=grad)
     torch.cuda.synchronize()
     assert api.sync_status() == 0
     print(json.dumps({"profile": True, "workload": wl.name, "n_mol": wl.batch.n_mol,

@@ -549,6 +549,7 @@ pg_status pg_voxelize_backward(const pg_batch *batch, const pg_grid *grid, int32
     a.grad_out = grad_out;
     a.grad_coords = grad_coords;
     a.err = d->err;
+    a.sched = d->take_slot();
     make_geometry(batch, grid, &a.geo);
     KernelLaunch kl;
     PG_CUDA(backward_plan(a, grad_dtype, d->sms, &kl), "backward_plan");

@@ -9,9 +9,9 @@
 // (The indicator is piecewise constant; its jump at the cutoff surface is not part of the
 // derivative.)
 //
-// One warp owns one atom and walks the voxels of the atom's cutoff box (clamped to the grid,
-// or wrapped for periodic cells), 32 voxels per step with z fastest so the reads of g are
-// coalesced.  Each lane keeps a partial sum; a fixed butterfly reduction combines them.  Each
+// One warp owns one atom at a time (atoms handed out from a per-launch counter) and walks the
+// voxels of the atom's cutoff box (clamped to the grid, or wrapped for periodic cells), 32
+// voxels per step with z fastest so the reads of g are coalesced.  Each lane keeps a partial sum; a fixed butterfly reduction combines them.  Each
 // atom's output is written by exactly one lane, so there are no atomics and the result is
 // deterministic.  Reads are ~(2 r_c / h)^3 voxels per atom: this kernel is latency-bound and
 // small next to the forward pass.
@@ -58,9 +58,11 @@ __device__ __forceinline__ void axis_support(float a, float o, float h, int n, f
         cnt = n;
         return;
     }
+    // Voxel centres o + (i + 1/2) h within rc of a (rc is already widened by a relative 1e-5,
+    // and 1e-3 of a voxel of slack covers the rounding of the bounds themselves).
     const float inv_h = 1.0f / h;
-    int l = (int)floorf((a - rc - o) * inv_h - 0.5f) - 1;
-    int u = (int)ceilf((a + rc - o) * inv_h - 0.5f) + 1;
+    int l = (int)fmaxf(ceilf((a - rc - o) * inv_h - 0.5f - 1e-3f), -1e8f);
+    int u = (int)fminf(floorf((a + rc - o) * inv_h - 0.5f + 1e-3f), 1e8f);
     if (PER) {
         if (u - l + 1 > n) u = l + n - 1;
     } else {
@@ -107,26 +109,43 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
 
     const long long plane = (long long)G.ny * G.nz;
     const long long grid_elems = (long long)G.nx * plane;
-    for (int b = blockIdx.x; b < G.n_mol; b += gridDim.x) {
+    const unsigned long long total_warps = (unsigned long long)gridDim.x * warps;
+    // Atoms of the batch, clamped to the array (bad offsets are flagged per atom below).
+    const int first = G.n_mol > 0 ? max(__ldg(A.in.mol_off), 0) : 0;
+    const int last = G.n_mol > 0 ? min(__ldg(A.in.mol_off + G.n_mol), G.n_atoms) : 0;
+    // Atoms are handed out one per grab from a per-launch counter (the last warp to retire
+    // resets it), so molecules of uneven size balance across the GPU.
+    while (true) {
+        unsigned long long grab = 0;
+        if (lane == 0) grab = atomicAdd(A.sched, 1ull);
+        grab = __shfl_sync(0xffffffffu, grab, 0);
+        const long long ga = (long long)first + (long long)grab;
+        if (G.n_mol == 0 || ga >= last) break;
+        const int a = (int)ga;
+        // Molecule of atom a: the last b with mol_off[b] <= a (offsets are checked below).
+        int lo = 0, hi = G.n_mol - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(A.in.mol_off + mid) <= a) lo = mid;
+            else hi = mid - 1;
+        }
+        const int b = lo;
         const int a0 = __ldg(A.in.mol_off + b), a1 = __ldg(A.in.mol_off + b + 1);
         const float ox = __ldg(A.in.origin + 3 * b), oy = __ldg(A.in.origin + 3 * b + 1),
                     oz = __ldg(A.in.origin + 3 * b + 2);
         const float hx = __ldg(A.in.spacing + 3 * b), hy = __ldg(A.in.spacing + 3 * b + 1),
                     hz = __ldg(A.in.spacing + 3 * b + 2);
-        const bool off_ok = (a0 >= 0) && (a0 <= a1) && (a1 <= G.n_atoms);
+        const bool off_ok = (a0 >= 0) && (a0 <= a) && (a < a1) && (a1 <= G.n_atoms);
         const bool sp_ok = (hx > 0.0f) && (hy > 0.0f) && (hz > 0.0f) && (hx < INFINITY) &&
                            (hy < INFINITY) && (hz < INFINITY);
-        if (!off_ok) {
-            if (threadIdx.x == 0) atomicOr(A.err, PG_DEVERR_OFFSETS);
-            continue;
-        }
         const float Lx = G.nx * hx, Ly = G.ny * hy, Lz = G.nz * hz;
         const float iLx = 1.0f / Lx, iLy = 1.0f / Ly, iLz = 1.0f / Lz;
-        for (int a = a0 + warp; a < a1; a += warps) {
+        {
             const int c = __ldg(A.in.elem + a);
-            if ((unsigned)c >= (unsigned)G.C || !sp_ok) {
+            if (!off_ok || (unsigned)c >= (unsigned)G.C || !sp_ok) {
                 if (lane == 0) {
-                    atomicOr(A.err, sp_ok ? PG_DEVERR_ELEMENT : PG_DEVERR_SPACING);
+                    atomicOr(A.err, !off_ok ? PG_DEVERR_OFFSETS
+                                            : (sp_ok ? PG_DEVERR_ELEMENT : PG_DEVERR_SPACING));
                     A.grad_coords[3 * a] = 0.0f;
                     A.grad_coords[3 * a + 1] = 0.0f;
                     A.grad_coords[3 * a + 2] = 0.0f;
@@ -232,6 +251,17 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
             }
         }
     }
+
+    // Retire (see the forward kernel): the last warp resets the counter.
+    if (lane == 0) {
+        __threadfence();
+        const unsigned long long done = atomicAdd(A.sched + 1, 1ull);
+        if (done == total_warps - 1) {
+            __threadfence();
+            atomicExch(A.sched, 0ull);
+            atomicExch(A.sched + 1, 0ull);
+        }
+    }
 }
 
 template <typename GT>
@@ -259,13 +289,11 @@ cudaError_t backward_plan(const BackwardArgs &a, int grad_dtype, int sm_count, K
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
+    // Persistent grid: atoms come from the work counter; never more warps than atoms.
     long long blocks = (long long)sm_count * per_sm;
-    const long long need = a.geo.n_mol > 0 ? a.geo.n_mol : 1;
+    const long long need = ((long long)a.geo.n_atoms + threads / 32 - 1) / (threads / 32);
     if (blocks > need) blocks = need;
-    // Enough blocks to zero stray atoms even with an empty batch.
-    const long long need_zero = (a.geo.n_atoms + threads - 1) / threads;
     if (blocks < 1) blocks = 1;
-    if (a.geo.n_mol == 0 && need_zero > blocks) blocks = need_zero < 1024 ? need_zero : 1024;
     kl->func = f;
     kl->grid = dim3((unsigned)blocks);
     kl->block = dim3((unsigned)threads);

@@ -55,6 +55,7 @@ struct BackwardArgs {
     const void *grad_out;
     float *grad_coords;
     unsigned *err;
+    unsigned long long *sched;  // {next atom, retired warps}; zero between launches
     Geometry geo;
 };
 
