@@ -192,12 +192,21 @@ pg_tuning default_tuning(int path)
 }
 
 // Floats of per-warp shared memory for the direct kernel's scatter mode (dense planes), or 0
-// where it does not apply: no cutoff, or planes above 16 KB of FP32 accumulators.
+// where it does not apply: no cutoff, planes above 16 KB of FP32 accumulators, or an axis
+// above 256 voxels (the per-atom tables hold one entry per row and per column).
 int direct_plane_stride(const pg_grid *g)
 {
     const long long plane = (long long)g->ny * g->nz;
-    if (g->cutoff == PG_CUTOFF_NONE || plane * 4 > 16384) return 0;
+    if (g->cutoff == PG_CUTOFF_NONE || plane * 4 > 16384 || g->ny > 256 || g->nz > 256) return 0;
     return (int)((plane + 3) / 4 * 4);
+}
+
+// Whether the direct kernel runs with scatter mode (its scatter-capable instantiation).
+// Molecules of at most 32 atoms never reach it (they take the register path), so a batch
+// whose mean is that small keeps the gather-only instantiation and its higher occupancy.
+bool direct_scatter_on(const pg_batch *b, const pg_grid *g, const pg_tuning &t)
+{
+    return !t.gather_only && direct_plane_stride(g) > 0 && b->n_atoms > 32LL * b->n_mol;
 }
 
 bool vec_stores_ok(const void *out, const pg_grid *g, int dtype)
@@ -238,7 +247,7 @@ pg_status plan_forward(const pg_batch *b, const pg_grid *g, int dtype, void *out
     a.out = out;
     a.err = err;
     a.sched = sched;
-    a.plane_stride = t.gather_only ? 0 : direct_plane_stride(g);
+    a.plane_stride = direct_scatter_on(b, g, t) ? direct_plane_stride(g) : 0;
     a.chunk_planes = (t.chunk_planes >= 1 && t.chunk_planes <= 64) ? t.chunk_planes : 8;
     a.geo = G;
     cudaError_t e = direct_plan(a, dtype, vec_stores_ok(out, g, dtype) ? 1 : 0, t, d.sms, kl);
@@ -473,10 +482,10 @@ pg_status direct_launch_with_scratch(const pg_batch *b, const pg_grid *g, int dt
     a.out = out;
     a.err = err;
     a.sched = sched;
-    a.plane_stride = direct_plane_stride(g);
+    const pg_tuning t = default_tuning(PG_PATH_DIRECT);
+    a.plane_stride = direct_scatter_on(b, g, t) ? direct_plane_stride(g) : 0;
     a.chunk_planes = 8;
     make_geometry(b, g, &a.geo);
-    const pg_tuning t = default_tuning(PG_PATH_DIRECT);
     cudaError_t e = direct_plan(a, dtype, vec_stores_ok(out, g, dtype) ? 1 : 0, t, sm_count, kl);
     if (e != cudaSuccess) return cuda_fail(e, "direct_plan");
     return PG_OK;
@@ -605,12 +614,15 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
         return PG_OK;
     }
 
+    // Direct candidates with scatter mode on accumulate dense planes in fixed point; those
+    // without sum in float.  Within a class every candidate must match the reference's bits.
+    auto scatter_class = [&](const pg_tuning &t) { return direct_scatter_on(batch, grid, t); };
     std::vector<pg_tuning> cands;
     if (path != PG_PATH_SEPARABLE) {
         // Full product of the direct kernel's launch knobs; the default comes first and is
         // the reference every other candidate must match bit for bit.
         cands.push_back(default_tuning(PG_PATH_DIRECT));
-        const int go_max = grid->cutoff != PG_CUTOFF_NONE ? 1 : 0;
+        const int go_max = direct_scatter_on(batch, grid, default_tuning(PG_PATH_DIRECT)) ? 1 : 0;
         for (int threads : {256, 512})
             for (int bps : {0, 1, 2})
                 for (int hint : {0, 1})
@@ -693,7 +705,8 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
                 return st;
             if ((st = cu(cudaStreamSynchronize(s), "sync"))) return st;
             ref_index = (int)i;
-        } else if (cands[i].path == cands[ref_index].path && cands[i].path == PG_PATH_DIRECT) {
+        } else if (cands[i].path == PG_PATH_DIRECT && cands[ref_index].path == PG_PATH_DIRECT &&
+                   scatter_class(cands[i]) == scatter_class(cands[ref_index])) {
             unsigned long long h = 0;
             if ((st = cu(buffer_hash(out, out_bytes, d_hash, s), "hash"))) return st;
             if ((st = cu(cudaMemcpyAsync(&h, d_hash, sizeof h, cudaMemcpyDeviceToHost, s),
@@ -710,7 +723,15 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
                          "copy compare")))
                 return st;
             if ((st = cu(cudaStreamSynchronize(s), "sync"))) return st;
-            pass = cmp[0] <= 1e-2f * cmp[1];
+            // Separable candidates round through BF16 operands; direct candidates of the other
+            // accumulation class differ only in the rounding of each voxel's sum, which the
+            // output dtype may round once more.
+            const bool sep = cands[i].path == PG_PATH_SEPARABLE ||
+                             cands[ref_index].path == PG_PATH_SEPARABLE;
+            const float tol = sep ? 1e-2f
+                                  : (out_dtype == PG_F32 ? 1e-5f
+                                                         : (out_dtype == PG_F16 ? 1e-3f : 8e-3f));
+            pass = cmp[0] <= tol * cmp[1];
         }
         if (!pass) continue;
         // Time: median over 5 batches of back-to-back launches, each batch >= ~0.5 ms.

@@ -22,8 +22,14 @@
 //      to nearest even), zeros included.
 // Culls are conservative and survivors are visited in atom order, so every voxel sums the
 // same terms in the same order whatever the launch shape: results are bitwise identical
-// across tunings and equal to the unstaged fallback used when an item has more than
-// kStageCap candidates.
+// across block sizes, occupancy, store hints and chunk sizes, and equal to the unstaged
+// fallback used when an item has more than kStageCap candidates.
+//
+// Dense planes (kScatterMin or more staged candidates) can instead be accumulated in scatter
+// mode (see scatter_plane), in a kernel instantiation of its own.  Scatter mode adds the same
+// terms in exact fixed point, so its results differ from the gather's float sums only by the
+// rounding of those sums (a few units in the last place of FP32); across launch shapes they are
+// again bitwise identical.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -176,6 +182,9 @@ __device__ __forceinline__ void store_lane(T *out, int v, const float (&acc)[VEC
 
 __device__ __forceinline__ int wrap_index(int i, int n)
 {
+    if (i >= 0 && i < n) return i;
+    if (i < 0 && i >= -n) return i + n;
+    if (i >= n && i < 2 * n) return i - n;
     const int r = i % n;
     return r < 0 ? r + n : r;
 }
@@ -197,108 +206,163 @@ __device__ __forceinline__ void disc_range(float a, float rho, float o, float in
     }
 }
 
-// Scatter mode for dense planes.  The warp accumulates the plane in its shared-memory buffer
-// atom by atom, in atom order; each atom visits only the bounding square of its disc in this
-// plane, and every lane owns distinct voxels within one atom.  Then the plane is converted and
-// stored.  Per voxel the same non-zero terms, computed by the same operations, are added in
-// the same order as in the gather mode, so both modes give identical bits.
+// Scatter mode for dense planes (Sec. VI-A visits each atom's non-zero box; here the box is cut
+// down to the exact disc row by row).  Work unit: one "run", the voxels of one row of one
+// candidate's disc in this plane.  The runs of all candidates are numbered consecutively
+// (per-candidate row counts, prefix-summed across the warp), and lane i takes runs i, i+32, ...
+// so lanes stay busy however many rows a disc has.  For its run a lane finds the exact z span
+// of the disc in that row and adds each in-cutoff term to the warp's plane accumulator with a
+// shared-memory integer atomic.  The accumulator is fixed point, scaled so that a voxel's sum
+// of at most `count` terms (each <= 1) stays below 2^30: integer addition is exact and
+// associative, so the result does not depend on the order in which lanes and runs land, and
+// every term is the same ex2 of the same d^2 as in the gather mode.
 template <typename T, int VEC, int CUT, bool PER, int HINT>
-__device__ __noinline__ void scatter_plane(T *out, float *acc_s, const float4 *stage, int count,
-                                           int ny, int nz, int lane, float q, float r2,
-                                           float rc, float oy, float oz, float hy, float hz,
-                                           float Ly, float iLy, float Lz, float iLz)
+__device__ __forceinline__ void scatter_plane(T *out, int *acc_i, int *run_off, int *run_ylo,
+                                              const float4 *stage, int count, int ny, int nz,
+                                              int lane, float q, float r2, float rc, float oy,
+                                              float oz, float hy, float hz, float Ly, float iLy,
+                                              float Lz, float iLz)
 {
-    const int plane = ny * nz;
-    const int nvec = plane / VEC;
-    for (int i = lane; i < plane; i += 32) acc_s[i] = 0.0f;
-    __syncwarp();
+    const int nvec = ny * nz / VEC;
     const float inv_hy = 1.0f / hy, inv_hz = 1.0f / hz;
-    for (int j = 0; j < count; ++j) {
+    // count < 2^bits, so a voxel's scaled sum is below 2^30.
+    const int bits = 32 - __clz(count);
+    const float scale = __int_as_float((127 + 30 - bits) << 23);
+    const float inv_scale = __int_as_float((127 - 30 + bits) << 23);
+
+    // 1. Row range of each candidate's disc, and the prefix offsets of its runs.
+    int total = 0;
+    for (int cb = 0; cb < count; cb += 32) {
+        const int j = cb + lane;
+        int nrows = 0, ylo = 0;
+        if (j < count) {
+            const float4 st = stage[j];
+            float rho = rc;
+            if (CUT == PG_CUTOFF_SPHERE) rho = sqrtf(fmaxf(fmaf(-st.x, st.x, rc * rc), 0.0f));
+            int lo, hi;
+            disc_range<PER>(st.y, rho, oy, inv_hy, ny, lo, hi);
+            nrows = max(hi - lo + 1, 0);
+            ylo = PER ? wrap_index(lo, ny) : lo;
+        }
+        int incl = nrows;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (j < count) {
+            run_off[j] = total + incl - nrows;
+            run_ylo[j] = ylo;
+        }
+        total += __shfl_sync(0xffffffffu, incl, 31);
+    }
+    if (lane == 0) run_off[count] = total;
+    __syncwarp();
+
+    // 2. Runs.
+    int j = 0;
+    for (int u = lane; u < total; u += 32) {
+        while (run_off[j + 1] <= u) ++j;
         const float4 st = stage[j];
         const float dx = st.x, ay = st.y, az = st.z;
         const float dx2 = dx * dx;
-        float rho = rc;
+        int y = run_ylo[j] + (u - run_off[j]);
+        if (PER && y >= ny) y -= ny;
+        float dy = fmaf((float)y + 0.5f, hy, oy) - ay;
+        if (PER) dy = wrap(dy, Ly, iLy);
+        const float dy2 = dy * dy;
+        const float dxy2 = fmaf(dy, dy, dx2);
+        float w = rc;
         if (CUT == PG_CUTOFF_SPHERE) {
-            const float t = fmaf(-dx, dx, rc * rc);
-            if (t < 0.0f) continue;
-            rho = sqrtf(t);
+            const float rem = fmaf(rc, rc, -dxy2);
+            if (rem < 0.0f) continue;
+            w = sqrtf(rem);
+        } else if (fmaxf(dx2, dy2) > r2) {
+            continue;
         }
-        int ylo, yhi, zlo, zhi;
-        disc_range<PER>(ay, rho, oy, inv_hy, ny, ylo, yhi);
-        disc_range<PER>(az, rho, oz, inv_hz, nz, zlo, zhi);
-        const int ny_s = yhi - ylo + 1, nz_s = zhi - zlo + 1;
-        if (ny_s <= 0 || nz_s <= 0) continue;
-        if (PER) {  // start inside [0, n): one conditional wrap per voxel suffices
-            ylo = wrap_index(ylo, ny);
-            zlo = wrap_index(zlo, nz);
-        }
-        auto add = [&](int y, float dy, int z, float dz) {
-            const float dxy2 = fmaf(dy, dy, dx2);
+        int zlo, zhi;
+        disc_range<PER>(az, w, oz, inv_hz, nz, zlo, zhi);
+        int *row = acc_i + y * nz;
+        int z = PER ? wrap_index(zlo, nz) : zlo;
+        // Fixed-point term of voxel zz of this run (0 when outside the cutoff).
+        auto term = [&](int zz) -> int {
+            float dz = fmaf((float)zz + 0.5f, hz, oz) - az;
+            if (PER) dz = wrap(dz, Lz, iLz);
             const float d2 = fmaf(dz, dz, dxy2);
-            const bool in = (CUT == PG_CUTOFF_SPHERE)
-                                ? (d2 <= r2)
-                                : (fmaxf(fmaxf(dx2, dy * dy), dz * dz) <= r2);
-            if (in) acc_s[y * nz + z] += ex2_approx(-q * d2);
+            const bool in = (CUT == PG_CUTOFF_SPHERE) ? (d2 <= r2)
+                                                      : (fmaxf(fmaxf(dx2, dy2), dz * dz) <= r2);
+            return in ? __float2int_rn(ex2_approx(-q * d2) * scale) : 0;
         };
-        auto row = [&](int fy, int &y, float &dy) {
-            y = ylo + fy;
-            if (PER && y >= ny) y -= ny;
-            dy = fmaf((float)y + 0.5f, hy, oy) - ay;
-            if (PER) dy = wrap(dy, Ly, iLy);
-        };
-        if (nz_s <= 32) {
-            // Lane -> (row offset ry, column rz) with rows_per_step rows per step: the lane's
-            // column, and so its z displacement, is fixed for the whole atom.
-            const int rows_per_step = 32 / nz_s;
-            const int ry = lane / nz_s, rz = lane - (lane / nz_s) * nz_s;
-            if (ry < rows_per_step) {
-                int z = zlo + rz;
-                if (PER && z >= nz) z -= nz;
-                float dz = fmaf((float)z + 0.5f, hz, oz) - az;
-                if (PER) dz = wrap(dz, Lz, iLz);
-                for (int fy = ry; fy < ny_s; fy += rows_per_step) {
-                    int y;
-                    float dy;
-                    row(fy, y, dy);
-                    add(y, dy, z, dz);
-                }
+        int k = zhi - zlo + 1;
+        // Four voxels at a time: independent terms first, then their atomics.
+        for (; k >= 4; k -= 4) {
+            int zz[4], tv[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                zz[i] = z + i;
+                if (PER && zz[i] >= nz) zz[i] -= nz;
+                tv[i] = term(zz[i]);
             }
-        } else {
-            for (int fy = 0; fy < ny_s; ++fy) {
-                int y;
-                float dy;
-                row(fy, y, dy);
-                for (int fz = lane; fz < nz_s; fz += 32) {
-                    int z = zlo + fz;
-                    if (PER && z >= nz) z -= nz;
-                    float dz = fmaf((float)z + 0.5f, hz, oz) - az;
-                    if (PER) dz = wrap(dz, Lz, iLz);
-                    add(y, dy, z, dz);
-                }
-            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (tv[i]) atomicAdd(row + zz[i], tv[i]);
+            z += 4;
+            if (PER && z >= nz) z -= nz;
         }
-        __syncwarp();
+        for (; k > 0; --k) {
+            const int tv = term(z);
+            if (tv) atomicAdd(row + z, tv);
+            ++z;
+            if (PER && z >= nz) z -= nz;
+        }
     }
+    __syncwarp();
+
+    // 3. Convert, store, and leave the accumulator zeroed for the next plane.
     for (int v = lane; v < nvec; v += 32) {
         float a[VEC];
+        if constexpr (VEC % 4 == 0) {
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) a[k] = acc_s[v * VEC + k];
+            for (int k = 0; k < VEC; k += 4) {
+                int4 *p = reinterpret_cast<int4 *>(acc_i + v * VEC) + k / 4;
+                const int4 w = *p;
+                *p = make_int4(0, 0, 0, 0);
+                a[k] = (float)w.x * inv_scale;
+                a[k + 1] = (float)w.y * inv_scale;
+                a[k + 2] = (float)w.z * inv_scale;
+                a[k + 3] = (float)w.w * inv_scale;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+                a[k] = (float)acc_i[v * VEC + k] * inv_scale;
+                acc_i[v * VEC + k] = 0;
+            }
+        }
         store_lane<T, VEC, HINT>(out, v, a);
     }
     __syncwarp();
 }
 
-template <typename T, int VEC, int CUT, bool PER, int HINT>
-__global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
+template <typename T, int VEC, int CUT, bool PER, int HINT, bool SCAT>
+__global__ void __launch_bounds__(512, SCAT ? 1 : 2) direct_kernel(const DirectArgs A)
 {
     extern __shared__ float4 smem_all[];
     const Geometry &G = A.geo;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int warps_per_block = blockDim.x >> 5;
-    // Per warp: kStageCap staged atoms, then (scatter mode) a plane of A.plane_stride floats.
-    float4 *stage = smem_all + (size_t)warp * (kStageCap + A.plane_stride / 4);
-    float *acc_s = reinterpret_cast<float *>(stage + kStageCap);
+    // Per warp (layout in direct_warp_floats): the plane's staged candidates, the chunk's
+    // channel atoms, then in scatter mode the plane accumulator and the run bookkeeping.
+    float4 *stage = smem_all + (size_t)warp * (direct_warp_floats(A.plane_stride) / 4);
+    float4 *chan = stage + kStageCap;
+    int *acc_i = reinterpret_cast<int *>(chan + kChanCap);
+    int *run_off = acc_i + A.plane_stride;
+    int *run_ylo = run_off + kStageCap + 4;
+    if (SCAT) {  // the scatter accumulator starts zeroed and each plane leaves it so
+        for (int i = lane; i < A.plane_stride; i += 32) acc_i[i] = 0;
+        __syncwarp();
+    }
     const unsigned lt_mask = (1u << lane) - 1u;
 
     // Work is handed out dynamically in chunks of up to chunk_planes consecutive x-planes of
@@ -377,6 +441,43 @@ __global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
             }
             if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(A.err, PG_DEVERR_ELEMENT);
         }
+        // Large molecule: this channel's atoms, in atom order, staged in shared memory once
+        // per chunk when they fit, so that each plane culls them from there.
+        int n_chan = -1;
+        if (!small) {
+            int cnt = 0;
+            // 64 atoms per step, all loads issued before any is used.
+            for (int base = a0; base < a1; base += 64) {
+                int e[2];
+                float ax[2], ay[2], az[2];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int ai = base + 32 * h + lane;
+                    e[h] = -1;
+                    ax[h] = ay[h] = az[h] = 0.0f;
+                    if (ai < a1) {
+                        e[h] = __ldg(A.in.elem + ai);
+                        ax[h] = __ldg(A.in.coords + 3 * ai);
+                        ay[h] = __ldg(A.in.coords + 3 * ai + 1);
+                        az[h] = __ldg(A.in.coords + 3 * ai + 2);
+                        if ((unsigned)e[h] >= (unsigned)G.C && c == 0 && x_begin == 0)
+                            atomicOr(A.err, PG_DEVERR_ELEMENT);
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const bool ok = e[h] == c;
+                    const unsigned m = __ballot_sync(0xffffffffu, ok);
+                    if (ok) {
+                        const int pos = cnt + __popc(m & lt_mask);
+                        if (pos < kChanCap) chan[pos] = make_float4(ax[h], ay[h], az[h], 0.0f);
+                    }
+                    cnt += __popc(m);
+                }
+            }
+            __syncwarp();
+            n_chan = cnt <= kChanCap ? cnt : -1;
+        }
         for (int x = x_begin; x < x_end; ++x) {
             const long long item = (long long)bc * G.nx + x;
             T *out = reinterpret_cast<T *>(A.out) + item * (long long)plane;
@@ -440,20 +541,38 @@ __global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
                     }
                 }
             } else {
-                // Large molecule: cull and stage this channel's atoms near the plane, in order.
+                // Large molecule: cull and stage this channel's atoms near the plane, in order,
+                // from the chunk's channel list, or else from global memory.
                 int count = 0;
-                for (int base = a0; base < a1; base += 32) {
+                for (int cb = 0; cb < n_chan; cb += 32) {
+                    const int j = cb + lane;
+                    bool ok = false;
+                    float dx = 0.0f, ay = 0.0f, az = 0.0f;
+                    if (j < n_chan) {
+                        const float4 a = chan[j];
+                        ay = a.y;
+                        az = a.z;
+                        dx = vx - a.x;
+                        if (PER) dx = wrap(dx, Lx, iLx);
+                        ok = (CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc);
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, ok);
+                    if (ok) stage[count + __popc(m & lt_mask)] = make_float4(dx, ay, az, 0.0f);
+                    count += __popc(m);
+                }
+                for (int base = n_chan >= 0 ? a1 : a0; base < a1; base += 32) {
                     const int ai = base + lane;
                     bool ok = false;
                     float dx = 0.0f, ay = 0.0f, az = 0.0f;
                     if (ai < a1) {
+                        // Loads issued together, used after.
                         const int e = __ldg(A.in.elem + ai);
+                        const float ax = __ldg(A.in.coords + 3 * ai);
+                        ay = __ldg(A.in.coords + 3 * ai + 1);
+                        az = __ldg(A.in.coords + 3 * ai + 2);
                         if ((unsigned)e >= (unsigned)G.C) {
                             if (c == 0 && x == 0) atomicOr(A.err, PG_DEVERR_ELEMENT);
                         } else if (e == c) {
-                            const float ax = __ldg(A.in.coords + 3 * ai);
-                            ay = __ldg(A.in.coords + 3 * ai + 1);
-                            az = __ldg(A.in.coords + 3 * ai + 2);
                             dx = vx - ax;
                             if (PER) dx = wrap(dx, Lx, iLx);
                             ok = (CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc);
@@ -469,11 +588,10 @@ __global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
                 __syncwarp();
                 if (count == 0) {
                     zero_plane<T, VEC, HINT>(out, nvec, lane);
-                } else if (CUT != PG_CUTOFF_NONE && A.plane_stride > 0 && count >= kScatterMin &&
-                           count <= kStageCap) {
-                    scatter_plane<T, VEC, CUT, PER, HINT>(out, acc_s, stage, count, G.ny, G.nz,
-                                                         lane, q, r2, rc, oy, oz, hy, hz, Ly,
-                                                         iLy, Lz, iLz);
+                } else if (SCAT && count >= kScatterMin && count <= kStageCap) {
+                    scatter_plane<T, VEC, CUT, PER, HINT>(out, acc_i, run_off, run_ylo, stage,
+                                                         count, G.ny, G.nz, lane, q, r2, rc, oy,
+                                                         oz, hy, hz, Ly, iLy, Lz, iLz);
                 } else {
                     int y = y_start, z0 = z_start;
                     for (int g = 0; g < nvec; g += 32) {
@@ -569,24 +687,34 @@ __global__ void __launch_bounds__(512, 2) direct_kernel(const DirectArgs A)
     }
 }
 
-template <typename T, int VEC, int CUT, bool PER>
-const void *pick_hint(int hint)
+// Scatter-capable instantiations (SCAT) exist only where a cutoff bounds each atom's disc;
+// the gather-only ones carry no scatter code and so keep their register allocation.
+template <typename T, int VEC, int CUT, bool PER, int HINT>
+const void *pick_scat(bool scat)
 {
-    return hint == 1 ? (const void *)direct_kernel<T, VEC, CUT, PER, 1>
-                     : (const void *)direct_kernel<T, VEC, CUT, PER, 0>;
+    if constexpr (CUT != PG_CUTOFF_NONE)
+        if (scat) return (const void *)direct_kernel<T, VEC, CUT, PER, HINT, true>;
+    return (const void *)direct_kernel<T, VEC, CUT, PER, HINT, false>;
+}
+
+template <typename T, int VEC, int CUT, bool PER>
+const void *pick_hint(int hint, bool scat)
+{
+    return hint == 1 ? pick_scat<T, VEC, CUT, PER, 1>(scat) : pick_scat<T, VEC, CUT, PER, 0>(scat);
 }
 
 template <typename T, int VEC>
-const void *pick_shape(int cutoff, int periodic, int hint)
+const void *pick_shape(int cutoff, int periodic, int hint, bool scat)
 {
     if (periodic) {
-        if (cutoff == PG_CUTOFF_SPHERE) return pick_hint<T, VEC, PG_CUTOFF_SPHERE, true>(hint);
-        if (cutoff == PG_CUTOFF_BOX) return pick_hint<T, VEC, PG_CUTOFF_BOX, true>(hint);
-        return pick_hint<T, VEC, PG_CUTOFF_NONE, true>(hint);
+        if (cutoff == PG_CUTOFF_SPHERE)
+            return pick_hint<T, VEC, PG_CUTOFF_SPHERE, true>(hint, scat);
+        if (cutoff == PG_CUTOFF_BOX) return pick_hint<T, VEC, PG_CUTOFF_BOX, true>(hint, scat);
+        return pick_hint<T, VEC, PG_CUTOFF_NONE, true>(hint, scat);
     }
-    if (cutoff == PG_CUTOFF_SPHERE) return pick_hint<T, VEC, PG_CUTOFF_SPHERE, false>(hint);
-    if (cutoff == PG_CUTOFF_BOX) return pick_hint<T, VEC, PG_CUTOFF_BOX, false>(hint);
-    return pick_hint<T, VEC, PG_CUTOFF_NONE, false>(hint);
+    if (cutoff == PG_CUTOFF_SPHERE) return pick_hint<T, VEC, PG_CUTOFF_SPHERE, false>(hint, scat);
+    if (cutoff == PG_CUTOFF_BOX) return pick_hint<T, VEC, PG_CUTOFF_BOX, false>(hint, scat);
+    return pick_hint<T, VEC, PG_CUTOFF_NONE, false>(hint, scat);
 }
 
 }  // namespace
@@ -595,20 +723,22 @@ cudaError_t direct_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tun
                         int sm_count, KernelLaunch *kl)
 {
     const int hint = t.store_hint == 1 ? 1 : 0;
+    const bool scat = a.plane_stride > 0 && a.geo.cutoff != PG_CUTOFF_NONE;
+    const int cut = a.geo.cutoff, per = a.geo.periodic;
     const void *f = nullptr;
     if (dtype == PG_F32)
-        f = vec_ok ? pick_shape<float, 4>(a.geo.cutoff, a.geo.periodic, hint)
-                   : pick_shape<float, 1>(a.geo.cutoff, a.geo.periodic, hint);
+        f = vec_ok ? pick_shape<float, 4>(cut, per, hint, scat)
+                   : pick_shape<float, 1>(cut, per, hint, scat);
     else if (dtype == PG_F16)
-        f = vec_ok ? pick_shape<__half, 8>(a.geo.cutoff, a.geo.periodic, hint)
-                   : pick_shape<__half, 1>(a.geo.cutoff, a.geo.periodic, hint);
+        f = vec_ok ? pick_shape<__half, 8>(cut, per, hint, scat)
+                   : pick_shape<__half, 1>(cut, per, hint, scat);
     else
-        f = vec_ok ? pick_shape<__nv_bfloat16, 8>(a.geo.cutoff, a.geo.periodic, hint)
-                   : pick_shape<__nv_bfloat16, 1>(a.geo.cutoff, a.geo.periodic, hint);
+        f = vec_ok ? pick_shape<__nv_bfloat16, 8>(cut, per, hint, scat)
+                   : pick_shape<__nv_bfloat16, 1>(cut, per, hint, scat);
 
     int threads = t.block_threads;
     if (threads != 128 && threads != 256 && threads != 512) threads = 256;
-    const size_t per_warp = kStageCap * sizeof(float4) + (size_t)a.plane_stride * sizeof(float);
+    const size_t per_warp = (size_t)direct_warp_floats(a.plane_stride) * sizeof(float);
     while (threads > 128 && (size_t)(threads / 32) * per_warp > 200 * 1024) threads /= 2;
     const size_t smem = (size_t)(threads / 32) * per_warp;
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -15,6 +15,7 @@ constexpr int kMaxC = PG_MAX_CHANNELS;
 // Candidate atoms one warp stages in shared memory for one (molecule, channel, x-plane)
 // item.  Items with more candidates take the unstaged path (same result, bit for bit).
 constexpr int kStageCap = 128;
+constexpr int kChanCap = 128;  // one channel's atoms of a molecule, staged per chunk
 
 // Per-call constants (kernel parameter space; uniform across the grid).
 struct Geometry {
@@ -35,6 +36,17 @@ struct Inputs {
     const float *origin;
     const float *spacing;
 };
+
+// 32-bit words of dynamic shared memory per warp of the direct kernel: kStageCap staged
+// candidates and kChanCap channel atoms (float4 each), then, when scatter mode is on
+// (plane_stride > 0), the plane's fixed-point accumulator (plane_stride words, a multiple of
+// 4), the run offsets (kStageCap + 4) and the first row of each candidate's disc (kStageCap).
+// A multiple of 4 words.
+__host__ __device__ inline int direct_warp_floats(int plane_stride)
+{
+    return 4 * (kStageCap + kChanCap) +
+           (plane_stride > 0 ? plane_stride + 2 * kStageCap + 4 : 0);
+}
 
 struct DirectArgs {
     Inputs in;
