@@ -121,8 +121,10 @@ typedef struct {
  *   blocks_per_sm  persistent CTAs per SM (0 = as many as fit)
  *   store_hint     0: default global stores; 1: streaming (evict-first) stores
  *   n_tile         separable path: output columns per tensor-core tile (64, 128 or 256)
- *   gather_only    direct path: 0 lets dense planes accumulate atom by atom in shared memory
- *                  (scatter mode); 1 gathers every plane.  Both give identical bits.
+ *   gather_only    direct path: 0 lets planes with many candidate atoms accumulate in
+ *                  shared memory in exact fixed point (scatter mode; batches of molecules with
+ *                  more than 32 atoms on average); 1 gathers every plane in float.  The two
+ *                  differ only in the rounding of each voxel's sum.
  *   chunk_planes   direct path: x-planes per dynamically scheduled work chunk (1..64; 0 = 8)
  *   separable_simple  separable path: 0 = warp-specialized pipeline (default), 1 = one-stage
  *                  kernel.  Both accumulate the same BF16 products in the same order.

@@ -108,7 +108,18 @@ __device__ __forceinline__ void store16(void *p, uint4 v)
         *reinterpret_cast<uint4 *>(p) = v;
 }
 
-// Per-lane accumulation of one atom's contribution into the lane's VEC voxels.
+// Per-voxel z factor 2^(-q dz^2) of a separable (box or no-cutoff) term; zero outside a box.
+template <int CUT>
+__device__ __forceinline__ float z_factor(float dz, float q, float r2)
+{
+    const float dz2 = dz * dz;
+    const float e = ex2_approx(-q * dz2);
+    return (CUT == PG_CUTOFF_BOX && dz2 > r2) ? 0.0f : e;
+}
+
+// Per-lane accumulation of one atom's contribution into the lane's VEC voxels.  With a
+// sphere cutoff each term is 2^(-q d^2) of the voxel's own d^2; with a box or no cutoff it is
+// the product of the row factor 2^(-q (dx^2 + dy^2)) and the voxel's z factor.
 template <int VEC, int CUT, bool PER>
 struct LaneVoxels {
     float vy;        // voxel-centre y of the lane's row
@@ -122,19 +133,26 @@ struct LaneVoxels {
         if (PER) dy = wrap(dy, Ly, iLy);
         const float dx2 = dx * dx;
         const float dxy2 = fmaf(dy, dy, dx2);
-        const float mxy = fmaxf(dx2, dy * dy);
+        if (CUT == PG_CUTOFF_SPHERE) {
 #pragma unroll
-        for (int k = 0; k < VEC; ++k) {
-            float dz = vz[k] - az;
-            if (PER) dz = wrap(dz, Lz, iLz);
-            const float d2 = fmaf(dz, dz, dxy2);
-            const float t = ex2_approx(-q * d2);
-            if (CUT == PG_CUTOFF_SPHERE)
+            for (int k = 0; k < VEC; ++k) {
+                float dz = vz[k] - az;
+                if (PER) dz = wrap(dz, Lz, iLz);
+                const float d2 = fmaf(dz, dz, dxy2);
+                const float t = ex2_approx(-q * d2);
                 acc[k] += (d2 <= r2) ? t : 0.0f;
-            else if (CUT == PG_CUTOFF_BOX)
-                acc[k] += (fmaxf(mxy, dz * dz) <= r2) ? t : 0.0f;
-            else
-                acc[k] += t;
+            }
+        } else {
+            // Box or no cutoff: the Gaussian separates into a per-row factor and a per-voxel
+            // z factor (Sec. VI-A), which saves the per-voxel range test of the row.
+            float exy = ex2_approx(-q * dxy2);
+            if (CUT == PG_CUTOFF_BOX && fmaxf(dx2, dy * dy) > r2) exy = 0.0f;
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+                float dz = vz[k] - az;
+                if (PER) dz = wrap(dz, Lz, iLz);
+                acc[k] += exy * z_factor<CUT>(dz, q, r2);
+            }
         }
     }
 };
@@ -284,14 +302,20 @@ __device__ __forceinline__ void scatter_plane(T *out, int *acc_i, int *run_off, 
         disc_range<PER>(az, w, oz, inv_hz, nz, zlo, zhi);
         int *row = acc_i + y * nz;
         int z = PER ? wrap_index(zlo, nz) : zlo;
-        // Fixed-point term of voxel zz of this run (0 when outside the cutoff).
+        const float exy = CUT == PG_CUTOFF_SPHERE ? 0.0f : ex2_approx(-q * dxy2);
+        // Fixed-point term of voxel zz of this run (0 when outside the cutoff): the same float
+        // term as the gather mode adds.
         auto term = [&](int zz) -> int {
             float dz = fmaf((float)zz + 0.5f, hz, oz) - az;
             if (PER) dz = wrap(dz, Lz, iLz);
-            const float d2 = fmaf(dz, dz, dxy2);
-            const bool in = (CUT == PG_CUTOFF_SPHERE) ? (d2 <= r2)
-                                                      : (fmaxf(fmaxf(dx2, dy2), dz * dz) <= r2);
-            return in ? __float2int_rn(ex2_approx(-q * d2) * scale) : 0;
+            float t;
+            if (CUT == PG_CUTOFF_SPHERE) {
+                const float d2 = fmaf(dz, dz, dxy2);
+                t = d2 <= r2 ? ex2_approx(-q * d2) : 0.0f;
+            } else {
+                t = exy * z_factor<CUT>(dz, q, r2);
+            }
+            return __float2int_rn(t * scale);
         };
         int k = zhi - zlo + 1;
         // Four voxels at a time: independent terms first, then their atomics.
