@@ -161,12 +161,16 @@ def write_probe_gbs(nbytes=4 << 30, reps=10):
     return max(res.values()), res
 
 
-def kernel_source_sha():
+KERNEL_SOURCES = {"direct": "pg_direct.cu", "separable": "pg_separable.cu",
+                  "backward": "pg_backward.cu"}
+
+
+def kernel_source_sha(kernel: str) -> str:
+    """First 16 hex digits of the SHA-256 of the kernel's CUDA source file."""
     h = hashlib.sha256()
-    for f in ("pg_direct.cu", "pg_separable.cu"):
-        p = os.path.join(ROOT, "paper_2211_08506_gb300", "csrc", f)
-        if os.path.exists(p):
-            h.update(open(p, "rb").read())
+    p = os.path.join(ROOT, "paper_2211_08506_gb300", "csrc", KERNEL_SOURCES[kernel])
+    if os.path.exists(p):
+        h.update(open(p, "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -180,7 +184,7 @@ def profiled_traffic(workload: str, kernel: str):
     except Exception:
         return None
     e = entries.get(f"{kernel}:{workload}")
-    if not e or e.get("kernel_source_sha") != kernel_source_sha():
+    if not e or e.get("kernel_source_sha") != kernel_source_sha(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
