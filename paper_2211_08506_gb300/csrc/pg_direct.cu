@@ -151,7 +151,7 @@ struct LaneVoxels {
             for (int k = 0; k < VEC; ++k) {
                 float dz = vz[k] - az;
                 if (PER) dz = wrap(dz, Lz, iLz);
-                acc[k] += exy * z_factor<CUT>(dz, q, r2);
+                acc[k] = fmaf(exy, z_factor<CUT>(dz, q, r2), acc[k]);
             }
         }
     }
@@ -520,6 +520,68 @@ __global__ void __launch_bounds__(512, SCAT ? 1 : 2) direct_kernel(const DirectA
                 const unsigned cmask = __ballot_sync(0xffffffffu, cand);
                 if (cmask == 0u) {
                     zero_plane<T, VEC, HINT>(out, nvec, lane);
+                } else if (CUT != PG_CUTOFF_SPHERE && z_step == 0) {
+                    // Separable terms and a lane whose columns repeat from group to group: two
+                    // groups (rows y and y + y_step) per pass share each atom's z factors.
+                    // Atoms culled for one of the two rows add exact zeros there, so the
+                    // sums are bitwise those of one group at a time.
+                    const int z0 = z_start;
+                    float vz[VEC];
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) vz[k] = fmaf((float)(z0 + k) + 0.5f, hz, oz);
+                    const int z_lo = (32 * VEC >= G.nz) ? 0 : __shfl_sync(0xffffffffu, z0, 0);
+                    const int z_hi = (32 * VEC >= G.nz) ? G.nz - 1
+                                                        : __shfl_sync(0xffffffffu, z0, 31) + VEC - 1;
+                    const float cz = fmaf(0.5f * (float)(z_lo + z_hi) + 0.5f, hz, oz);
+                    const float wz = 0.5f * (float)(z_hi - z_lo) * hz;
+                    int y = y_start;
+                    for (int g = 0; g < nvec; g += 64) {
+                        const bool two = g + 32 < nvec;
+                        // Row ranges of the two groups (each spans y_step rows).
+                        const int ya = __shfl_sync(0xffffffffu, y, 0);
+                        const int yb = ya + y_step - 1 + (two ? y_step : 0);
+                        const float cy = fmaf(0.5f * (float)(ya + yb) + 0.5f, hy, oy);
+                        const float wy = 0.5f * (float)(yb - ya) * hy;
+                        const bool hit = cand && reaches<CUT, PER>(dx, my_y, my_z, cy, wy, cz, wz,
+                                                                   rc, Ly, iLy, Lz, iLz);
+                        unsigned m = __ballot_sync(0xffffffffu, hit);
+                        float acc0[VEC], acc1[VEC];
+#pragma unroll
+                        for (int k = 0; k < VEC; ++k) acc0[k] = acc1[k] = 0.0f;
+                        const float vy0 = fmaf((float)y + 0.5f, hy, oy);
+                        const float vy1 = fmaf((float)(y + y_step) + 0.5f, hy, oy);
+                        while (m) {
+                            const int src = __ffs(m) - 1;
+                            m &= m - 1;
+                            const float sdx = __shfl_sync(0xffffffffu, dx, src);
+                            const float sy = __shfl_sync(0xffffffffu, my_y, src);
+                            const float sz = __shfl_sync(0xffffffffu, my_z, src);
+                            const float dx2 = sdx * sdx;
+                            float dy0 = vy0 - sy, dy1 = vy1 - sy;
+                            if (PER) {
+                                dy0 = wrap(dy0, Ly, iLy);
+                                dy1 = wrap(dy1, Ly, iLy);
+                            }
+                            float e0 = ex2_approx(-q * fmaf(dy0, dy0, dx2));
+                            float e1 = ex2_approx(-q * fmaf(dy1, dy1, dx2));
+                            if (CUT == PG_CUTOFF_BOX) {
+                                if (fmaxf(dx2, dy0 * dy0) > r2) e0 = 0.0f;
+                                if (fmaxf(dx2, dy1 * dy1) > r2) e1 = 0.0f;
+                            }
+#pragma unroll
+                            for (int k = 0; k < VEC; ++k) {
+                                float dz = vz[k] - sz;
+                                if (PER) dz = wrap(dz, Lz, iLz);
+                                const float ez = z_factor<CUT>(dz, q, r2);
+                                acc0[k] = fmaf(e0, ez, acc0[k]);
+                                acc1[k] = fmaf(e1, ez, acc1[k]);
+                            }
+                        }
+                        if (g + lane < nvec) store_lane<T, VEC, HINT>(out, g + lane, acc0);
+                        if (two && g + 32 + lane < nvec)
+                            store_lane<T, VEC, HINT>(out, g + 32 + lane, acc1);
+                        y += 2 * y_step;
+                    }
                 } else {
                     int y = y_start, z0 = z_start;
                     for (int g = 0; g < nvec; g += 32) {
