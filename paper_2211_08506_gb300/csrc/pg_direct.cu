@@ -133,26 +133,17 @@ struct LaneVoxels {
         if (PER) dy = wrap(dy, Ly, iLy);
         const float dx2 = dx * dx;
         const float dxy2 = fmaf(dy, dy, dx2);
-        if (CUT == PG_CUTOFF_SPHERE) {
+        float exy = ex2_approx(-q * dxy2);
+        if (CUT == PG_CUTOFF_BOX && fmaxf(dx2, dy * dy) > r2) exy = 0.0f;
 #pragma unroll
-            for (int k = 0; k < VEC; ++k) {
-                float dz = vz[k] - az;
-                if (PER) dz = wrap(dz, Lz, iLz);
-                const float d2 = fmaf(dz, dz, dxy2);
-                const float t = ex2_approx(-q * d2);
-                acc[k] += (d2 <= r2) ? t : 0.0f;
-            }
-        } else {
-            // Box or no cutoff: the Gaussian separates into a per-row factor and a per-voxel
-            // z factor (Sec. VI-A), which saves the per-voxel range test of the row.
-            float exy = ex2_approx(-q * dxy2);
-            if (CUT == PG_CUTOFF_BOX && fmaxf(dx2, dy * dy) > r2) exy = 0.0f;
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) {
-                float dz = vz[k] - az;
-                if (PER) dz = wrap(dz, Lz, iLz);
-                acc[k] = fmaf(exy, z_factor<CUT>(dz, q, r2), acc[k]);
-            }
+        for (int k = 0; k < VEC; ++k) {
+            float dz = vz[k] - az;
+            if (PER) dz = wrap(dz, Lz, iLz);
+            const float ez = z_factor<CUT>(dz, q, r2);
+            if (CUT == PG_CUTOFF_SPHERE)
+                acc[k] = (fmaf(dz, dz, dxy2) <= r2) ? fmaf(exy, ez, acc[k]) : acc[k];
+            else
+                acc[k] = fmaf(exy, ez, acc[k]);
         }
     }
 };
@@ -196,6 +187,69 @@ __device__ __forceinline__ void store_lane(T *out, int v, const float (&acc)[VEC
         store16<HINT>(out + (long long)v * VEC, pack16<T, VEC>(acc));
     else
         out[v] = from_float<T>(acc[0]);
+}
+
+// Gather of one plane in passes of two lane groups, for planes whose lane columns repeat
+// from group to group: with lpr = nz / VEC lanes per row, lane l < act = rpg * lpr owns the
+// columns z0 .. z0 + VEC - 1 of rows y0 + l / lpr and y0 + l / lpr + rpg of each pass of
+// 2 * rpg rows.  Each surviving atom's z factors are computed once per pass and shared by both
+// rows.  for_each(cy, wy, cz, wz, f) calls f(dx, ay, az) for the candidates that can reach
+// the pass's box of voxel centres, in atom order.  Every voxel adds the same terms in the same
+// order as LaneVoxels::add does (atoms culled for one of the two rows add exact zeros or are
+// skipped by the same test), so both give identical bits.
+template <typename T, int VEC, int CUT, bool PER, int HINT, typename ForEach>
+__device__ __forceinline__ void blocked_plane(T *out, int ny, int nz, int rpg, int act,
+                                              int my_row, int z0, int lane, float q, float r2,
+                                              float oy, float oz, float hy, float hz, float Ly,
+                                              float iLy, float Lz, float iLz, ForEach for_each)
+{
+    float vz[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) vz[k] = fmaf((float)(z0 + k) + 0.5f, hz, oz);
+    const float cz = fmaf(0.5f * (float)(nz - 1) + 0.5f, hz, oz);
+    const float wz = 0.5f * (float)(nz - 1) * hz;
+    for (int y0 = 0; y0 < ny; y0 += 2 * rpg) {
+        const int y_end = min(y0 + 2 * rpg, ny) - 1;
+        const float cy = fmaf(0.5f * (float)(y0 + y_end) + 0.5f, hy, oy);
+        const float wy = 0.5f * (float)(y_end - y0) * hy;
+        const int ya = y0 + my_row, yb = ya + rpg;
+        const float vya = fmaf((float)ya + 0.5f, hy, oy);
+        const float vyb = fmaf((float)yb + 0.5f, hy, oy);
+        float acc0[VEC], acc1[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) acc0[k] = acc1[k] = 0.0f;
+        for_each(cy, wy, cz, wz, [&](float dx, float ay, float az) {
+            const float dx2 = dx * dx;
+            float dya = vya - ay, dyb = vyb - ay;
+            if (PER) {
+                dya = wrap(dya, Ly, iLy);
+                dyb = wrap(dyb, Ly, iLy);
+            }
+            const float dxya = fmaf(dya, dya, dx2), dxyb = fmaf(dyb, dyb, dx2);
+            float ea = ex2_approx(-q * dxya), eb = ex2_approx(-q * dxyb);
+            if (CUT == PG_CUTOFF_BOX) {
+                if (fmaxf(dx2, dya * dya) > r2) ea = 0.0f;
+                if (fmaxf(dx2, dyb * dyb) > r2) eb = 0.0f;
+            }
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+                float dz = vz[k] - az;
+                if (PER) dz = wrap(dz, Lz, iLz);
+                const float ez = z_factor<CUT>(dz, q, r2);
+                if (CUT == PG_CUTOFF_SPHERE) {
+                    acc0[k] = (fmaf(dz, dz, dxya) <= r2) ? fmaf(ea, ez, acc0[k]) : acc0[k];
+                    acc1[k] = (fmaf(dz, dz, dxyb) <= r2) ? fmaf(eb, ez, acc1[k]) : acc1[k];
+                } else {
+                    acc0[k] = fmaf(ea, ez, acc0[k]);
+                    acc1[k] = fmaf(eb, ez, acc1[k]);
+                }
+            }
+        });
+        if (lane < act) {
+            if (ya < ny) store_lane<T, VEC, HINT>(out, (ya * nz + z0) / VEC, acc0);
+            if (yb < ny) store_lane<T, VEC, HINT>(out, (yb * nz + z0) / VEC, acc1);
+        }
+    }
 }
 
 __device__ __forceinline__ int wrap_index(int i, int n)
@@ -302,20 +356,14 @@ __device__ __forceinline__ void scatter_plane(T *out, int *acc_i, int *run_off, 
         disc_range<PER>(az, w, oz, inv_hz, nz, zlo, zhi);
         int *row = acc_i + y * nz;
         int z = PER ? wrap_index(zlo, nz) : zlo;
-        const float exy = CUT == PG_CUTOFF_SPHERE ? 0.0f : ex2_approx(-q * dxy2);
-        // Fixed-point term of voxel zz of this run (0 when outside the cutoff): the same float
-        // term as the gather mode adds.
+        const float exy = ex2_approx(-q * dxy2);
+        // Fixed-point term of voxel zz of this run (0 when outside the cutoff): the product
+        // of the same row and z factors, under the same test, as the gather mode adds.
         auto term = [&](int zz) -> int {
             float dz = fmaf((float)zz + 0.5f, hz, oz) - az;
             if (PER) dz = wrap(dz, Lz, iLz);
-            float t;
-            if (CUT == PG_CUTOFF_SPHERE) {
-                const float d2 = fmaf(dz, dz, dxy2);
-                t = d2 <= r2 ? ex2_approx(-q * d2) : 0.0f;
-            } else {
-                t = exy * z_factor<CUT>(dz, q, r2);
-            }
-            return __float2int_rn(t * scale);
+            if (CUT == PG_CUTOFF_SPHERE && fmaf(dz, dz, dxy2) > r2) return 0;
+            return __float2int_rn(exy * z_factor<CUT>(dz, q, r2) * scale);
         };
         int k = zhi - zlo + 1;
         // Four voxels at a time: independent terms first, then their atomics.
@@ -369,7 +417,7 @@ __device__ __forceinline__ void scatter_plane(T *out, int *acc_i, int *run_off, 
 }
 
 template <typename T, int VEC, int CUT, bool PER, int HINT, bool SCAT>
-__global__ void __launch_bounds__(512, SCAT ? 1 : 2) direct_kernel(const DirectArgs A)
+__global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel(const DirectArgs A)
 {
     extern __shared__ float4 smem_all[];
     const Geometry &G = A.geo;
@@ -403,6 +451,13 @@ __global__ void __launch_bounds__(512, SCAT ? 1 : 2) direct_kernel(const DirectA
     const int nvec = plane / VEC;
     const int y_start = (lane * VEC) / G.nz, z_start = (lane * VEC) % G.nz;
     const int y_step = (32 * VEC) / G.nz, z_step = (32 * VEC) % G.nz;
+    // Two-group passes (blocked_plane) when whole rows fill at least 28 of the 32 lanes.
+    const int lpr = G.nz / VEC;
+    const int rpg = (lpr >= 1 && lpr <= 32) ? 32 / lpr : 0;
+    const int act = rpg * lpr;
+    const bool blocked = act >= 28;
+    const int my_row = blocked ? lane / lpr : 0;
+    const int my_z0 = blocked ? (lane - my_row * lpr) * VEC : 0;
 
     int cur_b = -1;
     int a0 = 0, a1 = 0;
@@ -520,68 +575,21 @@ __global__ void __launch_bounds__(512, SCAT ? 1 : 2) direct_kernel(const DirectA
                 const unsigned cmask = __ballot_sync(0xffffffffu, cand);
                 if (cmask == 0u) {
                     zero_plane<T, VEC, HINT>(out, nvec, lane);
-                } else if (CUT != PG_CUTOFF_SPHERE && z_step == 0) {
-                    // Separable terms and a lane whose columns repeat from group to group: two
-                    // groups (rows y and y + y_step) per pass share each atom's z factors.
-                    // Atoms culled for one of the two rows add exact zeros there, so the
-                    // sums are bitwise those of one group at a time.
-                    const int z0 = z_start;
-                    float vz[VEC];
-#pragma unroll
-                    for (int k = 0; k < VEC; ++k) vz[k] = fmaf((float)(z0 + k) + 0.5f, hz, oz);
-                    const int z_lo = (32 * VEC >= G.nz) ? 0 : __shfl_sync(0xffffffffu, z0, 0);
-                    const int z_hi = (32 * VEC >= G.nz) ? G.nz - 1
-                                                        : __shfl_sync(0xffffffffu, z0, 31) + VEC - 1;
-                    const float cz = fmaf(0.5f * (float)(z_lo + z_hi) + 0.5f, hz, oz);
-                    const float wz = 0.5f * (float)(z_hi - z_lo) * hz;
-                    int y = y_start;
-                    for (int g = 0; g < nvec; g += 64) {
-                        const bool two = g + 32 < nvec;
-                        // Row ranges of the two groups (each spans y_step rows).
-                        const int ya = __shfl_sync(0xffffffffu, y, 0);
-                        const int yb = ya + y_step - 1 + (two ? y_step : 0);
-                        const float cy = fmaf(0.5f * (float)(ya + yb) + 0.5f, hy, oy);
-                        const float wy = 0.5f * (float)(yb - ya) * hy;
-                        const bool hit = cand && reaches<CUT, PER>(dx, my_y, my_z, cy, wy, cz, wz,
-                                                                   rc, Ly, iLy, Lz, iLz);
-                        unsigned m = __ballot_sync(0xffffffffu, hit);
-                        float acc0[VEC], acc1[VEC];
-#pragma unroll
-                        for (int k = 0; k < VEC; ++k) acc0[k] = acc1[k] = 0.0f;
-                        const float vy0 = fmaf((float)y + 0.5f, hy, oy);
-                        const float vy1 = fmaf((float)(y + y_step) + 0.5f, hy, oy);
-                        while (m) {
-                            const int src = __ffs(m) - 1;
-                            m &= m - 1;
-                            const float sdx = __shfl_sync(0xffffffffu, dx, src);
-                            const float sy = __shfl_sync(0xffffffffu, my_y, src);
-                            const float sz = __shfl_sync(0xffffffffu, my_z, src);
-                            const float dx2 = sdx * sdx;
-                            float dy0 = vy0 - sy, dy1 = vy1 - sy;
-                            if (PER) {
-                                dy0 = wrap(dy0, Ly, iLy);
-                                dy1 = wrap(dy1, Ly, iLy);
+                } else if (blocked) {
+                    blocked_plane<T, VEC, CUT, PER, HINT>(
+                        out, G.ny, G.nz, rpg, act, my_row, my_z0, lane, q, r2, oy, oz, hy, hz, Ly,
+                        iLy, Lz, iLz, [&](float cy, float wy, float cz, float wz, auto &&f) {
+                            const bool hit = cand && reaches<CUT, PER>(dx, my_y, my_z, cy, wy, cz,
+                                                                       wz, rc, Ly, iLy, Lz, iLz);
+                            unsigned m = __ballot_sync(0xffffffffu, hit);
+                            while (m) {
+                                const int src = __ffs(m) - 1;
+                                m &= m - 1;
+                                f(__shfl_sync(0xffffffffu, dx, src),
+                                  __shfl_sync(0xffffffffu, my_y, src),
+                                  __shfl_sync(0xffffffffu, my_z, src));
                             }
-                            float e0 = ex2_approx(-q * fmaf(dy0, dy0, dx2));
-                            float e1 = ex2_approx(-q * fmaf(dy1, dy1, dx2));
-                            if (CUT == PG_CUTOFF_BOX) {
-                                if (fmaxf(dx2, dy0 * dy0) > r2) e0 = 0.0f;
-                                if (fmaxf(dx2, dy1 * dy1) > r2) e1 = 0.0f;
-                            }
-#pragma unroll
-                            for (int k = 0; k < VEC; ++k) {
-                                float dz = vz[k] - sz;
-                                if (PER) dz = wrap(dz, Lz, iLz);
-                                const float ez = z_factor<CUT>(dz, q, r2);
-                                acc0[k] = fmaf(e0, ez, acc0[k]);
-                                acc1[k] = fmaf(e1, ez, acc1[k]);
-                            }
-                        }
-                        if (g + lane < nvec) store_lane<T, VEC, HINT>(out, g + lane, acc0);
-                        if (two && g + 32 + lane < nvec)
-                            store_lane<T, VEC, HINT>(out, g + 32 + lane, acc1);
-                        y += 2 * y_step;
-                    }
+                        });
                 } else {
                     int y = y_start, z0 = z_start;
                     for (int g = 0; g < nvec; g += 32) {
@@ -678,6 +686,27 @@ __global__ void __launch_bounds__(512, SCAT ? 1 : 2) direct_kernel(const DirectA
                     scatter_plane<T, VEC, CUT, PER, HINT>(out, acc_i, run_off, run_ylo, stage,
                                                          count, G.ny, G.nz, lane, q, r2, rc, oy,
                                                          oz, hy, hz, Ly, iLy, Lz, iLz);
+                } else if (blocked && count <= kStageCap) {
+                    blocked_plane<T, VEC, CUT, PER, HINT>(
+                        out, G.ny, G.nz, rpg, act, my_row, my_z0, lane, q, r2, oy, oz, hy, hz, Ly,
+                        iLy, Lz, iLz, [&](float cy, float wy, float cz, float wz, auto &&f) {
+                            for (int cb = 0; cb < count; cb += 32) {
+                                const int j = cb + lane;
+                                bool ok = false;
+                                if (j < count) {
+                                    const float4 st = stage[j];
+                                    ok = reaches<CUT, PER>(st.x, st.y, st.z, cy, wy, cz, wz, rc, Ly,
+                                                           iLy, Lz, iLz);
+                                }
+                                unsigned m = __ballot_sync(0xffffffffu, ok);
+                                while (m) {
+                                    const int src = __ffs(m) - 1;
+                                    m &= m - 1;
+                                    const float4 st = stage[cb + src];
+                                    f(st.x, st.y, st.z);
+                                }
+                            }
+                        });
                 } else {
                     int y = y_start, z0 = z_start;
                     for (int g = 0; g < nvec; g += 32) {
