@@ -8,7 +8,8 @@ marshals it.
 
 Functions (each mirrors one C entry point; see the C file for the equations):
 
-* ``voxelize(wl_or_batch, ..., mode="bbox"|"brute")``    - Sec. III-A, Eq. 1, point sampled
+* ``voxelize(wl_or_batch, ..., mode="bbox"|"brute")``    - Sec. III-A, Eq. 1, point sampled,
+  or (``form="integral"``) integrated over each voxel with the per-axis erf factors
 * ``voxelize_band(...)``                                 - same, split at the cutoff surface
 * ``separable(...)``                                     - Sec. III-A / VI-A per-axis form
 * ``gradient(...)``                                      - Sec. IV-C, dL/dx for L = <W, G>
@@ -29,6 +30,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "libpg_oracle.so")
 
 CUTOFFS = {"sphere": 0, "none": 1, "box": 2}
+FORMS = {"point": 0, "integral": 1}
 _lock = threading.Lock()
 _lib = None
 
@@ -63,6 +65,7 @@ class _Problem(ctypes.Structure):
         ("cutoff_k", ctypes.c_double),
         ("cutoff", ctypes.c_int32),
         ("periodic", ctypes.c_int32),
+        ("form", ctypes.c_int32),
     ]
 
 
@@ -91,7 +94,7 @@ class Problem:
     """FP64 copy of a batch plus its grid description, kept alive for ctypes."""
 
     def __init__(self, batch, nx, ny, nz, n_channels, sigma, cutoff="sphere", cutoff_k=3.0,
-                 periodic=False, coords=None):
+                 periodic=False, coords=None, form="point"):
         self.mol_off = np.ascontiguousarray(batch.mol_off, np.int32)
         src = batch.coords if coords is None else coords
         self.coords = np.ascontiguousarray(np.asarray(src, np.float64).reshape(-1, 3))
@@ -114,12 +117,14 @@ class Problem:
             cutoff_k=float(cutoff_k),
             cutoff=CUTOFFS[cutoff],
             periodic=1 if periodic else 0,
+            form=FORMS[form],
         )
 
     @classmethod
     def from_workload(cls, wl, batch=None, coords=None):
         return cls(batch if batch is not None else wl.batch, wl.nx, wl.ny, wl.nz,
-                   wl.n_channels, wl.sigma, wl.cutoff, wl.cutoff_k, wl.periodic, coords)
+                   wl.n_channels, wl.sigma, wl.cutoff, wl.cutoff_k, wl.periodic, coords,
+                   getattr(wl, "form", "point"))
 
 
 def _check(rc, what):

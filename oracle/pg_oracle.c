@@ -26,6 +26,24 @@
  * Readings taken where the paper is silent or differs from the point-sampled form:
  * voxel values are sampled at voxel centres; sigma is the standard deviation; the cutoff
  * is inclusive; atoms outside the grid still contribute wherever their support reaches.
+ *
+ * Voxel-integrated form (Sec. III-A, the gridding function after Eq. 5 and its per-axis
+ * erf integrals).  Instead of the point sample, each voxel holds the normalised Gaussian
+ * integrated over the voxel, a product of one factor per axis:
+ *
+ *   F = (1/2)^3 * prod over axes of [erf((x_i + h - mu) / (sqrt(2) sigma))
+ *                                    - erf((x_i - mu) / (sqrt(2) sigma))],
+ *
+ * with x_i the voxel's lower edge and mu the atom coordinate (its nearest image relative
+ * to the voxel centre on a periodic axis).  The printed formula is taken in this order, the
+ * upper edge first, so that each factor is positive.  The cutoff indicator chi is evaluated
+ * at the voxel centre exactly as in the point form.  Its coordinate derivative (Sec. IV-C) is
+ * per axis
+ *
+ *   d/dmu [...]/2 = (1 / (sqrt(2 pi) sigma)) [exp(-(x_i - mu)^2 / 2 sigma^2)
+ *                                            - exp(-(x_i + h - mu)^2 / 2 sigma^2)],
+ *
+ * times the other two axes' factors.  This uses d/dt erf(t) = (2 / sqrt(pi)) exp(-t^2).
  */
 #include <math.h>
 #include <stdint.h>
@@ -36,6 +54,7 @@
 #endif
 
 enum { PGO_SPHERE = 0, PGO_NONE = 1, PGO_BOX = 2 };
+enum { PGO_POINT = 0, PGO_INTEGRAL = 1 };
 enum { PGO_OK = 0, PGO_BAD_ARG = 1, PGO_BAD_ELEM = 2, PGO_UNSUPPORTED = 3 };
 
 typedef struct {
@@ -50,6 +69,7 @@ typedef struct {
     double cutoff_k;
     int32_t cutoff;          /* PGO_SPHERE / PGO_NONE / PGO_BOX */
     int32_t periodic;
+    int32_t form;            /* PGO_POINT / PGO_INTEGRAL */
 } pgo_problem;
 
 /* Voxel centre along one axis: o + (i + 1/2) h. */
@@ -66,6 +86,38 @@ static int inside(int cutoff, double dx, double dy, double dz, double r)
     return 1;
 }
 
+/*
+ * One axis of the voxel-integrated form: half the erf difference across the voxel whose
+ * centre lies at displacement d from the atom (lower edge at d - h/2, upper at d + h/2).
+ */
+static double erf_factor(double d, double h, double sigma)
+{
+    double s = sqrt(2.0) * sigma;
+    return 0.5 * (erf((d + 0.5 * h) / s) - erf((d - 0.5 * h) / s));
+}
+
+/* Derivative of erf_factor with respect to the atom coordinate (d = centre - mu). */
+static double erf_factor_dmu(double d, double h, double sigma)
+{
+    double s2 = 2.0 * sigma * sigma;
+    double lo = d - 0.5 * h, hi = d + 0.5 * h;
+    return (exp(-lo * lo / s2) - exp(-hi * hi / s2)) / (sqrt(2.0 * acos(-1.0)) * sigma);
+}
+
+/*
+ * The value one atom adds to a voxel at displacement d (inside the cutoff): the point
+ * sample exp(-|d|^2 / 2 sigma^2), or the product of the three erf factors.
+ */
+static double term(const pgo_problem *p, int b, double sigma, double dx, double dy, double dz)
+{
+    if (p->form == PGO_INTEGRAL) {
+        const double *h = p->spacing + 3 * b;
+        return erf_factor(dx, h[0], sigma) * erf_factor(dy, h[1], sigma) *
+               erf_factor(dz, h[2], sigma);
+    }
+    return exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * sigma * sigma));
+}
+
 static long grid_index(const pgo_problem *p, long b, long c, long i, long j, long k)
 {
     return (((b * p->n_channels + c) * p->nx + i) * p->ny + j) * p->nz + k;
@@ -77,6 +129,7 @@ static int check(const pgo_problem *p)
         return PGO_BAD_ARG;
     if (p->cutoff != PGO_SPHERE && p->cutoff != PGO_NONE && p->cutoff != PGO_BOX)
         return PGO_BAD_ARG;
+    if (p->form != PGO_POINT && p->form != PGO_INTEGRAL) return PGO_BAD_ARG;
     for (int b = 0; b < p->n_mol; ++b)
         for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a)
             if (p->elem[a] < 0 || p->elem[a] >= p->n_channels) return PGO_BAD_ELEM;
@@ -100,7 +153,6 @@ static double disp(const pgo_problem *p, int b, int ax, long i, double x)
 static void brute_molecule(const pgo_problem *p, int b, double *out)
 {
     for (int c = 0; c < p->n_channels; ++c) {
-        double s2 = 2.0 * p->sigma[c] * p->sigma[c];
         double r = p->cutoff_k * p->sigma[c];
         for (long i = 0; i < p->nx; ++i)
             for (long j = 0; j < p->ny; ++j)
@@ -112,7 +164,7 @@ static void brute_molecule(const pgo_problem *p, int b, double *out)
                         double dy = disp(p, b, 1, j, p->coords[3 * a + 1]);
                         double dz = disp(p, b, 2, k, p->coords[3 * a + 2]);
                         if (inside(p->cutoff, dx, dy, dz, r))
-                            s += exp(-(dx * dx + dy * dy + dz * dz) / s2);
+                            s += term(p, b, p->sigma[c], dx, dy, dz);
                     }
                     out[grid_index(p, b, c, i, j, k)] = s;
                 }
@@ -163,7 +215,6 @@ static void bbox_molecule(const pgo_problem *p, int b, double *out, double eps, 
     if (band) memset(band + b * per_mol, 0, sizeof(double) * per_mol);
     for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a) {
         int c = p->elem[a];
-        double s2 = 2.0 * p->sigma[c] * p->sigma[c];
         double r = p->cutoff_k * p->sigma[c];
         double x = p->coords[3 * a + 0], y = p->coords[3 * a + 1], z = p->coords[3 * a + 2];
         long ilo, ihi, jlo, jhi, klo, khi;
@@ -188,12 +239,12 @@ static void bbox_molecule(const pgo_problem *p, int b, double *out, double eps, 
                                         ? d2
                                         : fmax(dx * dx, fmax(dy * dy, dz * dz));
                         if (fabs(m2 - r * r) <= eps * r * r) {
-                            band[v] += exp(-d2 / s2);
+                            band[v] += term(p, b, p->sigma[c], dx, dy, dz);
                             continue;
                         }
                     }
                     if (!inside(p->cutoff, dx, dy, dz, r)) continue;
-                    out[v] += exp(-d2 / s2);
+                    out[v] += term(p, b, p->sigma[c], dx, dy, dz);
                 }
             }
         }
@@ -245,7 +296,8 @@ int pgo_voxelize_band(const pgo_problem *p, double eps, double *out_in, double *
  * Separable form (Sec. III-A after Eq. 5; Sec. VI-A): for the no-cutoff and box-cutoff
  * indicators the Gaussian factors per axis, so the grid is the per-channel sum of outer
  * products of three per-axis tables
- *   g_x[a][i] = [|d_x| <= r] exp(-d_x^2 / 2 sigma^2)  (the bracket is 1 with no cutoff)
+ *   g_x[a][i] = [|d_x| <= r] exp(-d_x^2 / 2 sigma^2)  (the bracket is 1 with no cutoff),
+ * or [|d_x| <= r] times the erf factor in the voxel-integrated form,
  * and G[c,i,j,k] = sum_{a: elem(a)=c} g_x[a][i] g_y[a][j] g_z[a][k].
  * The spherical indicator does not factor; that case is rejected.
  */
@@ -273,7 +325,10 @@ int pgo_separable(const pgo_problem *p, double *out, int n_threads)
                 for (long i = 0; i < n[ax]; ++i) {
                     double d = disp(p, b, ax, i, p->coords[3 * a + ax]);
                     int keep = (p->cutoff == PGO_NONE) || fabs(d) <= r;
-                    g[ax][i] = keep ? exp(-d * d / s2) : 0.0;
+                    double f = p->form == PGO_INTEGRAL
+                                   ? erf_factor(d, p->spacing[3 * b + ax], p->sigma[c])
+                                   : exp(-d * d / s2);
+                    g[ax][i] = keep ? f : 0.0;
                 }
             for (long i = 0; i < p->nx; ++i)
                 for (long j = 0; j < p->ny; ++j)
@@ -289,7 +344,9 @@ int pgo_separable(const pgo_problem *p, double *out, int n_threads)
 
 /*
  * Coordinate gradient of L = <W, G> (Sec. IV-C):
- *   dL/dx_a = sum_v W(v) chi(d) exp(-|d|^2/2 sigma^2) d / sigma^2,  d = v - x_a.
+ *   dL/dx_a = sum_v W(v) chi(d) exp(-|d|^2/2 sigma^2) d / sigma^2,  d = v - x_a,
+ * and in the voxel-integrated form, per axis, the derivative of that axis's erf factor
+ * times the other two factors.
  * mode 0 visits every voxel of the atom's channel, mode 1 only its cutoff box.
  * W has the grid layout [B][C][nx][ny][nz]; grad is [N][3].
  */
@@ -323,17 +380,27 @@ int pgo_gradient(const pgo_problem *p, int mode, const double *W, double *grad, 
                         long k = p->periodic ? wrap_index(ku, p->nz) : ku;
                         double dz = disp(p, b, 2, k, z);
                         if (!inside(p->cutoff, dx, dy, dz, r)) continue;
-                        double w = W[grid_index(p, b, c, i, j, k)] *
-                                   exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * sg2));
-                        gx += w * dx;
-                        gy += w * dy;
-                        gz += w * dz;
+                        double Wv = W[grid_index(p, b, c, i, j, k)];
+                        if (p->form == PGO_INTEGRAL) {
+                            const double *h = p->spacing + 3 * b, sg = p->sigma[c];
+                            double fx = erf_factor(dx, h[0], sg), fy = erf_factor(dy, h[1], sg);
+                            double fz = erf_factor(dz, h[2], sg);
+                            gx += Wv * erf_factor_dmu(dx, h[0], sg) * fy * fz;
+                            gy += Wv * fx * erf_factor_dmu(dy, h[1], sg) * fz;
+                            gz += Wv * fx * fy * erf_factor_dmu(dz, h[2], sg);
+                        } else {
+                            double w = Wv * exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * sg2));
+                            gx += w * dx;
+                            gy += w * dy;
+                            gz += w * dz;
+                        }
                     }
                 }
             }
-            grad[3 * a + 0] = gx / sg2;
-            grad[3 * a + 1] = gy / sg2;
-            grad[3 * a + 2] = gz / sg2;
+            /* The point form's common 1/sigma^2 is applied once at the end. */
+            grad[3 * a + 0] = p->form == PGO_INTEGRAL ? gx : gx / sg2;
+            grad[3 * a + 1] = p->form == PGO_INTEGRAL ? gy : gy / sg2;
+            grad[3 * a + 2] = p->form == PGO_INTEGRAL ? gz : gz / sg2;
         }
     }
     return PGO_OK;
@@ -358,7 +425,6 @@ int pgo_fd_gradient_frozen(const pgo_problem *p, const double *W, double step, d
     for (int b = 0; b < p->n_mol; ++b) {
         for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a) {
             int c = p->elem[a];
-            double s2 = 2.0 * p->sigma[c] * p->sigma[c];
             double r = p->cutoff_k * p->sigma[c];
             double x = p->coords[3 * a + 0], y = p->coords[3 * a + 1], z = p->coords[3 * a + 2];
             double lp[3] = {0, 0, 0}, lm[3] = {0, 0, 0};
@@ -374,9 +440,9 @@ int pgo_fd_gradient_frozen(const pgo_problem *p, const double *W, double step, d
                         for (int ax = 0; ax < 3; ++ax) {
                             double e[3] = {d[0], d[1], d[2]};
                             e[ax] = d[ax] - step; /* atom moved by +step */
-                            lp[ax] += w * exp(-(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) / s2);
+                            lp[ax] += w * term(p, b, p->sigma[c], e[0], e[1], e[2]);
                             e[ax] = d[ax] + step; /* atom moved by -step */
-                            lm[ax] += w * exp(-(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) / s2);
+                            lm[ax] += w * term(p, b, p->sigma[c], e[0], e[1], e[2]);
                         }
                     }
                 }

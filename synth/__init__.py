@@ -90,6 +90,7 @@ class Workload:
     periodic: bool
     out_dtype: str             # "f32" | "f16" | "bf16"
     description: str = ""
+    form: str = "point"        # "point" (sampled at voxel centres) | "integral" (erf form)
 
     @property
     def voxels_per_grid(self) -> int:
@@ -212,6 +213,16 @@ def precision_form(shard: int | None = None, n_mol: int = 4096) -> Workload:
                     f"{n_mol} QM9-shaped molecules, 5ch 64^3 @0.25A, no cutoff")
 
 
+def precision_form_integral(shard: int | None = None, n_mol: int = 4096) -> Workload:
+    """The precision-form batch with the voxel-integrated (erf) voxel function of Sec. III-A:
+    the same molecules and grid, each voxel holding the Gaussian's integral over it."""
+    wl = precision_form(shard, n_mol)
+    wl.name = "precision_form_integral"
+    wl.form = "integral"
+    wl.description = f"{n_mol} QM9-shaped molecules, 5ch 64^3 @0.25A, no cutoff, erf voxel integrals"
+    return wl
+
+
 ZIPF_EXPONENT = 1.2
 CRYSTAL_ELEMENTS = 10
 JAMMING_SKIP = 0.32
@@ -319,6 +330,7 @@ WORKLOADS = {
     "plain_small": plain_small,
     "qm9_shaped": qm9_shaped,
     "precision_form": precision_form,
+    "precision_form_integral": precision_form_integral,
     "crystal_shaped": crystal_shaped,
     "differentiation": differentiation,
 }
