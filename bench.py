@@ -161,16 +161,17 @@ def write_probe_gbs(nbytes=4 << 30, reps=10):
     return max(res.values()), res
 
 
-KERNEL_SOURCES = {"direct": "pg_direct.cu", "separable": "pg_separable.cu",
-                  "backward": "pg_backward.cu"}
+KERNEL_SOURCES = {"direct": ("direct_kernel.cuh",), "separable": ("pg_separable.cu",),
+                  "backward": ("pg_backward.cu",)}
 
 
 def kernel_source_sha(kernel: str) -> str:
-    """First 16 hex digits of the SHA-256 of the kernel's CUDA source file."""
+    """First 16 hex digits of the SHA-256 of the kernel's CUDA source."""
     h = hashlib.sha256()
-    p = os.path.join(ROOT, "paper_2211_08506_gb300", "csrc", KERNEL_SOURCES[kernel])
-    if os.path.exists(p):
-        h.update(open(p, "rb").read())
+    for f in KERNEL_SOURCES[kernel]:
+        p = os.path.join(ROOT, "paper_2211_08506_gb300", "csrc", f)
+        if os.path.exists(p):
+            h.update(open(p, "rb").read())
     return h.hexdigest()[:16]
 
 

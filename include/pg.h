@@ -16,6 +16,14 @@
  * PG_CUTOFF_NONE: always 1.  Sec. VI-B truncates where the Gaussian is negligible; here
  * the truncation radius is explicit.
  *
+ * With voxel_form = PG_FORM_INTEGRAL each voxel instead holds the normalised Gaussian
+ * integrated over the voxel (Sec. III-A, the gridding function after Eq. 5 and its per-axis
+ * erf integrals): the product over axes of
+ *     (1/2) [erf((e_hi - x) / (sqrt(2) sigma_c)) - erf((e_lo - x) / (sqrt(2) sigma_c))],
+ * with e_lo, e_hi the voxel's edges and x the atom coordinate (its nearest image relative to
+ * the voxel centre when periodic); chi is still evaluated at the voxel centre.  Each atom
+ * then adds exactly one to a grid that covers its support (the conservation law after Eq. 5).
+ *
  * General conventions
  *  - All buffers belong to the caller.  The library keeps only a small per-device error
  *    word, per-plan buffers (pg_plan_*) and an in-memory tuning cache; pg_shutdown()
@@ -57,6 +65,9 @@ typedef enum {
 typedef enum { PG_F32 = 0, PG_F16 = 1, PG_BF16 = 2 } pg_dtype;
 
 typedef enum { PG_CUTOFF_SPHERE = 0, PG_CUTOFF_NONE = 1, PG_CUTOFF_BOX = 2 } pg_cutoff;
+
+/* Voxel function: the point sample at the voxel centre, or the voxel integral (erf form). */
+typedef enum { PG_FORM_POINT = 0, PG_FORM_INTEGRAL = 1 } pg_form;
 
 typedef enum {
     PG_PATH_AUTO = 0,      /* tuned choice for this problem's bucket, else DIRECT */
@@ -104,6 +115,7 @@ typedef struct {
  *   cutoff       pg_cutoff
  *   periodic     0: open boundaries; 1: orthorhombic cell of edges n*h with nearest-image
  *                distances (requires r_c < L/2 on every axis, checked on the device)
+ *   voxel_form   pg_form (0 = point sample; zero-initialised grids keep the point form)
  */
 typedef struct {
     int32_t nx, ny, nz;
@@ -112,6 +124,7 @@ typedef struct {
     float cutoff_k;
     int32_t cutoff;
     int32_t periodic;
+    int32_t voxel_form;
 } pg_grid;
 
 /*

@@ -20,6 +20,7 @@ DTYPES = {"f32": (B.PG_F32, torch.float32), "f16": (B.PG_F16, torch.float16),
 TORCH_TO_PG = {torch.float32: B.PG_F32, torch.float16: B.PG_F16, torch.bfloat16: B.PG_BF16}
 CUTOFFS = {"sphere": B.PG_CUTOFF_SPHERE, "none": B.PG_CUTOFF_NONE, "box": B.PG_CUTOFF_BOX}
 PATHS = {"auto": B.PG_PATH_AUTO, "direct": B.PG_PATH_DIRECT, "separable": B.PG_PATH_SEPARABLE}
+FORMS = {"point": B.PG_FORM_POINT, "integral": B.PG_FORM_INTEGRAL}
 
 
 @dataclass
@@ -34,12 +35,14 @@ class Grid:
     cutoff: str = "sphere"
     cutoff_k: float = 3.0
     periodic: bool = False
+    form: str = "point"          # "point" sample or voxel "integral" (erf form)
     _sigma_buf: object = field(default=None, repr=False, compare=False)
 
     @classmethod
     def from_workload(cls, wl) -> "Grid":
         return cls(wl.nx, wl.ny, wl.nz, wl.n_channels, [float(s) for s in wl.sigma],
-                   wl.cutoff, float(wl.cutoff_k), bool(wl.periodic))
+                   wl.cutoff, float(wl.cutoff_k), bool(wl.periodic),
+                   getattr(wl, "form", "point"))
 
     def to_c(self) -> B.pg_grid:
         sig = (ctypes.c_float * len(self.sigma))(*[float(s) for s in self.sigma])
@@ -48,7 +51,7 @@ class Grid:
                          n_channels=int(self.n_channels),
                          sigma=ctypes.cast(sig, ctypes.POINTER(ctypes.c_float)),
                          cutoff_k=float(self.cutoff_k), cutoff=CUTOFFS[self.cutoff],
-                         periodic=1 if self.periodic else 0)
+                         periodic=1 if self.periodic else 0, voxel_form=FORMS[self.form])
 
     def out_shape(self, n_mol: int):
         return (n_mol, self.n_channels, self.nx, self.ny, self.nz)

@@ -20,6 +20,7 @@ PG_ERR_TIMEOUT = 5
 
 PG_F32, PG_F16, PG_BF16 = 0, 1, 2
 PG_CUTOFF_SPHERE, PG_CUTOFF_NONE, PG_CUTOFF_BOX = 0, 1, 2
+PG_FORM_POINT, PG_FORM_INTEGRAL = 0, 1
 PG_PATH_AUTO, PG_PATH_DIRECT, PG_PATH_SEPARABLE = 0, 1, 2
 PG_MAX_CHANNELS = 64
 
@@ -59,6 +60,7 @@ class pg_grid(ctypes.Structure):
         ("cutoff_k", ctypes.c_float),
         ("cutoff", ctypes.c_int32),
         ("periodic", ctypes.c_int32),
+        ("voxel_form", ctypes.c_int32),
     ]
 
 

@@ -130,6 +130,8 @@ pg_status validate(const pg_batch *b, const pg_grid *g)
                     (double)g->cutoff_k);
     if (g->periodic != 0 && g->periodic != 1)
         return fail(PG_ERR_INVALID_ARG, "periodic must be 0 or 1");
+    if (g->voxel_form != PG_FORM_POINT && g->voxel_form != PG_FORM_INTEGRAL)
+        return fail(PG_ERR_INVALID_ARG, "unknown voxel_form %d", g->voxel_form);
     const long long plane = (long long)g->ny * g->nz;
     if (plane > INT32_MAX || (long long)g->nx * plane > INT32_MAX)
         return fail(PG_ERR_INVALID_ARG, "one channel grid must hold fewer than 2^31 voxels");
@@ -157,12 +159,16 @@ void make_geometry(const pg_batch *b, const pg_grid *g, Geometry *G)
     G->C = g->n_channels;
     G->cutoff = g->cutoff;
     G->periodic = g->periodic;
+    G->form = g->voxel_form;
     const double log2e = 1.4426950408889634;
+    const double pi = 3.14159265358979323846;
     for (int c = 0; c < g->n_channels; ++c) {
         const double s = g->sigma[c];
         const double r = (double)g->cutoff_k * s;
         G->q[c] = (float)(log2e / (2.0 * s * s));
         G->inv_s2[c] = (float)(1.0 / (s * s));
+        G->kerf[c] = (float)(1.0 / (std::sqrt(2.0) * s));
+        G->kdmu[c] = (float)(1.0 / (std::sqrt(2.0 * pi) * s));
         if (g->cutoff == PG_CUTOFF_NONE) {
             G->r2[c] = INFINITY;
             G->rcull[c] = INFINITY;
@@ -206,7 +212,8 @@ int direct_plane_stride(const pg_grid *g)
 // whose mean is that small keeps the gather-only instantiation and its higher occupancy.
 bool direct_scatter_on(const pg_batch *b, const pg_grid *g, const pg_tuning &t)
 {
-    return !t.gather_only && direct_plane_stride(g) > 0 && b->n_atoms > 32LL * b->n_mol;
+    return !t.gather_only && g->voxel_form == PG_FORM_POINT && direct_plane_stride(g) > 0 &&
+           b->n_atoms > 32LL * b->n_mol;
 }
 
 bool vec_stores_ok(const void *out, const pg_grid *g, int dtype)
@@ -286,8 +293,9 @@ std::string bucket_key(const pg_batch *b, const pg_grid *g, int dtype, int path,
     const double apm = b->n_mol > 0 ? (double)b->n_atoms / b->n_mol : 0.0;
     const int bucket = apm >= 1.0 ? (int)std::floor(std::log2(apm)) : 0;
     char buf[256];
-    snprintf(buf, sizeof buf, "%s|%dx%dx%d|C%d|dt%d|cut%d|per%d|apm%d|path%d", d.name.c_str(),
-             g->nx, g->ny, g->nz, g->n_channels, dtype, g->cutoff, g->periodic, bucket, path);
+    snprintf(buf, sizeof buf, "%s|%dx%dx%d|C%d|dt%d|cut%d|per%d|apm%d|path%d%s", d.name.c_str(),
+             g->nx, g->ny, g->nz, g->n_channels, dtype, g->cutoff, g->periodic, bucket, path,
+             g->voxel_form == PG_FORM_INTEGRAL ? "|form1" : "");
     return buf;
 }
 

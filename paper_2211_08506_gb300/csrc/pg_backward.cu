@@ -7,7 +7,10 @@
 // with respect to x_a is chi(d) exp(-|d|^2 / 2 sigma^2) d / sigma^2, so
 //     dL/dx_a = (1/sigma^2) sum_{v : chi} g_{c(a)}(v) exp(-|d|^2 / 2 sigma^2) d.
 // (The indicator is piecewise constant; its jump at the cutoff surface is not part of the
-// derivative.)
+// derivative.)  In the voxel-integrated form (Sec. III-A) each term is a product of per-axis
+// erf integrals, and the derivative along an axis replaces that axis's factor by its
+// derivative (Sec. IV-C's separable-product rule), which is a difference of the Gaussian at
+// the voxel's two edges.
 //
 // One warp owns one atom at a time (atoms handed out from a per-launch counter) and walks the
 // voxels of the atom's cutoff box (clamped to the grid, or wrapped for periodic cells), 32
@@ -79,7 +82,7 @@ __device__ __forceinline__ int wrap_index(int i, int n)
     return r < 0 ? r + n : r;
 }
 
-template <typename GT, int CUT, bool PER>
+template <typename GT, int CUT, bool PER, int FORM>
 __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
 {
     const Geometry &G = A.geo;
@@ -155,6 +158,7 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
             const float ax = __ldg(A.in.coords + 3 * a), ay = __ldg(A.in.coords + 3 * a + 1),
                         az = __ldg(A.in.coords + 3 * a + 2);
             const float q = G.q[c], r2 = G.r2[c], rc = G.rcull[c];
+            const float kf = G.kerf[c], kd = G.kdmu[c];
             int ilo, ni, jlo, nj, klo, nk;
             axis_support<CUT, PER>(ax, ox, hx, G.nx, rc, ilo, ni);
             axis_support<CUT, PER>(ay, oy, hy, G.ny, rc, jlo, nj);
@@ -182,7 +186,7 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
             float sx = 0.0f, sy = 0.0f, sz = 0.0f;
             constexpr int U = 4;  // voxels in flight per lane
             for (long long f0 = lane; f0 < total; f0 += 32 * U) {
-                float gv[U], dxv[U], dyv[U], dzv[U];
+                float gv[U], dxv[U], dyv[U], dzv[U];  // FORM 1: gv unused, d*v hold terms
                 bool inv[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -216,7 +220,16 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
                     inv[u] = valid && in;
                     gv[u] = valid ? to_float<GT>(g[(long long)i * plane + (long long)j * G.nz + k])
                                   : 0.0f;
-                    gv[u] *= inv[u] ? ex2_approx(-q * d2) : 0.0f;
+                    if (FORM == 0) {
+                        gv[u] *= inv[u] ? ex2_approx(-q * d2) : 0.0f;
+                    } else {
+                        const float w = inv[u] ? gv[u] : 0.0f;
+                        const float fx = erf_axis(dx, hx, kf), fy = erf_axis(dy, hy, kf),
+                                    fz = erf_axis(dz, hz, kf);
+                        dxv[u] = w * erf_axis_dmu(dx, hx, kf, kd) * fy * fz;
+                        dyv[u] = w * fx * erf_axis_dmu(dy, hy, kf, kd) * fz;
+                        dzv[u] = w * fx * fy * erf_axis_dmu(dz, hz, kf, kd);
+                    }
                     // advance this lane by 32 voxels
                     fk += sk;
                     if (fk >= nk) {
@@ -232,9 +245,15 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
-                    sx = fmaf(gv[u], dxv[u], sx);
-                    sy = fmaf(gv[u], dyv[u], sy);
-                    sz = fmaf(gv[u], dzv[u], sz);
+                    if (FORM == 0) {
+                        sx = fmaf(gv[u], dxv[u], sx);
+                        sy = fmaf(gv[u], dyv[u], sy);
+                        sz = fmaf(gv[u], dzv[u], sz);
+                    } else {
+                        sx += dxv[u];
+                        sy += dyv[u];
+                        sz += dzv[u];
+                    }
                 }
             }
 #pragma unroll
@@ -244,7 +263,7 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
                 sz += __shfl_xor_sync(0xffffffffu, sz, o);
             }
             if (lane == 0) {
-                const float s = G.inv_s2[c];
+                const float s = FORM == 0 ? G.inv_s2[c] : 1.0f;
                 A.grad_coords[3 * a] = sx * s;
                 A.grad_coords[3 * a + 1] = sy * s;
                 A.grad_coords[3 * a + 2] = sz * s;
@@ -264,26 +283,37 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
     }
 }
 
-template <typename GT>
-const void *pick(int cutoff, int periodic)
+template <typename GT, int FORM>
+const void *pick_form(int cutoff, int periodic)
 {
     if (periodic) {
-        if (cutoff == PG_CUTOFF_SPHERE) return (const void *)backward_kernel<GT, PG_CUTOFF_SPHERE, true>;
-        if (cutoff == PG_CUTOFF_BOX) return (const void *)backward_kernel<GT, PG_CUTOFF_BOX, true>;
-        return (const void *)backward_kernel<GT, PG_CUTOFF_NONE, true>;
+        if (cutoff == PG_CUTOFF_SPHERE)
+            return (const void *)backward_kernel<GT, PG_CUTOFF_SPHERE, true, FORM>;
+        if (cutoff == PG_CUTOFF_BOX)
+            return (const void *)backward_kernel<GT, PG_CUTOFF_BOX, true, FORM>;
+        return (const void *)backward_kernel<GT, PG_CUTOFF_NONE, true, FORM>;
     }
-    if (cutoff == PG_CUTOFF_SPHERE) return (const void *)backward_kernel<GT, PG_CUTOFF_SPHERE, false>;
-    if (cutoff == PG_CUTOFF_BOX) return (const void *)backward_kernel<GT, PG_CUTOFF_BOX, false>;
-    return (const void *)backward_kernel<GT, PG_CUTOFF_NONE, false>;
+    if (cutoff == PG_CUTOFF_SPHERE)
+        return (const void *)backward_kernel<GT, PG_CUTOFF_SPHERE, false, FORM>;
+    if (cutoff == PG_CUTOFF_BOX) return (const void *)backward_kernel<GT, PG_CUTOFF_BOX, false, FORM>;
+    return (const void *)backward_kernel<GT, PG_CUTOFF_NONE, false, FORM>;
+}
+
+template <typename GT>
+const void *pick(int cutoff, int periodic, int form)
+{
+    return form == PG_FORM_INTEGRAL ? pick_form<GT, 1>(cutoff, periodic)
+                                    : pick_form<GT, 0>(cutoff, periodic);
 }
 
 }  // namespace
 
 cudaError_t backward_plan(const BackwardArgs &a, int grad_dtype, int sm_count, KernelLaunch *kl)
 {
-    const void *f = grad_dtype == PG_F32   ? pick<float>(a.geo.cutoff, a.geo.periodic)
-                    : grad_dtype == PG_F16 ? pick<__half>(a.geo.cutoff, a.geo.periodic)
-                                           : pick<__nv_bfloat16>(a.geo.cutoff, a.geo.periodic);
+    const int cut = a.geo.cutoff, per = a.geo.periodic, form = a.geo.form;
+    const void *f = grad_dtype == PG_F32   ? pick<float>(cut, per, form)
+                    : grad_dtype == PG_F16 ? pick<__half>(cut, per, form)
+                                           : pick<__nv_bfloat16>(cut, per, form);
     const int threads = 256;
     int per_sm = 0;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, 0);

@@ -27,7 +27,31 @@ struct Geometry {
     float r2[kMaxC];     // r_c^2, the exact per-voxel cutoff test
     float rcull[kMaxC];  // r_c widened by a relative 1e-5 for conservative culling
     float inv_s2[kMaxC]; // 1 / sigma_c^2 (adjoint)
+    int form;            // pg_form
+    float kerf[kMaxC];   // 1 / (sqrt(2) sigma_c): erf argument scale of the integral form
+    float kdmu[kMaxC];   // kerf / sqrt(pi): scale of the integral form's derivative
 };
+
+#ifdef __CUDACC__
+// Voxel-integrated form (Sec. III-A, per-axis erf integrals): the normalised Gaussian's
+// integral along one axis over the voxel whose centre lies at displacement d from the atom,
+// with k = 1 / (sqrt(2) sigma).  The factor is even in d; when both edges lie on the same
+// side of the atom it is taken as a difference of erfc values, which does not cancel.
+__device__ __forceinline__ float erf_axis(float d, float h, float k)
+{
+    const float a = fabsf(d);
+    const float lo = (a - 0.5f * h) * k, hi = (a + 0.5f * h) * k;
+    return lo > 0.0f ? 0.5f * (erfcf(lo) - erfcf(hi)) : 0.5f * (erff(hi) + erff(-lo));
+}
+
+// Derivative of erf_axis with respect to the atom coordinate (d = centre - atom), from
+// d/dt erf(t) = (2 / sqrt(pi)) exp(-t^2); kd = k / sqrt(pi).
+__device__ __forceinline__ float erf_axis_dmu(float d, float h, float k, float kd)
+{
+    const float lo = (d - 0.5f * h) * k, hi = (d + 0.5f * h) * k;
+    return kd * (expf(-lo * lo) - expf(-hi * hi));
+}
+#endif
 
 struct Inputs {
     const float *coords;
@@ -93,6 +117,8 @@ struct KernelLaunch {
 };
 
 // Direct per-voxel gather (pg_direct.cu).
+// The direct kernel's voxel-integrated instantiation for one launch (pg_direct_integral.cu).
+const void *pick_direct_integral(int dtype, bool vec_ok, int cutoff, int periodic, int hint);
 cudaError_t direct_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tuning &t,
                         int sm_count, KernelLaunch *kl);
 

@@ -260,12 +260,15 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
     return *reinterpret_cast<uint32_t *>(&v);
 }
 
-// Per-axis factor chi_axis(d) 2^(-q d^2).
+// Per-axis factor: chi_axis(d) 2^(-q d^2) for the point sample, or chi_axis(d) times the
+// voxel's erf integral along the axis (spacing h, k = 1 / (sqrt(2) sigma)) for the
+// voxel-integrated form of Sec. III-A.
 template <int CUT>
-__device__ __forceinline__ float axis_factor(float d, float q, float r2)
+__device__ __forceinline__ float axis_factor(float d, float q, float r2, int form, float h,
+                                             float k)
 {
     const float d2 = d * d;
-    const float v = ex2_approx(-q * d2);
+    const float v = form ? erf_axis(d, h, k) : ex2_approx(-q * d2);
     return (CUT == PG_CUTOFF_BOX && d2 > r2) ? 0.0f : v;
 }
 
@@ -463,7 +466,7 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                                 pos = make_float4(__ldg(A.in.coords + 3 * ai),
                                                   __ldg(A.in.coords + 3 * ai + 1),
                                                   __ldg(A.in.coords + 3 * ai + 2), G.q[e]);
-                                aux = make_float4(G.r2[e], (float)e, 0.f, 0.f);
+                                aux = make_float4(G.r2[e], (float)e, G.kerf[e], 0.f);
                             } else if (m0 == 0) {
                                 atomicOr(A.err, PG_DEVERR_ELEMENT);
                             }
@@ -479,7 +482,8 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                         if (atom_aux[j].y >= 0.0f) {
                             float d = fmaf((float)y + 0.5f, hy, oy) - p.y;
                             if (PER) d = wrap(d, Ly, iLy);
-                            v = axis_factor<CUT>(d, p.w, atom_aux[j].x);
+                            v = axis_factor<CUT>(d, p.w, atom_aux[j].x, G.form, hy,
+                                                 atom_aux[j].z);
                         }
                         tgy[y * kTab + j] = v;
                     }
@@ -490,7 +494,8 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                         if (atom_aux[j].y >= 0.0f) {
                             float d = fmaf((float)z + 0.5f, hz, oz) - p.z;
                             if (PER) d = wrap(d, Lz, iLz);
-                            v = axis_factor<CUT>(d, p.w, atom_aux[j].x);
+                            v = axis_factor<CUT>(d, p.w, atom_aux[j].x, G.form, hz,
+                                                 atom_aux[j].z);
                         }
                         tgz[z * kTab + j] = v;
                     }
@@ -507,7 +512,7 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                             if (row_ok && (int)aux.y == row_c) {
                                 float d = vx - p.x;
                                 if (PER) d = wrap(d, Lx, iLx);
-                                v[t] = axis_factor<CUT>(d, p.w, aux.x);
+                                v[t] = axis_factor<CUT>(d, p.w, aux.x, G.form, hx, aux.z);
                             }
                         }
                         const uint4 w = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
@@ -813,7 +818,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                                     pos = make_float4(__ldg(A.in.coords + 3 * ai),
                                                       __ldg(A.in.coords + 3 * ai + 1),
                                                       __ldg(A.in.coords + 3 * ai + 2), G.q[e]);
-                                    aux = make_float4(G.r2[e], (float)e, 0.f, 0.f);
+                                    aux = make_float4(G.r2[e], (float)e, G.kerf[e], 0.f);
                                 } else if (it.m0 == 0) {
                                     atomicOr(A.err, PG_DEVERR_ELEMENT);
                                 }
@@ -829,7 +834,8 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             if (atom_aux[j].y >= 0.0f) {
                                 float d = fmaf((float)y + 0.5f, it.hy, it.oy) - q4.y;
                                 if (PER) d = wrap(d, Ly, iLy);
-                                v = axis_factor<CUT>(d, q4.w, atom_aux[j].x);
+                                v = axis_factor<CUT>(d, q4.w, atom_aux[j].x, G.form, it.hy,
+                                                     atom_aux[j].z);
                             }
                             tgy[y * kTab + j] = v;
                         }
@@ -840,7 +846,8 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             if (atom_aux[j].y >= 0.0f) {
                                 float d = fmaf((float)z + 0.5f, it.hz, it.oz) - q4.z;
                                 if (PER) d = wrap(d, Lz, iLz);
-                                v = axis_factor<CUT>(d, q4.w, atom_aux[j].x);
+                                v = axis_factor<CUT>(d, q4.w, atom_aux[j].x, G.form, it.hz,
+                                                     atom_aux[j].z);
                             }
                             tgz[z * kTab + j] = v;
                         }
@@ -861,7 +868,8 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                                 if (row_ok && (int)aux.y == row_c) {
                                     float d = vx - q4.x;
                                     if (PER) d = wrap(d, Lx, iLx);
-                                    v[t] = axis_factor<CUT>(d, q4.w, aux.x);
+                                    v[t] = axis_factor<CUT>(d, q4.w, aux.x, G.form, it.hx,
+                                                            aux.z);
                                 }
                             }
                             *reinterpret_cast<uint4 *>(sa + (p >> 3) * 512 + jg * 128 +

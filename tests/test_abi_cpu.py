@@ -61,6 +61,7 @@ def _grid(lib, **kw):
     ("cutoff", 7, "cutoff mode"),
     ("cutoff_k", -1.0, "cutoff_k"),
     ("periodic", 2, "periodic"),
+    ("voxel_form", 5, "voxel_form"),
 ])
 def test_host_validation_rejects_bad_grid(lib, field, value, needle):
     g, keep = _grid(lib, **{field: value})
