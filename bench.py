@@ -422,6 +422,7 @@ def run_ours(args):
             "description": wl.description,
             "batch_per_gpu": B,
             "grid": [wl.n_channels, wl.nx, wl.ny, wl.nz],
+            "voxel_form": wl.form,
             "out_dtype": dtype,
             "path": kernel,
             "tuning": tuning,
@@ -498,8 +499,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="qm9_shaped",
-                    choices=["qm9_shaped", "plain_small", "precision_form", "crystal_shaped",
-                             "differentiation"])
+                    choices=["qm9_shaped", "plain_small", "precision_form",
+                             "precision_form_integral", "crystal_shaped", "differentiation"])
     ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default=None)
     ap.add_argument("--path", choices=["auto", "direct", "separable"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -43,6 +43,7 @@ namespace {
 
 constexpr int kKC = 32;         // atoms per K chunk (two K=16 MMA steps)
 constexpr int kTab = 36;        // floats per table row: 32 atoms + 4 pad (conflict-free reads)
+constexpr int kTabX = 33;       // g_x rows: A-tile threads read one atom across 32 rows
 constexpr int kRows = 128;      // M tile = CTA threads = TMEM lanes
 constexpr unsigned kWaitLimit = 1u << 24;         // polls of one mbarrier wait, at most
 constexpr unsigned long long kWaitNs = 2000000000ull;  // and at most 2 s of wall time
@@ -263,12 +264,11 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi)
 // Per-axis factor: chi_axis(d) 2^(-q d^2) for the point sample, or chi_axis(d) times the
 // voxel's erf integral along the axis (spacing h, k = 1 / (sqrt(2) sigma)) for the
 // voxel-integrated form of Sec. III-A.
-template <int CUT>
-__device__ __forceinline__ float axis_factor(float d, float q, float r2, int form, float h,
-                                             float k)
+template <int CUT, int FORM>
+__device__ __forceinline__ float axis_factor(float d, float q, float r2, float h, float k)
 {
     const float d2 = d * d;
-    const float v = form ? erf_axis(d, h, k) : ex2_approx(-q * d2);
+    const float v = FORM ? erf_axis(d, h, k) : ex2_approx(-q * d2);
     return (CUT == PG_CUTOFF_BOX && d2 > r2) ? 0.0f : v;
 }
 
@@ -382,7 +382,7 @@ __device__ __forceinline__ void store_warp_rows(T *out, const unsigned char *sta
     }
 }
 
-template <typename T, int CUT, bool PER>
+template <typename T, int CUT, bool PER, int FORM>
 __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                         if (atom_aux[j].y >= 0.0f) {
                             float d = fmaf((float)y + 0.5f, hy, oy) - p.y;
                             if (PER) d = wrap(d, Ly, iLy);
-                            v = axis_factor<CUT>(d, p.w, atom_aux[j].x, G.form, hy,
+                            v = axis_factor<CUT, FORM>(d, p.w, atom_aux[j].x, hy,
                                                  atom_aux[j].z);
                         }
                         tgy[y * kTab + j] = v;
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                         if (atom_aux[j].y >= 0.0f) {
                             float d = fmaf((float)z + 0.5f, hz, oz) - p.z;
                             if (PER) d = wrap(d, Lz, iLz);
-                            v = axis_factor<CUT>(d, p.w, atom_aux[j].x, G.form, hz,
+                            v = axis_factor<CUT, FORM>(d, p.w, atom_aux[j].x, hz,
                                                  atom_aux[j].z);
                         }
                         tgz[z * kTab + j] = v;
@@ -512,7 +512,7 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                             if (row_ok && (int)aux.y == row_c) {
                                 float d = vx - p.x;
                                 if (PER) d = wrap(d, Lx, iLx);
-                                v[t] = axis_factor<CUT>(d, p.w, aux.x, G.form, hx, aux.z);
+                                v[t] = axis_factor<CUT, FORM>(d, p.w, aux.x, hx, aux.z);
                             }
                         }
                         const uint4 w = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
@@ -607,10 +607,10 @@ constexpr int kPipeStages = 2;
 constexpr int kPipeThreads = 288;  // 9 warps
 
 struct PipeLayout {
-    int bars, tmem, flag, atoms, stage0, stage_bytes, a_bytes, gy, gz, out, out_stride, total;
+    int bars, tmem, flag, atoms, stage0, stage_bytes, a_bytes, gx, gy, gz, out, out_stride, total;
 };
 
-__host__ __device__ inline PipeLayout pipe_layout(int ny, int nz, int n_tile, int esz)
+__host__ __device__ inline PipeLayout pipe_layout(int nx, int ny, int nz, int n_tile, int esz)
 {
     PipeLayout L;
     int o = 0;
@@ -628,6 +628,9 @@ __host__ __device__ inline PipeLayout pipe_layout(int ny, int nz, int n_tile, in
     L.stage_bytes = align_up(L.a_bytes + n_tile * kKC * 2, 1024);
     L.stage0 = o;
     o += kPipeStages * L.stage_bytes;
+    L.gx = o;
+    o += nx * kTabX * 4;
+    o = align_up(o, 128);
     L.gy = o;
     o += ny * kTab * 4;
     o = align_up(o, 128);
@@ -729,7 +732,7 @@ __device__ __forceinline__ PipeItem pipe_item(const SeparableArgs &A, long long 
     return it;
 }
 
-template <typename T, int CUT, bool PER>
+template <typename T, int CUT, bool PER, int FORM>
 __global__ void __launch_bounds__(kPipeThreads, 2)
     separable_pipe_kernel(const __grid_constant__ SeparableArgs A)
 {
@@ -739,7 +742,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
     const int warp = tid >> 5;
     const int lane = tid & 31;
     const int n_tile = A.n_tile;
-    const PipeLayout L = pipe_layout(G.ny, G.nz, n_tile, (int)sizeof(T));
+    const PipeLayout L = pipe_layout(G.nx, G.ny, G.nz, n_tile, (int)sizeof(T));
     const uint32_t bars = smem_u32(smem + L.bars);
     auto b_full = [&](int s) { return bars + 8u * s; };
     auto b_empty = [&](int s) { return bars + 8u * (2 + s); };
@@ -777,6 +780,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
         const int p = tid - 128;
         float4 *atom_pos = reinterpret_cast<float4 *>(smem + L.atoms);
         float4 *atom_aux = atom_pos + kKC;
+        float *tgx = reinterpret_cast<float *>(smem + L.gx);
         float *tgy = reinterpret_cast<float *>(smem + L.gy);
         float *tgz = reinterpret_cast<float *>(smem + L.gz);
         long long stage_item[kPipeStages] = {-1, -1};
@@ -827,6 +831,20 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             atom_aux[p] = aux;
                         }
                         producer_sync();
+                        // Per-axis tables of this K chunk: g_y, g_z, and for the erf form also
+                        // g_x (an erf per A entry would cost more than the table).
+                        for (int i = p; FORM == 1 && i < G.nx * kKC; i += 128) {
+                            const int x = i / kKC, j = i - (i / kKC) * kKC;
+                            const float4 q4 = atom_pos[j];
+                            float v = 0.0f;
+                            if (atom_aux[j].y >= 0.0f) {
+                                float d = fmaf((float)x + 0.5f, it.hx, it.ox) - q4.x;
+                                if (PER) d = wrap(d, Lx, iLx);
+                                v = axis_factor<CUT, FORM>(d, q4.w, atom_aux[j].x, it.hx,
+                                                     atom_aux[j].z);
+                            }
+                            tgx[x * kTabX + j] = v;
+                        }
                         for (int i = p; i < G.ny * kKC; i += 128) {
                             const int y = i / kKC, j = i - (i / kKC) * kKC;
                             const float4 q4 = atom_pos[j];
@@ -834,7 +852,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             if (atom_aux[j].y >= 0.0f) {
                                 float d = fmaf((float)y + 0.5f, it.hy, it.oy) - q4.y;
                                 if (PER) d = wrap(d, Ly, iLy);
-                                v = axis_factor<CUT>(d, q4.w, atom_aux[j].x, G.form, it.hy,
+                                v = axis_factor<CUT, FORM>(d, q4.w, atom_aux[j].x, it.hy,
                                                      atom_aux[j].z);
                             }
                             tgy[y * kTab + j] = v;
@@ -846,7 +864,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             if (atom_aux[j].y >= 0.0f) {
                                 float d = fmaf((float)z + 0.5f, it.hz, it.oz) - q4.z;
                                 if (PER) d = wrap(d, Lz, iLz);
-                                v = axis_factor<CUT>(d, q4.w, atom_aux[j].x, G.form, it.hz,
+                                v = axis_factor<CUT, FORM>(d, q4.w, atom_aux[j].x, it.hz,
                                                      atom_aux[j].z);
                             }
                             tgz[z * kTab + j] = v;
@@ -862,14 +880,17 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
 #pragma unroll
                             for (int t = 0; t < 8; ++t) {
                                 const int j = jg * 8 + t;
-                                const float4 q4 = atom_pos[j];
                                 const float4 aux = atom_aux[j];
                                 v[t] = 0.0f;
                                 if (row_ok && (int)aux.y == row_c) {
-                                    float d = vx - q4.x;
-                                    if (PER) d = wrap(d, Lx, iLx);
-                                    v[t] = axis_factor<CUT>(d, q4.w, aux.x, G.form, it.hx,
-                                                            aux.z);
+                                    if (FORM == 1) {
+                                        v[t] = tgx[row_x * kTabX + j];
+                                    } else {
+                                        float d = vx - atom_pos[j].x;
+                                        if (PER) d = wrap(d, Lx, iLx);
+                                        v[t] = axis_factor<CUT, FORM>(d, atom_pos[j].w, aux.x,
+                                                                      it.hx, aux.z);
+                                    }
                                 }
                             }
                             *reinterpret_cast<uint4 *>(sa + (p >> 3) * 512 + jg * 128 +
@@ -1009,21 +1030,26 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
     }
 }
 
-template <typename T, int CUT>
+template <typename T, int CUT, int FORM>
 const void *pick_per(int periodic, bool pipe)
 {
     if (pipe)
-        return periodic ? (const void *)separable_pipe_kernel<T, CUT, true>
-                        : (const void *)separable_pipe_kernel<T, CUT, false>;
-    return periodic ? (const void *)separable_kernel<T, CUT, true>
-                    : (const void *)separable_kernel<T, CUT, false>;
+        return periodic ? (const void *)separable_pipe_kernel<T, CUT, true, FORM>
+                        : (const void *)separable_pipe_kernel<T, CUT, false, FORM>;
+    return periodic ? (const void *)separable_kernel<T, CUT, true, FORM>
+                    : (const void *)separable_kernel<T, CUT, false, FORM>;
 }
 
+// Point-sampled (FORM 0) and voxel-integrated (FORM 1, Sec. III-A) operand factors are
+// separate instantiations, so the point form carries no erf code.
 template <typename T>
-const void *pick_cut(int cutoff, int periodic, bool pipe)
+const void *pick_cut(int cutoff, int periodic, bool pipe, int form)
 {
-    return cutoff == PG_CUTOFF_BOX ? pick_per<T, PG_CUTOFF_BOX>(periodic, pipe)
-                                   : pick_per<T, PG_CUTOFF_NONE>(periodic, pipe);
+    if (form == PG_FORM_INTEGRAL)
+        return cutoff == PG_CUTOFF_BOX ? pick_per<T, PG_CUTOFF_BOX, 1>(periodic, pipe)
+                                       : pick_per<T, PG_CUTOFF_NONE, 1>(periodic, pipe);
+    return cutoff == PG_CUTOFF_BOX ? pick_per<T, PG_CUTOFF_BOX, 0>(periodic, pipe)
+                                   : pick_per<T, PG_CUTOFF_NONE, 0>(periodic, pipe);
 }
 
 }  // namespace
@@ -1035,7 +1061,7 @@ bool separable_supported(const Geometry &g, int dtype)
     const long long N = (long long)g.ny * g.nz;
     // Row segments go out as bulk copies: 16-byte multiples; tables must fit shared memory.
     if (N % 16 != 0) return false;
-    if (g.ny > 256 || g.nz > 256) return false;
+    if (g.nx > 256 || g.ny > 256 || g.nz > 256) return false;
     return true;
 }
 
@@ -1084,7 +1110,7 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
     if (n_tile != 64 && n_tile != 128 && n_tile != 256) n_tile = 128;
     const int esz = dtype == PG_F32 ? 4 : 2;
     auto bytes = [&](int nt) {
-        return pipe ? pipe_layout(a.geo.ny, a.geo.nz, nt, esz).total
+        return pipe ? pipe_layout(a.geo.nx, a.geo.ny, a.geo.nz, nt, esz).total
                     : sep_layout(a.geo.ny, a.geo.nz, nt, esz).total;
     };
     // Largest requested tile whose shared-memory footprint fits one SM's 227 KB.
@@ -1097,9 +1123,10 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
         cudaError_t em = encode_out_map(a, dtype);
         if (em != cudaSuccess) return em;
     }
-    const void *f = dtype == PG_F32   ? pick_cut<float>(a.geo.cutoff, a.geo.periodic, pipe)
-                    : dtype == PG_F16 ? pick_cut<__half>(a.geo.cutoff, a.geo.periodic, pipe)
-                                      : pick_cut<__nv_bfloat16>(a.geo.cutoff, a.geo.periodic, pipe);
+    const int cut = a.geo.cutoff, per = a.geo.periodic, form = a.geo.form;
+    const void *f = dtype == PG_F32   ? pick_cut<float>(cut, per, pipe, form)
+                    : dtype == PG_F16 ? pick_cut<__half>(cut, per, pipe, form)
+                                      : pick_cut<__nv_bfloat16>(cut, per, pipe, form);
     const int threads = pipe ? kPipeThreads : kRows;
     const int tmem_cols = pipe ? 2 * n_tile : n_tile;
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
