@@ -833,7 +833,36 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                         producer_sync();
                         // Per-axis tables of this K chunk: g_y, g_z, and for the erf form also
                         // g_x (an erf per A entry would cost more than the table).
-                        for (int i = p; FORM == 1 && i < G.nx * kKC; i += 128) {
+                        if (FORM == 1 && !PER) {
+                            // Open boundaries: neighbouring voxels share an edge, so each lane
+                            // evaluates erf at one lower edge and takes the upper one from the
+                            // next lane (Sec. VI-A's reuse of the subtrahend): n + n/32 erf
+                            // evaluations per atom and axis instead of 2n.
+                            const int pw = p >> 5;
+                            auto erf_table = [&](float *tab, int n, int stride, float h, float o,
+                                                 int axis) {
+                                const int blocks = (n + 31) >> 5;
+                                for (int task = pw; task < kKC * blocks; task += 4) {
+                                    const int j = task % kKC, i = (task / kKC) * 32 + lane;
+                                    const float4 q4 = atom_pos[j];
+                                    const float4 aux = atom_aux[j];
+                                    const float mu = axis == 0 ? q4.x : (axis == 1 ? q4.y : q4.z);
+                                    const float e_lo = erff((fmaf((float)i, h, o) - mu) * aux.z);
+                                    float e_hi = __shfl_down_sync(0xffffffffu, e_lo, 1);
+                                    if (lane == 31)
+                                        e_hi = erff((fmaf((float)(i + 1), h, o) - mu) * aux.z);
+                                    float v = 0.5f * (e_hi - e_lo);
+                                    const float d = fmaf((float)i + 0.5f, h, o) - mu;
+                                    if (aux.y < 0.0f || (CUT == PG_CUTOFF_BOX && d * d > aux.x))
+                                        v = 0.0f;
+                                    if (i < n) tab[i * stride + j] = v;
+                                }
+                            };
+                            erf_table(tgx, G.nx, kTabX, it.hx, it.ox, 0);
+                            erf_table(tgy, G.ny, kTab, it.hy, it.oy, 1);
+                            erf_table(tgz, G.nz, kTab, it.hz, it.oz, 2);
+                        }
+                        for (int i = p; FORM == 1 && PER && i < G.nx * kKC; i += 128) {
                             const int x = i / kKC, j = i - (i / kKC) * kKC;
                             const float4 q4 = atom_pos[j];
                             float v = 0.0f;
@@ -845,7 +874,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             }
                             tgx[x * kTabX + j] = v;
                         }
-                        for (int i = p; i < G.ny * kKC; i += 128) {
+                        for (int i = p; (FORM == 0 || PER) && i < G.ny * kKC; i += 128) {
                             const int y = i / kKC, j = i - (i / kKC) * kKC;
                             const float4 q4 = atom_pos[j];
                             float v = 0.0f;
@@ -857,7 +886,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             }
                             tgy[y * kTab + j] = v;
                         }
-                        for (int i = p; i < G.nz * kKC; i += 128) {
+                        for (int i = p; (FORM == 0 || PER) && i < G.nz * kKC; i += 128) {
                             const int z = i / kKC, j = i - (i / kKC) * kKC;
                             const float4 q4 = atom_pos[j];
                             float v = 0.0f;
