@@ -342,6 +342,11 @@ struct pg_plan {
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t n_memset = nullptr, n_copy[5] = {}, n_kernel = nullptr, n_errcopy = nullptr;
     const void *kernel_func = nullptr;
+    // What the executable graph currently holds, so that an unchanged run skips the update.
+    const void *cur_src[5] = {};
+    size_t cur_cnt[5] = {};
+    KernelLaunch cur_kl;
+    bool cur_valid = false;
 };
 
 namespace {
@@ -408,8 +413,40 @@ pg_status plan_build_graph(pg_plan *p, const void *const src[5], const size_t by
     return PG_OK;
 }
 
+bool same_launch(const KernelLaunch &a, const KernelLaunch &b)
+{
+    return a.func == b.func && a.grid.x == b.grid.x && a.grid.y == b.grid.y &&
+           a.grid.z == b.grid.z && a.block.x == b.block.x && a.block.y == b.block.y &&
+           a.block.z == b.block.z && a.smem == b.smem && a.args_size == b.args_size &&
+           std::memcmp(a.args, b.args, a.args_size) == 0;
+}
+
+pg_status plan_update_graph_nodes(pg_plan *p, const void *const src[5], const size_t bytes[5],
+                                  void *const dst[5], KernelLaunch &kl);
+
+// Bring the executable graph in line with this run; nothing to do when the copies and the
+// launch are those of the previous run.
 pg_status plan_update_graph(pg_plan *p, const void *const src[5], const size_t bytes[5],
                             void *const dst[5], KernelLaunch &kl)
+{
+    bool same = p->exec && p->cur_valid && same_launch(kl, p->cur_kl);
+    for (int i = 0; same && i < 5; ++i)
+        same = src[i] == p->cur_src[i] && bytes[i] == p->cur_cnt[i];
+    if (same) return PG_OK;
+    pg_status st = plan_update_graph_nodes(p, src, bytes, dst, kl);
+    p->cur_valid = st == PG_OK;
+    if (st == PG_OK) {
+        for (int i = 0; i < 5; ++i) {
+            p->cur_src[i] = src[i];
+            p->cur_cnt[i] = bytes[i];
+        }
+        p->cur_kl = kl;
+    }
+    return st;
+}
+
+pg_status plan_update_graph_nodes(pg_plan *p, const void *const src[5], const size_t bytes[5],
+                                  void *const dst[5], KernelLaunch &kl)
 {
     if (!p->exec || kl.func != p->kernel_func) return plan_build_graph(p, src, bytes, dst, kl);
     for (int i = 0; i < 5; ++i) {
@@ -766,15 +803,27 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
     }
     cleanup();
 
+    // Fastest candidate, except that direct candidates within 2% of the fastest direct time
+    // count as tied and the tie goes to the largest chunk: fewer grabs of the shared work
+    // counter, which keeps isolated launches (graph replays, one plan run at a time) at the
+    // speed measured back to back.
+    auto better = [&](int i, int j) {
+        if (j < 0) return true;
+        if (cands[i].path == PG_PATH_DIRECT && cands[j].path == PG_PATH_DIRECT &&
+            times[i] <= 1.02f * times[j] && times[j] <= 1.02f * times[i] &&
+            cands[i].chunk_planes != cands[j].chunk_planes)
+            return cands[i].chunk_planes > cands[j].chunk_planes;
+        return times[i] < times[j];
+    };
     int best = -1, best_direct = -1, best_sep = -1;
     for (size_t i = 0; i < cands.size(); ++i) {
         if (!std::isfinite(times[i])) continue;
-        if (best < 0 || times[i] < times[best]) best = (int)i;
-        if (cands[i].path == PG_PATH_DIRECT && (best_direct < 0 || times[i] < times[best_direct]))
-            best_direct = (int)i;
+        if (cands[i].path == PG_PATH_DIRECT && better((int)i, best_direct)) best_direct = (int)i;
         if (cands[i].path == PG_PATH_SEPARABLE && (best_sep < 0 || times[i] < times[best_sep]))
             best_sep = (int)i;
     }
+    if (best_direct >= 0) best = best_direct;
+    if (best_sep >= 0 && (best < 0 || times[best_sep] < times[best])) best = best_sep;
     if (best < 0) return fail(PG_ERR_CUDA, "no autotune candidate ran and passed parity");
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
