@@ -14,6 +14,7 @@ Functions (each mirrors one C entry point; see the C file for the equations):
 * ``separable(...)``                                     - Sec. III-A / VI-A per-axis form
 * ``gradient(...)``                                      - Sec. IV-C, dL/dx for L = <W, G>
 * ``fd_gradient_frozen(...)``                            - central differences, frozen support
+* ``refine(...)``                                        - Sec. IV-A/IV-C grid reversal by descent
 """
 from __future__ import annotations
 
@@ -81,6 +82,9 @@ def _load():
             lib.pgo_separable.argtypes = [P, dp, ctypes.c_int]
             lib.pgo_gradient.argtypes = [P, ctypes.c_int, dp, dp, ctypes.c_int]
             lib.pgo_fd_gradient_frozen.argtypes = [P, dp, ctypes.c_double, dp, ctypes.c_int]
+            lib.pgo_refine.argtypes = [P, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                       dp, dp, dp, ctypes.c_int]
+            lib.pgo_refine.restype = ctypes.c_int
             lib.pgo_inner.argtypes = [dp, dp, ctypes.c_long]
             lib.pgo_inner.restype = ctypes.c_double
             for f in (lib.pgo_voxelize, lib.pgo_voxelize_band, lib.pgo_separable,
@@ -170,6 +174,20 @@ def fd_gradient_frozen(prob: Problem, W: np.ndarray, step: float = 1e-4,
     _check(_load().pgo_fd_gradient_frozen(ctypes.byref(prob.c), W.ctypes.data, float(step),
                                           g.ctypes.data, threads), "fd_gradient_frozen")
     return g
+
+
+def refine(prob: Problem, target: np.ndarray, iters: int, lr: float, eps: float = 0.0,
+           threads: int = 0):
+    """Grid reversal by gradient descent (Sec. IV-A, IV-C) from the problem's coordinates
+    towards `target` ([B][C][nx][ny][nz]).  Returns (coords [N][3], loss [B], steps [B])."""
+    T = np.ascontiguousarray(target, np.float64).reshape(prob.shape)
+    out = np.empty_like(prob.coords)
+    loss = np.empty(prob.shape[0], np.float64)
+    steps = np.empty(prob.shape[0], np.int32)
+    _check(_load().pgo_refine(ctypes.byref(prob.c), T.ctypes.data, int(iters), float(lr),
+                              float(eps), out.ctypes.data, loss.ctypes.data, steps.ctypes.data,
+                              threads), "refine")
+    return out, loss, steps
 
 
 def loss(prob: Problem, W: np.ndarray, threads: int = 0) -> float:

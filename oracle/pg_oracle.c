@@ -350,6 +350,56 @@ int pgo_separable(const pgo_problem *p, double *out, int n_threads)
  * mode 0 visits every voxel of the atom's channel, mode 1 only its cutoff box.
  * W has the grid layout [B][C][nx][ny][nz]; grad is [N][3].
  */
+/* Gradient for the atoms of molecule b (see pgo_gradient). */
+static void gradient_molecule(const pgo_problem *p, int b, int mode, const double *W,
+                              double *grad)
+{
+    for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a) {
+        int c = p->elem[a];
+        double sg2 = p->sigma[c] * p->sigma[c];
+        double r = p->cutoff_k * p->sigma[c];
+        double x = p->coords[3 * a + 0], y = p->coords[3 * a + 1], z = p->coords[3 * a + 2];
+        long ilo = 0, ihi = p->nx - 1, jlo = 0, jhi = p->ny - 1, klo = 0, khi = p->nz - 1;
+        if (mode == 1) {
+            support(p, b, 0, x, r, &ilo, &ihi);
+            support(p, b, 1, y, r, &jlo, &jhi);
+            support(p, b, 2, z, r, &klo, &khi);
+        }
+        double gx = 0.0, gy = 0.0, gz = 0.0;
+        for (long iu = ilo; iu <= ihi; ++iu) {
+            long i = p->periodic ? wrap_index(iu, p->nx) : iu;
+            double dx = disp(p, b, 0, i, x);
+            for (long ju = jlo; ju <= jhi; ++ju) {
+                long j = p->periodic ? wrap_index(ju, p->ny) : ju;
+                double dy = disp(p, b, 1, j, y);
+                for (long ku = klo; ku <= khi; ++ku) {
+                    long k = p->periodic ? wrap_index(ku, p->nz) : ku;
+                    double dz = disp(p, b, 2, k, z);
+                    if (!inside(p->cutoff, dx, dy, dz, r)) continue;
+                    double Wv = W[grid_index(p, b, c, i, j, k)];
+                    if (p->form == PGO_INTEGRAL) {
+                        const double *h = p->spacing + 3 * b, sg = p->sigma[c];
+                        double fx = erf_factor(dx, h[0], sg), fy = erf_factor(dy, h[1], sg);
+                        double fz = erf_factor(dz, h[2], sg);
+                        gx += Wv * erf_factor_dmu(dx, h[0], sg) * fy * fz;
+                        gy += Wv * fx * erf_factor_dmu(dy, h[1], sg) * fz;
+                        gz += Wv * fx * fy * erf_factor_dmu(dz, h[2], sg);
+                    } else {
+                        double w = Wv * exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * sg2));
+                        gx += w * dx;
+                        gy += w * dy;
+                        gz += w * dz;
+                    }
+                }
+            }
+        }
+        /* The point form's common 1/sigma^2 is applied once at the end. */
+        grad[3 * a + 0] = p->form == PGO_INTEGRAL ? gx : gx / sg2;
+        grad[3 * a + 1] = p->form == PGO_INTEGRAL ? gy : gy / sg2;
+        grad[3 * a + 2] = p->form == PGO_INTEGRAL ? gz : gz / sg2;
+    }
+}
+
 int pgo_gradient(const pgo_problem *p, int mode, const double *W, double *grad, int n_threads)
 {
     int st = check(p);
@@ -357,51 +407,65 @@ int pgo_gradient(const pgo_problem *p, int mode, const double *W, double *grad, 
     int nt = threads_or_default(n_threads);
     (void)nt;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int b = 0; b < p->n_mol; ++b) gradient_molecule(p, b, mode, W, grad);
+    return PGO_OK;
+}
+
+/*
+ * Grid reversal by gradient descent (Sec. IV-A steps 2-5, Sec. IV-C).  Each molecule b, from
+ * its coordinates x^0 in p->coords, repeats:
+ *   F = grid of x^t;  L = sum_v (F(v) - T(v))^2 over the molecule's voxels;
+ *   stop if L < eps;  otherwise x^{t+1} = x^t - lr * dL/dx^t,
+ * with dL/dx = sum_v 2 (F - T) dF/dx, the gradient above with W = 2 (F - T), for at most
+ * `iters` updates.  out_coords [N][3] receives the final coordinates, loss[b] the loss of
+ * the final coordinates and steps[b] the number of updates applied.
+ */
+int pgo_refine(const pgo_problem *p, const double *target, int iters, double lr, double eps,
+               double *out_coords, double *loss, int32_t *steps, int n_threads)
+{
+    int st = check(p);
+    if (st) return st;
+    if (iters < 0 || !(lr >= 0.0)) return PGO_BAD_ARG;
+    int nt = threads_or_default(n_threads);
+    (void)nt;
+    long per_mol = (long)p->n_channels * p->nx * p->ny * p->nz;
+    long n_atoms = p->n_mol > 0 ? p->mol_off[p->n_mol] : 0;
+    memcpy(out_coords, p->coords, sizeof(double) * 3 * n_atoms);
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
     for (int b = 0; b < p->n_mol; ++b) {
-        for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a) {
-            int c = p->elem[a];
-            double sg2 = p->sigma[c] * p->sigma[c];
-            double r = p->cutoff_k * p->sigma[c];
-            double x = p->coords[3 * a + 0], y = p->coords[3 * a + 1], z = p->coords[3 * a + 2];
-            long ilo = 0, ihi = p->nx - 1, jlo = 0, jhi = p->ny - 1, klo = 0, khi = p->nz - 1;
-            if (mode == 1) {
-                support(p, b, 0, x, r, &ilo, &ihi);
-                support(p, b, 1, y, r, &jlo, &jhi);
-                support(p, b, 2, z, r, &klo, &khi);
+        /* Molecule b as a one-molecule problem (atom indices stay global), reading and
+           updating its own atoms in out_coords. */
+        pgo_problem q = *p;
+        q.n_mol = 1;
+        q.mol_off = p->mol_off + b;
+        q.origin = p->origin + 3 * b;
+        q.spacing = p->spacing + 3 * b;
+        q.coords = out_coords;
+        double *F = malloc(sizeof(double) * per_mol);
+        double *W = malloc(sizeof(double) * per_mol);
+        double *g = malloc(sizeof(double) * 3 * (n_atoms > 0 ? n_atoms : 1));
+        const double *T = target + b * per_mol;
+        int t = 0;
+        double L = 0.0;
+        for (;;) {
+            bbox_molecule(&q, 0, F, 0.0, NULL);
+            L = 0.0;
+            for (long v = 0; v < per_mol; ++v) {
+                double r = F[v] - T[v];
+                L += r * r;
+                W[v] = 2.0 * r;
             }
-            double gx = 0.0, gy = 0.0, gz = 0.0;
-            for (long iu = ilo; iu <= ihi; ++iu) {
-                long i = p->periodic ? wrap_index(iu, p->nx) : iu;
-                double dx = disp(p, b, 0, i, x);
-                for (long ju = jlo; ju <= jhi; ++ju) {
-                    long j = p->periodic ? wrap_index(ju, p->ny) : ju;
-                    double dy = disp(p, b, 1, j, y);
-                    for (long ku = klo; ku <= khi; ++ku) {
-                        long k = p->periodic ? wrap_index(ku, p->nz) : ku;
-                        double dz = disp(p, b, 2, k, z);
-                        if (!inside(p->cutoff, dx, dy, dz, r)) continue;
-                        double Wv = W[grid_index(p, b, c, i, j, k)];
-                        if (p->form == PGO_INTEGRAL) {
-                            const double *h = p->spacing + 3 * b, sg = p->sigma[c];
-                            double fx = erf_factor(dx, h[0], sg), fy = erf_factor(dy, h[1], sg);
-                            double fz = erf_factor(dz, h[2], sg);
-                            gx += Wv * erf_factor_dmu(dx, h[0], sg) * fy * fz;
-                            gy += Wv * fx * erf_factor_dmu(dy, h[1], sg) * fz;
-                            gz += Wv * fx * fy * erf_factor_dmu(dz, h[2], sg);
-                        } else {
-                            double w = Wv * exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * sg2));
-                            gx += w * dx;
-                            gy += w * dy;
-                            gz += w * dz;
-                        }
-                    }
-                }
-            }
-            /* The point form's common 1/sigma^2 is applied once at the end. */
-            grad[3 * a + 0] = p->form == PGO_INTEGRAL ? gx : gx / sg2;
-            grad[3 * a + 1] = p->form == PGO_INTEGRAL ? gy : gy / sg2;
-            grad[3 * a + 2] = p->form == PGO_INTEGRAL ? gz : gz / sg2;
+            if (L < eps || t == iters) break;
+            gradient_molecule(&q, 0, 1, W, g);
+            for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a)
+                for (int ax = 0; ax < 3; ++ax) out_coords[3 * a + ax] -= lr * g[3 * a + ax];
+            ++t;
         }
+        loss[b] = L;
+        steps[b] = t;
+        free(F);
+        free(W);
+        free(g);
     }
     return PGO_OK;
 }
