@@ -229,6 +229,8 @@ def run_reference(args):
     oracle.build()
     wl = synth.workload(args.workload)
     threads = os.cpu_count() or 1
+    if wl.name == "refinement":
+        return run_reference_refinement(args, wl, threads)
     n = wl.batch.n_mol
     calib = wl.batch.subset(range(min(n, 32)))
     t = time.perf_counter()
@@ -256,6 +258,51 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": "grids/s", "cores": threads, "kind": "oracle",
                          "sample": f"{per_step} molecules of the {wl.name} batch per step"},
         "e2e": {"value": value, "unit": "grids/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_reference_refinement(args, wl, threads):
+    """Reference arm for grid reversal: the oracle's FP64 descent on a sample per step."""
+    import numpy as np
+    import oracle
+    import synth
+
+    iters, lr = synth.REFINE_ITERS, synth.REFINE_LR
+    start = synth.refinement_start(wl)
+
+    def problem(n):
+        sub = wl.batch.subset(range(n))
+        s = slice(0, int(sub.mol_off[-1]))
+        T = oracle.voxelize(oracle.Problem.from_workload(wl, batch=sub), "bbox", threads)
+        return oracle.Problem.from_workload(wl, batch=sub, coords=start[s].astype(np.float64)), T
+
+    prob, T = problem(min(wl.batch.n_mol, threads))
+    t = time.perf_counter()
+    oracle.refine(prob, T, iters, lr, 0.0, threads)
+    per_mol = (time.perf_counter() - t) / prob.shape[0]
+    steps = args.steps + args.warmup
+    per_step = max(1, min(wl.batch.n_mol, int(150.0 / steps / max(per_mol, 1e-9))))
+    prob, T = problem(per_step)
+    for _ in range(args.warmup):
+        oracle.refine(prob, T, iters, lr, 0.0, threads)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.refine(prob, T, iters, lr, 0.0, threads)
+    dt = time.perf_counter() - t
+    value = per_step * iters * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "molecule-iterations/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "description": wl.description,
+                   "batch_per_step": per_step, "iters": iters, "lr": lr},
+        "cpu_baseline": {"value": value, "unit": "molecule-iterations/s", "cores": threads,
+                         "kind": "oracle",
+                         "sample": f"{per_step} molecules of the refinement batch per step"},
+        "e2e": {"value": value, "unit": "molecule-iterations/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -463,6 +510,165 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_refinement(args):
+    """Grid reversal (Sec. IV-A/IV-C): a step is one pg_refine call of REFINE_ITERS descent
+    iterations over the whole batch, from the seeded start (reset by a device copy inside the
+    step).  value = molecule-iterations per second over all ranks."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2211_08506_gb300 as pkg
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    pkg.build()
+    from paper_2211_08506_gb300 import api
+
+    shard = rank if world > 1 else None
+    wl = synth.workload("refinement", shard=shard, **({"n_mol": args.n_mol} if args.n_mol else {}))
+    iters, lr = synth.REFINE_ITERS, synth.REFINE_LR
+    grid = api.Grid.from_workload(wl)
+    db = api.DeviceBatch.from_numpy(wl.batch)
+    B = wl.batch.n_mol
+    stream = torch.cuda.Stream()
+    start_h = synth.refinement_start(wl, shard)
+    start = torch.as_tensor(start_h, device="cuda")
+    x = start.clone()
+    work = torch.empty(max(1, B * wl.voxels_per_grid + 3 * wl.batch.n_atoms),
+                       dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        # The grid to reverse: the true coordinates' own grid (input preparation, untimed).
+        api.autotune(db, grid, dtype="f32", path="direct")
+        target = api.voxelize(db, grid, dtype="f32", path="direct")
+        for _ in range(args.warmup):
+            x.copy_(start)
+            api.refine(db, grid, target, x, iters, lr, 0.0, work=work, stream=stream)
+    api.sync_status(stream)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.4)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark("start")
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(args.steps):
+            x.copy_(start)
+            loss, steps = api.refine(db, grid, target, x, iters, lr, 0.0, work=work,
+                                     stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark("stop")
+    total_ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    sampler.stop()
+    assert api.sync_status(stream) == 0
+    ms = total_ms / args.steps
+    value = world * B * iters / (ms / 1e3)
+
+    # End to end: the grid to reverse and the start come from pinned host memory, the refined
+    # coordinates and losses go back, every step.
+    target_h = target.cpu().pin_memory()
+    start_p = torch.from_numpy(start_h).pin_memory()
+    x_h = torch.empty_like(start_p).pin_memory()
+    loss_h = torch.empty(B, dtype=torch.float32).pin_memory()
+    tgt_d = torch.empty_like(target)
+    e2e_steps = max(3, min(args.steps, 20))
+    with torch.cuda.stream(stream):
+        for it in range(2 + e2e_steps):
+            if it == 2:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            tgt_d.copy_(target_h, non_blocking=True)
+            x.copy_(start_p, non_blocking=True)
+            loss, _ = api.refine(db, grid, tgt_d, x, iters, lr, 0.0, work=work, stream=stream)
+            x_h.copy_(x, non_blocking=True)
+            loss_h.copy_(loss, non_blocking=True)
+            stream.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peak, peak_src = load_peaks()
+    grid_bytes = B * wl.voxels_per_grid * 4
+    # Per step: iters + 1 forward passes (grid written) and residual passes (grid and target
+    # read, upstream gradient written); the adjoint's reads of the cutoff boxes are small.
+    algo = (iters + 1) * 4 * grid_bytes
+    achieved = algo / (ms / 1e3) / 1e9
+    base = None
+    if world == 1 and not args.no_cpu_baseline:
+        base = refinement_cpu_baseline(wl, start_h)
+    line = {
+        "metric": METRIC, "value": value, "unit": "molecule-iterations/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl.name, "description": wl.description, "batch_per_gpu": B,
+                   "grid": [wl.n_channels, wl.nx, wl.ny, wl.nz], "iters": iters, "lr": lr,
+                   "parallelism": f"dp{world}" if world > 1 else "single",
+                   "l2": f"grid {grid_bytes / 1e9:.2f} GB > 129 MB L2; no flush"},
+        "final_loss_median": float(torch.median(loss).item()),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": f"{peak_src} hbm_gbs (copy)",
+                     "algorithmic_bytes_per_step": algo,
+                     "kernel": "refinement step (forward, residual, adjoint, update kernels)"},
+        "e2e": {"value": world * B * iters / e2e_s, "unit": "molecule-iterations/s",
+                "h2d_bytes_per_step": target_h.numel() * 4 + start_p.numel() * 4,
+                "d2h_bytes_per_step": x_h.numel() * 4 + B * 4,
+                "api": "pg_refine with the target and start copied in and results copied out"},
+        "gpu_launches": args.steps * (4 * iters + 2),
+        "clocks": sampler.summary(),
+        "cpu_baseline": base,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def refinement_cpu_baseline(wl, start, budget_s=12.0):
+    """The FP64 oracle's refinement on a bounded sample of the batch, all host cores."""
+    import numpy as np
+    import oracle
+    import synth
+
+    oracle.build()
+    threads = os.cpu_count() or 1
+    iters = synth.REFINE_ITERS
+
+    def run(n):
+        sub = wl.batch.subset(range(n))
+        s = slice(0, int(sub.mol_off[-1]))
+        T = oracle.voxelize(oracle.Problem.from_workload(wl, batch=sub), "bbox", threads)
+        prob = oracle.Problem.from_workload(wl, batch=sub, coords=start[s].astype(np.float64))
+        t = time.perf_counter()
+        oracle.refine(prob, T, iters, synth.REFINE_LR, 0.0, threads)
+        return time.perf_counter() - t
+
+    n = min(wl.batch.n_mol, threads)
+    dt = run(n)
+    n2 = max(1, min(wl.batch.n_mol, int(n * budget_s / max(dt, 1e-6) / 2)))
+    if n2 > n:
+        n, dt = n2, run(n2)
+    return {"value": n * iters / dt, "unit": "molecule-iterations/s", "cores": threads,
+            "kind": "oracle",
+            "sample": f"first {n} molecules of the refinement batch, {iters} FP64 descent "
+                      f"iterations each, OpenMP over molecules"}
+
+
 def run_profile(args, wl, dtype):
     """Plain launches for profiler captures: no tuning, no graph, no host-side extras.
     Prints a line marked "profile" (it is not a benchmark result)."""
@@ -500,7 +706,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="qm9_shaped",
                     choices=["qm9_shaped", "plain_small", "precision_form",
-                             "precision_form_integral", "crystal_shaped", "differentiation"])
+                             "precision_form_integral", "crystal_shaped", "differentiation",
+                             "refinement"])
     ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default=None)
     ap.add_argument("--path", choices=["auto", "direct", "separable"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -517,6 +724,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "refinement" and not args.profile:
+        run_refinement(args)
     else:
         run_ours(args)
 

@@ -195,6 +195,33 @@ pg_status pg_voxelize_tuned(const pg_batch *batch, const pg_grid *grid, int32_t 
 pg_status pg_voxelize_backward(const pg_batch *batch, const pg_grid *grid, int32_t grad_dtype,
                                const void *grad_out, float *grad_coords, void *stream);
 
+/*
+ * Grid reversal by gradient descent (Sec. IV-A steps 2-5, Sec. IV-C).  For each molecule,
+ * from the coordinates in `coords`, repeat on the stream (no host synchronisation):
+ *     F = grid of x (FP32, as pg_voxelize on the direct path);
+ *     L = sum_v (F(v) - target(v))^2 over the molecule's voxels;
+ *     stop if L < eps;  otherwise  x <- x - lr * dL/dx,
+ * with dL/dx = sum_v 2 (F - target) dF/dx, the adjoint of pg_voxelize_backward for the
+ * upstream gradient 2 (F - target), for at most `iters` updates.
+ *   batch    DEVICE CSR batch (elem, mol_off, origin, spacing, counts); batch->coords is not
+ *            read, the coordinates come from `coords`
+ *   target   DEVICE float[n_mol][C][nx][ny][nz]: the grid to reverse
+ *   coords   DEVICE float[n_atoms][3]: starting coordinates, overwritten with the result
+ *   work     DEVICE float workspace of pg_refine_work_floats(batch, grid) floats (the
+ *            current grid and the coordinate gradient), caller-owned
+ *   loss     DEVICE float[n_mol]: each molecule's loss at the returned coordinates
+ *   steps    DEVICE int32[n_mol]: updates applied to each molecule
+ *   iters >= 0, lr >= 0 and finite, eps >= 0 (eps = 0 runs exactly `iters` updates).
+ * Each iteration launches the forward, residual, adjoint and update kernels; a molecule
+ * that has reached eps keeps its coordinates (its loss is recomputed each iteration).
+ */
+pg_status pg_refine(const pg_batch *batch, const pg_grid *grid, const float *target,
+                    float *coords, float *work, float *loss, int32_t *steps, int32_t iters,
+                    float lr, float eps, void *stream);
+
+/* Floats of workspace pg_refine needs: n_mol * C * nx * ny * nz + 3 * n_atoms. */
+size_t pg_refine_work_floats(const pg_batch *batch, const pg_grid *grid);
+
 /* Synchronize `stream`, then read and clear the device error word.  Returns
    PG_ERR_DEVICE_VALIDATION (bits in *bits_out if non-NULL) if it was set. */
 pg_status pg_sync_status(void *stream, uint32_t *bits_out);

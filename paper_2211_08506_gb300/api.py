@@ -145,6 +145,26 @@ def voxelize_backward(batch: DeviceBatch, grid: Grid, grad_out: torch.Tensor,
     return grad_coords
 
 
+def refine(batch: DeviceBatch, grid: Grid, target: torch.Tensor, coords: torch.Tensor,
+           iters: int, lr: float, eps: float = 0.0, work: torch.Tensor | None = None,
+           stream=None):
+    """pg_refine: grid reversal by gradient descent.  `coords` (float32 [N, 3], device) holds
+    the start and is overwritten with the result.  Returns (loss [B], steps [B])."""
+    target = target.contiguous()
+    if target.dtype != torch.float32:
+        raise TypeError("target must be float32")
+    cb = batch.to_c(coords)
+    cg = grid.to_c()
+    n = B.pg_refine_work_floats(cb, cg)
+    if work is None or work.numel() < n:
+        work = torch.empty(max(n, 1), dtype=torch.float32, device=coords.device)
+    loss = torch.empty(batch.n_mol, dtype=torch.float32, device=coords.device)
+    steps = torch.empty(batch.n_mol, dtype=torch.int32, device=coords.device)
+    B.check(B.pg_refine(cb, cg, _ptr(target), _ptr(coords), _ptr(work), _ptr(loss),
+                        _ptr(steps), iters, lr, eps, _stream(stream)))
+    return loss, steps
+
+
 def sync_status(stream=None, raise_on_error: bool = True) -> int:
     """pg_sync_status: synchronize and return (and clear) the device error bits."""
     st, bits = B.pg_sync_status(_stream(stream))

@@ -34,7 +34,7 @@ EXPORTED = (
     "pg_version", "pg_last_error", "pg_status_string", "pg_voxelize", "pg_voxelize_tuned",
     "pg_voxelize_backward", "pg_sync_status", "pg_autotune", "pg_get_tuning",
     "pg_tuning_save", "pg_tuning_load", "pg_plan_create", "pg_plan_run", "pg_plan_destroy",
-    "pg_shutdown", "pg_voxelize_noalloc",
+    "pg_shutdown", "pg_voxelize_noalloc", "pg_refine", "pg_refine_work_floats",
 )
 
 
@@ -124,10 +124,14 @@ def load() -> ctypes.CDLL:
         lib.pg_shutdown.restype = None
         lib.pg_voxelize_noalloc.argtypes = [P(pg_batch), P(pg_grid), i32, vp, vp,
                                             P(ctypes.c_uint32)]
+        lib.pg_refine.argtypes = [P(pg_batch), P(pg_grid), vp, vp, vp, vp, vp, i32,
+                                  ctypes.c_float, ctypes.c_float, vp]
+        lib.pg_refine_work_floats.argtypes = [P(pg_batch), P(pg_grid)]
+        lib.pg_refine_work_floats.restype = ctypes.c_size_t
         for name in ("pg_voxelize", "pg_voxelize_tuned", "pg_voxelize_backward",
                      "pg_sync_status", "pg_autotune", "pg_get_tuning", "pg_tuning_save",
                      "pg_tuning_load", "pg_plan_create", "pg_plan_run", "pg_plan_destroy",
-                     "pg_voxelize_noalloc"):
+                     "pg_voxelize_noalloc", "pg_refine"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -171,6 +175,15 @@ def pg_voxelize_tuned(batch, grid, out_dtype, out, tuning, stream):
 def pg_voxelize_backward(batch, grid, grad_dtype, grad_out, grad_coords, stream):
     return load().pg_voxelize_backward(ctypes.byref(batch), ctypes.byref(grid), grad_dtype,
                                        grad_out, grad_coords, stream)
+
+
+def pg_refine(batch, grid, target, coords, work, loss, steps, iters, lr, eps, stream):
+    return load().pg_refine(ctypes.byref(batch), ctypes.byref(grid), target, coords, work, loss,
+                            steps, int(iters), float(lr), float(eps), stream)
+
+
+def pg_refine_work_floats(batch, grid):
+    return load().pg_refine_work_floats(ctypes.byref(batch), ctypes.byref(grid))
 
 
 def pg_sync_status(stream):

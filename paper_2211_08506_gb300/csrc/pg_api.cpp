@@ -611,6 +611,54 @@ pg_status pg_voxelize_backward(const pg_batch *batch, const pg_grid *grid, int32
     return PG_OK;
 }
 
+size_t pg_refine_work_floats(const pg_batch *batch, const pg_grid *grid)
+{
+    if (!batch || !grid || batch->n_mol < 0 || batch->n_atoms < 0 || grid->nx <= 0 ||
+        grid->ny <= 0 || grid->nz <= 0 || grid->n_channels <= 0)
+        return 0;
+    return (size_t)batch->n_mol * grid->n_channels * grid->nx * grid->ny * grid->nz +
+           3 * (size_t)batch->n_atoms;
+}
+
+pg_status pg_refine(const pg_batch *batch, const pg_grid *grid, const float *target,
+                    float *coords, float *work, float *loss, int32_t *steps, int32_t iters,
+                    float lr, float eps, void *stream)
+{
+    t_last_error.clear();
+    if (!batch) return fail(PG_ERR_INVALID_ARG, "batch must not be NULL");
+    if (iters < 0) return fail(PG_ERR_INVALID_ARG, "iters must be >= 0");
+    if (!(lr >= 0.0f) || !(lr < INFINITY))
+        return fail(PG_ERR_INVALID_ARG, "lr must be finite and >= 0");
+    if (!(eps >= 0.0f)) return fail(PG_ERR_INVALID_ARG, "eps must be >= 0");
+    pg_batch b = *batch;
+    b.coords = coords;  // the coordinates being refined
+    pg_status st = validate(&b, grid);
+    if (st) return st;
+    if (b.n_mol > 0 && (!target || !work || !loss || !steps))
+        return fail(PG_ERR_INVALID_ARG, "target, work, loss and steps are required");
+    if ((uintptr_t)work % 16 != 0 || (uintptr_t)target % 4 != 0 || (uintptr_t)coords % 4 != 0)
+        return fail(PG_ERR_INVALID_ARG, "work must be 16-byte aligned, target and coords 4-byte");
+    Device *d = nullptr;
+    if ((st = get_device(&d))) return st;
+    if (b.n_mol == 0) return PG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long per_mol = (long long)grid->n_channels * grid->nx * grid->ny * grid->nz;
+    float *F = work;
+    float *grad = work + per_mol * b.n_mol;
+    PG_CUDA(cudaMemsetAsync(steps, 0, sizeof(int32_t) * b.n_mol, s), "clear steps");
+    const pg_tuning t = resolve(&b, grid, PG_F32, PG_PATH_DIRECT, *d);
+    for (int it = 0;; ++it) {
+        if ((st = forward(&b, grid, PG_F32, F, t, s))) return st;
+        PG_CUDA(refine_residual(F, target, b.n_mol, per_mol, loss, d->sms, s), "residual");
+        if (it == iters) break;
+        if ((st = pg_voxelize_backward(&b, grid, PG_F32, F, grad, stream))) return st;
+        PG_CUDA(refine_update(coords, grad, b.mol_off, b.n_mol, b.n_atoms, loss, steps, lr,
+                              eps, s),
+                "update");
+    }
+    return PG_OK;
+}
+
 pg_status pg_sync_status(void *stream, uint32_t *bits_out)
 {
     t_last_error.clear();

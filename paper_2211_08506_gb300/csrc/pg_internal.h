@@ -117,6 +117,14 @@ struct KernelLaunch {
 };
 
 // Direct per-voxel gather (pg_direct.cu).
+// Grid reversal (pg_refine.cu): residual 2 (F - T) in place with per-molecule squared error,
+// and the per-atom descent step.
+cudaError_t refine_residual(float *F, const float *T, int n_mol, long long per_mol, float *loss,
+                            int sm_count, cudaStream_t s);
+cudaError_t refine_update(float *coords, const float *grad, const int *mol_off, int n_mol,
+                          int n_atoms, const float *loss, int *steps, float lr, float eps,
+                          cudaStream_t s);
+
 // The direct kernel's voxel-integrated instantiation for one launch (pg_direct_integral.cu).
 const void *pick_direct_integral(int dtype, bool vec_ok, int cutoff, int periodic, int hint);
 cudaError_t direct_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tuning &t,

@@ -326,6 +326,33 @@ def loss_weights(wl: Workload, molecules=None, shard: int | None = None) -> np.n
     return out
 
 
+REFINE_ITERS = 50      # descent steps per grid reversal
+REFINE_LR = 0.02       # step size (A^2 per unit of the squared grid error's gradient)
+REFINE_NOISE = 0.1     # A, standard deviation of the start's displacement from the truth
+
+
+def refinement(shard: int | None = None, n_mol: int = 1024) -> Workload:
+    """Grid reversal (Sec. IV-A): 1024 QM9-shaped molecules on 5ch 32^3 @0.5 A with
+    per-element sigma and a spherical 3 sigma cutoff.  The grid to reverse is that of the
+    true coordinates; descent starts from them displaced by N(0, 0.1 A) per coordinate
+    (``refinement_start``) and takes REFINE_ITERS steps of REFINE_LR."""
+    n = (32, 32, 32)
+    batch = qm9_batch(5, n_mol, n, 0.5, shard)
+    return Workload("refinement", batch, *n, 5, QM9_SIGMA.copy(), CUTOFF_SPHERE, 3.0, False,
+                    "f32",
+                    f"{n_mol} QM9-shaped molecules, 5ch 32^3 @0.5A, start = truth + N(0, "
+                    f"{REFINE_NOISE} A), {REFINE_ITERS} descent steps of {REFINE_LR}")
+
+
+def refinement_start(wl: Workload, shard: int | None = None) -> np.ndarray:
+    """Seeded starting coordinates for grid reversal: the true coordinates plus N(0,
+    REFINE_NOISE) per coordinate (float32 [N, 3])."""
+    rng = np.random.default_rng([SEED_BASE + 5, 1] if shard is None
+                                else [SEED_BASE + 5, 1, shard])
+    noise = rng.normal(0.0, REFINE_NOISE, wl.batch.coords.shape)
+    return (wl.batch.coords.astype(np.float64) + noise).astype(np.float32)
+
+
 WORKLOADS = {
     "plain_small": plain_small,
     "qm9_shaped": qm9_shaped,
@@ -333,6 +360,7 @@ WORKLOADS = {
     "precision_form_integral": precision_form_integral,
     "crystal_shaped": crystal_shaped,
     "differentiation": differentiation,
+    "refinement": refinement,
 }
 
 

@@ -105,3 +105,21 @@ def test_tuning_cache_file_round_trip(lib, tmp_path):
     bad = tmp_path / "bad.txt"
     bad.write_text("key only\n")
     assert lib.pg_tuning_load(str(bad)) == lib.PG_ERR_INVALID_ARG
+
+
+def test_refine_rejects_bad_arguments_on_the_host(lib):
+    g, keep = _grid(lib)
+    L = lib.load()
+    b = lib.pg_batch(n_mol=1, n_atoms=1)
+    bad = [
+        (dict(iters=-1, lr=0.1, eps=0.0), "iters"),
+        (dict(iters=3, lr=-1.0, eps=0.0), "lr"),
+        (dict(iters=3, lr=float("inf"), eps=0.0), "lr"),
+        (dict(iters=3, lr=0.1, eps=-1.0), "eps"),
+    ]
+    for kw, needle in bad:
+        st = L.pg_refine(b, g, None, None, None, None, None, kw["iters"], kw["lr"], kw["eps"],
+                         None)
+        assert st == lib.PG_ERR_INVALID_ARG and needle in lib.last_error(), (kw, lib.last_error())
+    assert L.pg_refine_work_floats(b, g) == 5 * 32 ** 3 + 3
+
