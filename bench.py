@@ -707,7 +707,7 @@ def main():
     ap.add_argument("--workload", default="qm9_shaped",
                     choices=["qm9_shaped", "plain_small", "precision_form",
                              "precision_form_integral", "crystal_shaped", "differentiation",
-                             "refinement"])
+                             "refinement", "pipeline_single_channel"])
     ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default=None)
     ap.add_argument("--path", choices=["auto", "direct", "separable"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")

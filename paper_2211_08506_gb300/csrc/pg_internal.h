@@ -96,13 +96,16 @@ struct BackwardArgs {
 };
 
 struct SeparableArgs {
-    CUtensorMap out_map;  // 3D [n_mol][C nx][ny nz] view of `out` for TMA stores (pipelined)
+    CUtensorMap out_map;  // TMA view of `out` (pipelined): 3D [n_mol][C nx][ny nz], or 2D
+                          // [n_mol C nx][ny nz] rows when molecules are packed
     Inputs in;
     void *out;
     unsigned *err;
     Geometry geo;
     int m_tiles;  // 128-row tiles of the (channel, x) axis per molecule
     int n_tile;   // output columns per tensor-core tile
+    int pack;     // pipelined: molecules per 128-row tile when C nx divides 128 (else 0)
+    int kslots;   // pipelined: K chunks whose atom tables stay resident per tile (>= 1)
 };
 
 // A fully resolved kernel launch (function, shape, single by-value argument struct), so

@@ -35,6 +35,8 @@
 
 #include <type_traits>
 
+#include <cmath>
+
 #include "pg_internal.h"
 
 namespace pgi {
@@ -216,6 +218,15 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap *map, uint32_t sr
         "cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
             reinterpret_cast<uint64_t>(map)),
         "r"(src), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, uint32_t src, int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(src), "r"(x), "r"(y)
         : "memory");
 }
 
@@ -610,7 +621,8 @@ struct PipeLayout {
     int bars, tmem, flag, atoms, stage0, stage_bytes, a_bytes, gx, gy, gz, out, out_stride, total;
 };
 
-__host__ __device__ inline PipeLayout pipe_layout(int nx, int ny, int nz, int n_tile, int esz)
+__host__ __device__ inline PipeLayout pipe_layout(int nx, int ny, int nz, int n_tile, int esz,
+                                               int kslots)
 {
     PipeLayout L;
     int o = 0;
@@ -622,20 +634,20 @@ __host__ __device__ inline PipeLayout pipe_layout(int nx, int ny, int nz, int n_
     o += 8;
     o = align_up(o, 128);
     L.atoms = o;
-    o += kKC * 2 * 16;
+    o += kslots * kKC * 4 * 16;  // per slot: pos, aux, geometry (2)
     o = align_up(o, 1024);
     L.a_bytes = kRows * kKC * 2;
     L.stage_bytes = align_up(L.a_bytes + n_tile * kKC * 2, 1024);
     L.stage0 = o;
     o += kPipeStages * L.stage_bytes;
     L.gx = o;
-    o += nx * kTabX * 4;
+    o += kslots * nx * kTabX * 4;
     o = align_up(o, 128);
     L.gy = o;
-    o += ny * kTab * 4;
+    o += kslots * ny * kTab * 4;
     o = align_up(o, 128);
     L.gz = o;
-    o += nz * kTab * 4;
+    o += kslots * nz * kTab * 4;
     o = align_up(o, 1024);
     L.out = o;
     L.out_stride = (n_tile * esz / 128) * 4096;  // per warp: slabs of 32 rows x 128 bytes
@@ -703,16 +715,44 @@ __device__ __forceinline__ void warp_arrive(uint32_t bar)
 }
 
 struct PipeItem {
-    int b, m0, a0, a1, n_kc;
+    int b, nb, m0, a0, a1, n_kc;  // first molecule, molecules in the tile (packed), rows
     float ox, oy, oz, hx, hy, hz;
     unsigned bad;  // PG_DEVERR_* bits of this molecule (its grid is then all zeros)
 };
 
-__device__ __forceinline__ PipeItem pipe_item(const SeparableArgs &A, long long item)
+// Packed tiles (A.pack > 0): item i holds molecules i*pack .. i*pack + nb - 1, whose rows
+// (molecule-major, C nx each) fill the 128-row tile and whose atoms are one contiguous CSR
+// range.  If any of them has bad offsets the whole tile is left without atoms (its grids
+// are written as zeros) and flagged; a molecule with bad spacing loses only its own atoms.
+__device__ __forceinline__ PipeItem pipe_item_packed(const SeparableArgs &A, long long item)
 {
     const Geometry &G = A.geo;
     PipeItem it;
+    it.b = (int)(item * A.pack);
+    it.nb = min(A.pack, G.n_mol - it.b);
+    it.m0 = 0;
+    it.ox = it.oy = it.oz = 0.0f;
+    it.hx = it.hy = it.hz = 1.0f;
+    it.a0 = __ldg(A.in.mol_off + it.b);
+    it.a1 = __ldg(A.in.mol_off + it.b + it.nb);
+    bool off_ok = (it.a0 >= 0) && (it.a1 <= G.n_atoms);
+    for (int k = 0; k < it.nb && off_ok; ++k)
+        off_ok = __ldg(A.in.mol_off + it.b + k) <= __ldg(A.in.mol_off + it.b + k + 1);
+    it.bad = off_ok ? 0u : PG_DEVERR_OFFSETS;
+    if (it.bad) it.a0 = it.a1 = 0;
+    const int n = it.a1 - it.a0;
+    it.n_kc = n > 0 ? (n + kKC - 1) / kKC : 1;
+    return it;
+}
+
+template <bool PACK>
+__device__ __forceinline__ PipeItem pipe_item(const SeparableArgs &A, long long item)
+{
+    if (PACK) return pipe_item_packed(A, item);
+    const Geometry &G = A.geo;
+    PipeItem it;
     it.b = (int)(item / A.m_tiles);
+    it.nb = 1;
     it.m0 = (int)(item % A.m_tiles) * kRows;
     it.a0 = __ldg(A.in.mol_off + it.b);
     it.a1 = __ldg(A.in.mol_off + it.b + 1);
@@ -732,7 +772,7 @@ __device__ __forceinline__ PipeItem pipe_item(const SeparableArgs &A, long long 
     return it;
 }
 
-template <typename T, int CUT, bool PER, int FORM>
+template <typename T, int CUT, bool PER, int FORM, bool PACK>
 __global__ void __launch_bounds__(kPipeThreads, 2)
     separable_pipe_kernel(const __grid_constant__ SeparableArgs A)
 {
@@ -742,7 +782,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
     const int warp = tid >> 5;
     const int lane = tid & 31;
     const int n_tile = A.n_tile;
-    const PipeLayout L = pipe_layout(G.nx, G.ny, G.nz, n_tile, (int)sizeof(T));
+    const PipeLayout L = pipe_layout(G.nx, G.ny, G.nz, n_tile, (int)sizeof(T), A.kslots);
     const uint32_t bars = smem_u32(smem + L.bars);
     auto b_full = [&](int s) { return bars + 8u * s; };
     auto b_empty = [&](int s) { return bars + 8u * (2 + s); };
@@ -773,30 +813,37 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
     const int M = G.C * G.nx;
     const int N = G.ny * G.nz;
     const int n_chunks = (N + n_tile - 1) / n_tile;
-    const long long n_items = (long long)G.n_mol * A.m_tiles;
+    const long long n_items = PACK ? ((long long)G.n_mol + A.pack - 1) / A.pack
+                                         : (long long)G.n_mol * A.m_tiles;
 
     if (warp >= 4 && warp < 8) {
         // ------------------------------------------------------------------ producer
         const int p = tid - 128;
-        float4 *atom_pos = reinterpret_cast<float4 *>(smem + L.atoms);
-        float4 *atom_aux = atom_pos + kKC;
-        float *tgx = reinterpret_cast<float *>(smem + L.gx);
-        float *tgy = reinterpret_cast<float *>(smem + L.gy);
-        float *tgz = reinterpret_cast<float *>(smem + L.gz);
+        // Per atom of the K chunk: {x, y, z, q}, {r2, elem, k_erf, molecule within the tile},
+        // and its molecule's grid geometry {ox, oy, oz, hx}, {hy, hz, -, -}.
+        // Tables of up to A.kslots K chunks stay resident for a tile, so a tile with several
+        // chunks builds each once instead of once per N chunk.
+        float4 *const atoms0 = reinterpret_cast<float4 *>(smem + L.atoms);
+        float *const tgx0 = reinterpret_cast<float *>(smem + L.gx);
+        float *const tgy0 = reinterpret_cast<float *>(smem + L.gy);
+        float *const tgz0 = reinterpret_cast<float *>(smem + L.gz);
         long long stage_item[kPipeStages] = {-1, -1};
         const int dy32 = 32 / G.nz, dz32 = 32 - (32 / G.nz) * G.nz;
         unsigned step = 0;
         bool ok = true;
         for (long long item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-            const PipeItem it = pipe_item(A, item);
+            const PipeItem it = pipe_item<PACK>(A, item);
             if (it.bad && p == 0 && it.m0 == 0) atomicOr(A.err, it.bad);
-            const float Lx = G.nx * it.hx, Ly = G.ny * it.hy, Lz = G.nz * it.hz;
-            const float iLx = 1.0f / Lx, iLy = 1.0f / Ly, iLz = 1.0f / Lz;
+            // This producer's A row: molecule lm of the tile (0 unless packed), channel, x.
             const int R = it.m0 + p;
-            const bool row_ok = R < M;
-            const int row_c = row_ok ? R / G.nx : -2;
-            const int row_x = row_ok ? R - (R / G.nx) * G.nx : 0;
-            const float vx = fmaf((float)row_x + 0.5f, it.hx, it.ox);
+            const int lm = PACK ? R / M : 0;
+            const int r = R - lm * M;
+            const bool row_ok = PACK ? lm < it.nb : R < M;
+            const int row_c = row_ok ? r / G.nx : -2;
+            const int row_x = row_ok ? r - (r / G.nx) * G.nx : 0;
+            // The row's voxel-centre x for a one-molecule tile (packed tiles take it from the
+            // atom's own molecule below).
+            const float vx_item = fmaf((float)row_x + 0.5f, it.hx, it.ox);
             for (int nc = 0; nc < n_chunks && ok; ++nc) {
                 const int n0 = nc * n_tile;
                 for (int kc = 0; kc < it.n_kc && ok; ++kc, ++step) {
@@ -809,26 +856,70 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                     }
                     unsigned char *sa = smem + L.stage0 + s * L.stage_bytes;
                     unsigned char *sb = sa + L.a_bytes;
-                    const bool new_atoms = (nc == 0 && kc == 0) || it.n_kc > 1;
+                    const bool resident = it.n_kc <= A.kslots;
+                    const int slot = resident ? kc : 0;
+                    float4 *atom_pos = atoms0 + slot * 4 * kKC;
+                    float4 *atom_aux = atom_pos + kKC;
+                    float4 *atom_g0 = atom_pos + 2 * kKC;
+                    float4 *atom_g1 = atom_pos + 3 * kKC;
+                    float *tgx = tgx0 + slot * G.nx * kTabX;
+                    float *tgy = tgy0 + slot * G.ny * kTab;
+                    float *tgz = tgz0 + slot * G.nz * kTab;
+                    const bool new_atoms =
+                        resident ? nc == 0 : ((nc == 0 && kc == 0) || it.n_kc > 1);
                     if (new_atoms) {
                         producer_sync();  // every producer is done reading the old tables
                         if (p < kKC) {
                             const int ai = it.a0 + kc * kKC + p;
                             float4 pos = make_float4(0.f, 0.f, 0.f, 0.f);
                             float4 aux = make_float4(0.f, -1.f, 0.f, 0.f);
+                            float4 g0 = make_float4(0.f, 0.f, 0.f, 1.f);
+                            float4 g1 = make_float4(1.f, 1.f, 0.f, 0.f);
                             if (ai < it.a1) {
+                                // The atom's molecule: the item's, or in a packed tile the last
+                                // k with mol_off[b + k] <= ai.
+                                int k = 0;
+                                if (PACK) {
+                                    int lo = 0, hi = it.nb - 1;
+                                    while (lo < hi) {
+                                        const int mid = (lo + hi + 1) >> 1;
+                                        if (__ldg(A.in.mol_off + it.b + mid) <= ai) lo = mid;
+                                        else hi = mid - 1;
+                                    }
+                                    k = lo;
+                                }
+                                const int mb = it.b + k;
+                                if (PACK) {
+                                    g0 = make_float4(__ldg(A.in.origin + 3 * mb),
+                                                     __ldg(A.in.origin + 3 * mb + 1),
+                                                     __ldg(A.in.origin + 3 * mb + 2),
+                                                     __ldg(A.in.spacing + 3 * mb));
+                                    g1 = make_float4(__ldg(A.in.spacing + 3 * mb + 1),
+                                                     __ldg(A.in.spacing + 3 * mb + 2), 0.f, 0.f);
+                                } else {
+                                    g0 = make_float4(it.ox, it.oy, it.oz, it.hx);
+                                    g1 = make_float4(it.hy, it.hz, 0.f, 0.f);
+                                }
+                                const bool sp_ok = g0.w > 0.0f && g1.x > 0.0f && g1.y > 0.0f &&
+                                                   g0.w < INFINITY && g1.x < INFINITY &&
+                                                   g1.y < INFINITY;
                                 const int e = __ldg(A.in.elem + ai);
-                                if ((unsigned)e < (unsigned)G.C) {
+                                if (!sp_ok) {
+                                    if (ai == __ldg(A.in.mol_off + mb))
+                                        atomicOr(A.err, PG_DEVERR_SPACING);
+                                } else if ((unsigned)e < (unsigned)G.C) {
                                     pos = make_float4(__ldg(A.in.coords + 3 * ai),
                                                       __ldg(A.in.coords + 3 * ai + 1),
                                                       __ldg(A.in.coords + 3 * ai + 2), G.q[e]);
-                                    aux = make_float4(G.r2[e], (float)e, G.kerf[e], 0.f);
+                                    aux = make_float4(G.r2[e], (float)e, G.kerf[e], (float)k);
                                 } else if (it.m0 == 0) {
                                     atomicOr(A.err, PG_DEVERR_ELEMENT);
                                 }
                             }
                             atom_pos[p] = pos;
                             atom_aux[p] = aux;
+                            atom_g0[p] = g0;
+                            atom_g1[p] = g1;
                         }
                         producer_sync();
                         // Per-axis tables of this K chunk: g_y, g_z, and for the erf form also
@@ -839,14 +930,16 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             // next lane (Sec. VI-A's reuse of the subtrahend): n + n/32 erf
                             // evaluations per atom and axis instead of 2n.
                             const int pw = p >> 5;
-                            auto erf_table = [&](float *tab, int n, int stride, float h, float o,
-                                                 int axis) {
+                            auto erf_table = [&](float *tab, int n, int stride, int axis) {
                                 const int blocks = (n + 31) >> 5;
                                 for (int task = pw; task < kKC * blocks; task += 4) {
                                     const int j = task % kKC, i = (task / kKC) * 32 + lane;
                                     const float4 q4 = atom_pos[j];
                                     const float4 aux = atom_aux[j];
+                                    const float4 g0 = atom_g0[j], g1 = atom_g1[j];
                                     const float mu = axis == 0 ? q4.x : (axis == 1 ? q4.y : q4.z);
+                                    const float o = axis == 0 ? g0.x : (axis == 1 ? g0.y : g0.z);
+                                    const float h = axis == 0 ? g0.w : (axis == 1 ? g1.x : g1.y);
                                     const float e_lo = erff((fmaf((float)i, h, o) - mu) * aux.z);
                                     float e_hi = __shfl_down_sync(0xffffffffu, e_lo, 1);
                                     if (lane == 31)
@@ -858,18 +951,23 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                                     if (i < n) tab[i * stride + j] = v;
                                 }
                             };
-                            erf_table(tgx, G.nx, kTabX, it.hx, it.ox, 0);
-                            erf_table(tgy, G.ny, kTab, it.hy, it.oy, 1);
-                            erf_table(tgz, G.nz, kTab, it.hz, it.oz, 2);
+                            erf_table(tgx, G.nx, kTabX, 0);
+                            erf_table(tgy, G.ny, kTab, 1);
+                            erf_table(tgz, G.nz, kTab, 2);
                         }
                         for (int i = p; FORM == 1 && PER && i < G.nx * kKC; i += 128) {
                             const int x = i / kKC, j = i - (i / kKC) * kKC;
                             const float4 q4 = atom_pos[j];
+                            const float4 g0 = PACK ? atom_g0[j]
+                                                         : make_float4(it.ox, 0.f, 0.f, it.hx);
                             float v = 0.0f;
                             if (atom_aux[j].y >= 0.0f) {
-                                float d = fmaf((float)x + 0.5f, it.hx, it.ox) - q4.x;
-                                if (PER) d = wrap(d, Lx, iLx);
-                                v = axis_factor<CUT, FORM>(d, q4.w, atom_aux[j].x, it.hx,
+                                float d = fmaf((float)x + 0.5f, g0.w, g0.x) - q4.x;
+                                if (PER) {
+                                    const float Lx = G.nx * g0.w;
+                                    d = wrap(d, Lx, 1.0f / Lx);
+                                }
+                                v = axis_factor<CUT, FORM>(d, q4.w, atom_aux[j].x, g0.w,
                                                      atom_aux[j].z);
                             }
                             tgx[x * kTabX + j] = v;
@@ -877,11 +975,16 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                         for (int i = p; (FORM == 0 || PER) && i < G.ny * kKC; i += 128) {
                             const int y = i / kKC, j = i - (i / kKC) * kKC;
                             const float4 q4 = atom_pos[j];
+                            const float oy = PACK ? atom_g0[j].y : it.oy;
+                            const float hy = PACK ? atom_g1[j].x : it.hy;
                             float v = 0.0f;
                             if (atom_aux[j].y >= 0.0f) {
-                                float d = fmaf((float)y + 0.5f, it.hy, it.oy) - q4.y;
-                                if (PER) d = wrap(d, Ly, iLy);
-                                v = axis_factor<CUT, FORM>(d, q4.w, atom_aux[j].x, it.hy,
+                                float d = fmaf((float)y + 0.5f, hy, oy) - q4.y;
+                                if (PER) {
+                                    const float Ly = G.ny * hy;
+                                    d = wrap(d, Ly, 1.0f / Ly);
+                                }
+                                v = axis_factor<CUT, FORM>(d, q4.w, atom_aux[j].x, hy,
                                                      atom_aux[j].z);
                             }
                             tgy[y * kTab + j] = v;
@@ -889,11 +992,16 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                         for (int i = p; (FORM == 0 || PER) && i < G.nz * kKC; i += 128) {
                             const int z = i / kKC, j = i - (i / kKC) * kKC;
                             const float4 q4 = atom_pos[j];
+                            const float oz = PACK ? atom_g0[j].z : it.oz;
+                            const float hz = PACK ? atom_g1[j].y : it.hz;
                             float v = 0.0f;
                             if (atom_aux[j].y >= 0.0f) {
-                                float d = fmaf((float)z + 0.5f, it.hz, it.oz) - q4.z;
-                                if (PER) d = wrap(d, Lz, iLz);
-                                v = axis_factor<CUT, FORM>(d, q4.w, atom_aux[j].x, it.hz,
+                                float d = fmaf((float)z + 0.5f, hz, oz) - q4.z;
+                                if (PER) {
+                                    const float Lz = G.nz * hz;
+                                    d = wrap(d, Lz, 1.0f / Lz);
+                                }
+                                v = axis_factor<CUT, FORM>(d, q4.w, atom_aux[j].x, hz,
                                                      atom_aux[j].z);
                             }
                             tgz[z * kTab + j] = v;
@@ -911,14 +1019,22 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                                 const int j = jg * 8 + t;
                                 const float4 aux = atom_aux[j];
                                 v[t] = 0.0f;
-                                if (row_ok && (int)aux.y == row_c) {
+                                if (row_ok && (int)aux.y == row_c && (int)aux.w == lm) {
                                     if (FORM == 1) {
                                         v[t] = tgx[row_x * kTabX + j];
                                     } else {
+                                        const float hx = PACK ? atom_g0[j].w : it.hx;
+                                        const float vx =
+                                            PACK
+                                                ? fmaf((float)row_x + 0.5f, hx, atom_g0[j].x)
+                                                : vx_item;
                                         float d = vx - atom_pos[j].x;
-                                        if (PER) d = wrap(d, Lx, iLx);
+                                        if (PER) {
+                                            const float Lx = G.nx * hx;
+                                            d = wrap(d, Lx, 1.0f / Lx);
+                                        }
                                         v[t] = axis_factor<CUT, FORM>(d, atom_pos[j].w, aux.x,
-                                                                      it.hx, aux.z);
+                                                                      hx, aux.z);
                                     }
                                 }
                             }
@@ -971,7 +1087,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
             unsigned step = 0, tile = 0;
             bool ok = true;
             for (long long item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-                const PipeItem it = pipe_item(A, item);
+                const PipeItem it = pipe_item<PACK>(A, item);
                 for (int nc = 0; nc < n_chunks && ok; ++nc, ++tile) {
                     const int buf = (int)(tile & 1u);
                     const uint32_t aph = (tile >> 1) & 1u;
@@ -1009,7 +1125,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
         unsigned tile = 0;
         bool ok = true;
         for (long long item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
-            const PipeItem it = pipe_item(A, item);
+            const PipeItem it = pipe_item<PACK>(A, item);
             for (int nc = 0; nc < n_chunks && ok; ++nc, ++tile) {
                 const int buf = (int)(tile & 1u);
                 const uint32_t ph = (tile >> 1) & 1u;
@@ -1036,14 +1152,29 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                 warp_arrive(acc_empty(buf));  // includes __syncwarp: the warp's rows are staged
                 // One TMA tensor store per 32-row x 128-byte slab; the tensor map clips rows
                 // past M and columns past N.  Boxes lying wholly outside are skipped.
-                const int row0 = it.m0 + warp * 32;
-                if (lane == 0 && row0 < M) {
-                    for (int sl = 0; sl < slabs; ++sl) {
-                        const int x = nc * n_tile + sl * slab_cols;
-                        if (x < N)
-                            tma_store_3d(&A.out_map, smem_u32(wstage + sl * 4096), x, row0, it.b);
+                if (PACK) {
+                    // Packed: rows are global (molecule-major); the map clips past the batch.
+                    const long long grow = (long long)it.b * M + warp * 32;
+                    if (lane == 0 && grow < (long long)G.n_mol * M) {
+                        for (int sl = 0; sl < slabs; ++sl) {
+                            const int x = nc * n_tile + sl * slab_cols;
+                            if (x < N)
+                                tma_store_2d(&A.out_map, smem_u32(wstage + sl * 4096), x,
+                                             (int)grow);
+                        }
+                        bulk_commit();
                     }
-                    bulk_commit();
+                } else {
+                    const int row0 = it.m0 + warp * 32;
+                    if (lane == 0 && row0 < M) {
+                        for (int sl = 0; sl < slabs; ++sl) {
+                            const int x = nc * n_tile + sl * slab_cols;
+                            if (x < N)
+                                tma_store_3d(&A.out_map, smem_u32(wstage + sl * 4096), x, row0,
+                                             it.b);
+                        }
+                        bulk_commit();
+                    }
                 }
             }
         }
@@ -1060,11 +1191,14 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
 }
 
 template <typename T, int CUT, int FORM>
-const void *pick_per(int periodic, bool pipe)
+const void *pick_per(int periodic, bool pipe, bool pack)
 {
+    if (pipe && pack)
+        return periodic ? (const void *)separable_pipe_kernel<T, CUT, true, FORM, true>
+                        : (const void *)separable_pipe_kernel<T, CUT, false, FORM, true>;
     if (pipe)
-        return periodic ? (const void *)separable_pipe_kernel<T, CUT, true, FORM>
-                        : (const void *)separable_pipe_kernel<T, CUT, false, FORM>;
+        return periodic ? (const void *)separable_pipe_kernel<T, CUT, true, FORM, false>
+                        : (const void *)separable_pipe_kernel<T, CUT, false, FORM, false>;
     return periodic ? (const void *)separable_kernel<T, CUT, true, FORM>
                     : (const void *)separable_kernel<T, CUT, false, FORM>;
 }
@@ -1072,13 +1206,13 @@ const void *pick_per(int periodic, bool pipe)
 // Point-sampled (FORM 0) and voxel-integrated (FORM 1, Sec. III-A) operand factors are
 // separate instantiations, so the point form carries no erf code.
 template <typename T>
-const void *pick_cut(int cutoff, int periodic, bool pipe, int form)
+const void *pick_cut(int cutoff, int periodic, bool pipe, int form, bool pack)
 {
     if (form == PG_FORM_INTEGRAL)
-        return cutoff == PG_CUTOFF_BOX ? pick_per<T, PG_CUTOFF_BOX, 1>(periodic, pipe)
-                                       : pick_per<T, PG_CUTOFF_NONE, 1>(periodic, pipe);
-    return cutoff == PG_CUTOFF_BOX ? pick_per<T, PG_CUTOFF_BOX, 0>(periodic, pipe)
-                                   : pick_per<T, PG_CUTOFF_NONE, 0>(periodic, pipe);
+        return cutoff == PG_CUTOFF_BOX ? pick_per<T, PG_CUTOFF_BOX, 1>(periodic, pipe, pack)
+                                       : pick_per<T, PG_CUTOFF_NONE, 1>(periodic, pipe, pack);
+    return cutoff == PG_CUTOFF_BOX ? pick_per<T, PG_CUTOFF_BOX, 0>(periodic, pipe, pack)
+                                   : pick_per<T, PG_CUTOFF_NONE, 0>(periodic, pipe, pack);
 }
 
 }  // namespace
@@ -1118,11 +1252,15 @@ cudaError_t encode_out_map(SeparableArgs &a, int dtype)
                                    : dtype == PG_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const cuuint64_t N = (cuuint64_t)a.geo.ny * a.geo.nz, M = (cuuint64_t)a.geo.C * a.geo.nx;
-    const cuuint64_t dims[3] = {N, M, (cuuint64_t)a.geo.n_mol};
+    // Packed tiles store global rows (2D); otherwise rows of one molecule (3D), so that a
+    // molecule's last tile cannot spill into the next molecule.
+    const cuuint32_t rank = a.pack > 0 ? 2 : 3;
+    const cuuint64_t dims[3] = {N, a.pack > 0 ? M * (cuuint64_t)a.geo.n_mol : M,
+                                (cuuint64_t)a.geo.n_mol};
     const cuuint64_t strides[2] = {N * esz, N * M * esz};
     const cuuint32_t box[3] = {(cuuint32_t)(128 / esz), 32, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    const CUresult r = encode(&a.out_map, dt, 3, a.out, dims, strides, box, estr,
+    const CUresult r = encode(&a.out_map, dt, rank, a.out, dims, strides, box, estr,
                               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorNotSupported;
@@ -1138,24 +1276,35 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
     int n_tile = t.n_tile;
     if (n_tile != 64 && n_tile != 128 && n_tile != 256) n_tile = 128;
     const int esz = dtype == PG_F32 ? 4 : 2;
-    auto bytes = [&](int nt) {
-        return pipe ? pipe_layout(a.geo.nx, a.geo.ny, a.geo.nz, nt, esz).total
+    // Molecules with fewer than 128 (channel, x) rows share a tile when their rows divide it.
+    const int Mrows = a.geo.C * a.geo.nx;
+    a.pack = (pipe && Mrows < kRows && kRows % Mrows == 0) ? kRows / Mrows : 0;
+    // Resident K-chunk tables: enough for a tile of average atoms with headroom, at most 8.
+    const double atoms_per_tile = (a.pack > 0 ? a.pack : 1) * (a.geo.n_mol > 0
+                                      ? (double)a.geo.n_atoms / a.geo.n_mol : 0.0);
+    int kslots = (int)std::ceil(1.5 * atoms_per_tile / kKC);
+    kslots = kslots < 1 ? 1 : (kslots > 8 ? 8 : kslots);
+    auto bytes = [&](int nt, int ks) {
+        return pipe ? pipe_layout(a.geo.nx, a.geo.ny, a.geo.nz, nt, esz, ks).total
                     : sep_layout(a.geo.ny, a.geo.nz, nt, esz).total;
     };
+    while (kslots > 1 && bytes(n_tile, kslots) > 227 * 1024) --kslots;
     // Largest requested tile whose shared-memory footprint fits one SM's 227 KB.
-    while (n_tile > 64 && bytes(n_tile) > 227 * 1024) n_tile /= 2;
-    const int smem = bytes(n_tile);
+    while (n_tile > 64 && bytes(n_tile, kslots) > 227 * 1024) n_tile /= 2;
+    const int smem = bytes(n_tile, kslots);
     if (smem > 227 * 1024) return cudaErrorNotSupported;
     a.n_tile = n_tile;
+    a.kslots = kslots;
     a.m_tiles = (a.geo.C * a.geo.nx + kRows - 1) / kRows;
     if (pipe) {
         cudaError_t em = encode_out_map(a, dtype);
         if (em != cudaSuccess) return em;
     }
     const int cut = a.geo.cutoff, per = a.geo.periodic, form = a.geo.form;
-    const void *f = dtype == PG_F32   ? pick_cut<float>(cut, per, pipe, form)
-                    : dtype == PG_F16 ? pick_cut<__half>(cut, per, pipe, form)
-                                      : pick_cut<__nv_bfloat16>(cut, per, pipe, form);
+    const bool pack = a.pack > 0;
+    const void *f = dtype == PG_F32   ? pick_cut<float>(cut, per, pipe, form, pack)
+                    : dtype == PG_F16 ? pick_cut<__half>(cut, per, pipe, form, pack)
+                                      : pick_cut<__nv_bfloat16>(cut, per, pipe, form, pack);
     const int threads = pipe ? kPipeThreads : kRows;
     const int tmem_cols = pipe ? 2 * n_tile : n_tile;
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -1181,7 +1330,8 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
     if (512 / tmem_cols < per_sm) per_sm = 512 / tmem_cols;
     if (per_sm < 1) return cudaErrorNotSupported;
     if (t.blocks_per_sm > 0 && t.blocks_per_sm < per_sm) per_sm = t.blocks_per_sm;
-    const long long items = (long long)a.geo.n_mol * a.m_tiles;
+    const long long items = a.pack > 0 ? ((long long)a.geo.n_mol + a.pack - 1) / a.pack
+                                       : (long long)a.geo.n_mol * a.m_tiles;
     long long blocks = (long long)sm_count * per_sm;
     if (blocks > items) blocks = items;
     if (blocks < 1) blocks = 1;

@@ -326,6 +326,42 @@ def loss_weights(wl: Workload, molecules=None, shard: int | None = None) -> np.n
     return out
 
 
+def _pcqm_molecule(rng: np.random.Generator):
+    """PCQM4Mv2-like size: k ~ U{3..25} heavy atoms and U{k/2 .. k+4} hydrogens, at most 51
+    atoms, placed on one random walk (bond 1.0-1.5 A)."""
+    k = int(rng.integers(3, 26))
+    n_h = int(rng.integers(k // 2, k + 5))
+    n = min(k + n_h, 51)
+    return random_walk(rng, n)
+
+
+def pipeline_single_channel(shard: int | None = None, n_mol: int = 16384) -> Workload:
+    """The training-input use case of Sec. VII: every atom in one channel, a 32^3 grid whose
+    spatial resolution adapts to each molecule's bounding box, sigma 0.4, generated on the
+    fly for a 3D CNN (training batches of 256; one step here covers 64 of them so the output
+    exceeds L2).  The voxel function is the paper's erf integral, with a box cutoff of
+    3 sigma, stored as BF16."""
+    rng = _rng(6, shard)
+    n = (32, 32, 32)
+    sigma = 0.4
+    coords, elems, origins, spacings = [], [], [], []
+    for _ in range(n_mol):
+        pos = _pcqm_molecule(rng)
+        lo, hi = pos.min(axis=0), pos.max(axis=0)
+        extent = float((hi - lo).max()) + 2 * 3.0 * sigma   # the box keeps every support
+        h = extent / n[0]
+        coords.append(pos)
+        elems.append(np.zeros(pos.shape[0], np.int64))
+        origins.append(0.5 * (lo + hi) - 0.5 * n[0] * h)
+        spacings.append((h, h, h))
+    batch = _pack(coords, elems, origins, spacings)
+    return Workload("pipeline_single_channel", batch, *n, 1, np.full(1, sigma, np.float32),
+                    CUTOFF_BOX, 3.0, False, "bf16",
+                    f"{n_mol} PCQM4Mv2-sized molecules (4-51 atoms), 1 channel, 32^3 adaptive box, "
+                    f"sigma 0.4, erf voxel integrals, box 3 sigma, BF16",
+                    form="integral")
+
+
 REFINE_ITERS = 50      # descent steps per grid reversal
 REFINE_LR = 0.02       # step size (A^2 per unit of the squared grid error's gradient)
 REFINE_NOISE = 0.1     # A, standard deviation of the start's displacement from the truth
@@ -361,6 +397,7 @@ WORKLOADS = {
     "crystal_shaped": crystal_shaped,
     "differentiation": differentiation,
     "refinement": refinement,
+    "pipeline_single_channel": pipeline_single_channel,
 }
 
 

@@ -158,3 +158,49 @@ def test_precision_form_full_batch_sampled(pg):
     stats = grid_check(sub, oracle.Problem.from_workload(wl, batch=wl.batch.subset(idx)),
                        SEPARABLE_TOL, abs_tol=ABS_TOL["f16"])
     assert stats["max_abs_rel"] < SEPARABLE_TOL
+
+
+@pytest.mark.parametrize("C,nx,ny,nz,n_mol,cutoff,periodic,form,dtype", [
+    (1, 32, 32, 32, 9, "none", False, "point", "f16"),      # 4 molecules per tile, ragged end
+    (2, 16, 24, 32, 7, "box", False, "point", "bf16"),      # 4 per tile
+    (2, 32, 16, 16, 5, "box", True, "point", "f32"),        # 2 per tile, periodic
+    (1, 32, 32, 32, 6, "box", False, "integral", "bf16"),   # erf tables per atom's molecule
+    (4, 8, 16, 16, 33, "none", False, "integral", "f16"),   # 4 per tile, 9 tiles
+])
+def test_packed_tiles_match_oracle(pg, C, nx, ny, nz, n_mol, cutoff, periodic, form, dtype):
+    # Molecules whose C * nx rows divide the 128-row tile share one tile: their atoms form
+    # one K range, each atom carries its own molecule's grid geometry, and the rows go out as
+    # global rows.  Every molecule gets its own spacing so a mix-up between molecules shows.
+    wl = synth.plain_small(n_mol=n_mol)
+    wl.n_channels = C
+    wl.sigma = np.array([0.45, 0.55, 0.5, 0.6][:C], np.float32)
+    wl.batch.elem = (wl.batch.elem % C).astype(np.int32)
+    wl.cutoff, wl.periodic, wl.form = cutoff, periodic, form
+    wl.nx, wl.ny, wl.nz = nx, ny, nz
+    if periodic:
+        wl.cutoff_k = 2.5
+    h = 0.4 + 0.05 * np.arange(n_mol, dtype=np.float32)
+    wl.batch.spacing = np.stack([h, h * 1.1, h * 0.9], axis=1).astype(np.float32)
+    G = sep(pg, wl, dtype=dtype)
+    grid_check(G, oracle.Problem.from_workload(wl), SEPARABLE_TOL, abs_tol=ABS_TOL[dtype])
+
+
+def test_packed_tiles_with_uneven_atom_counts(pg):
+    # Four molecules per tile; one tile holds far more atoms than the average, so its K
+    # chunks exceed the resident table slots and take the rebuild-per-step fallback, while
+    # the others keep their chunk tables resident.  Both must match the oracle.
+    rng = np.random.default_rng(31)
+    sizes = [3, 6, 4, 5, 150, 8, 2, 90, 7, 5, 4, 6]
+    pos = [8.0 + rng.uniform(-3, 3, (n, 3)) for n in sizes]
+    el = [np.zeros(n, np.int64) for n in sizes]
+    nb = synth._pack(pos, el, np.zeros((len(sizes), 3)),
+                     np.full((len(sizes), 3), 0.5))
+    wl = small("none", False, n_mol=len(sizes), shape=(32, 32, 32))
+    wl.n_channels = 1
+    wl.sigma = np.array([0.5], np.float32)
+    for form in ("point", "integral"):
+        wl.form = form
+        G = sep(pg, wl, batch=nb, dtype="f16")
+        grid_check(G, oracle.Problem.from_workload(wl, batch=nb), SEPARABLE_TOL,
+                   abs_tol=ABS_TOL["f16"])
+
