@@ -13,6 +13,7 @@ Functions (each mirrors one C entry point; see the C file for the equations):
 * ``voxelize_band(...)``                                 - same, split at the cutoff surface
 * ``separable(...)``                                     - Sec. III-A / VI-A per-axis form
 * ``gradient(...)``                                      - Sec. IV-C, dL/dx for L = <W, G>
+* ``gradient_weight(...)``                               - dL/dw of a weighted grid
 * ``fd_gradient_frozen(...)``                            - central differences, frozen support
 * ``refine(...)``                                        - Sec. IV-A/IV-C grid reversal by descent
 """
@@ -67,6 +68,8 @@ class _Problem(ctypes.Structure):
         ("cutoff", ctypes.c_int32),
         ("periodic", ctypes.c_int32),
         ("form", ctypes.c_int32),
+        ("weight", ctypes.c_void_p),
+        ("cell", ctypes.c_void_p),
     ]
 
 
@@ -81,6 +84,7 @@ def _load():
             lib.pgo_voxelize_band.argtypes = [P, ctypes.c_double, dp, dp, ctypes.c_int]
             lib.pgo_separable.argtypes = [P, dp, ctypes.c_int]
             lib.pgo_gradient.argtypes = [P, ctypes.c_int, dp, dp, ctypes.c_int]
+            lib.pgo_gradient_weight.argtypes = [P, ctypes.c_int, dp, dp, ctypes.c_int]
             lib.pgo_fd_gradient_frozen.argtypes = [P, dp, ctypes.c_double, dp, ctypes.c_int]
             lib.pgo_refine.argtypes = [P, dp, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                        dp, dp, dp, ctypes.c_int]
@@ -88,17 +92,20 @@ def _load():
             lib.pgo_inner.argtypes = [dp, dp, ctypes.c_long]
             lib.pgo_inner.restype = ctypes.c_double
             for f in (lib.pgo_voxelize, lib.pgo_voxelize_band, lib.pgo_separable,
-                      lib.pgo_gradient, lib.pgo_fd_gradient_frozen):
+                      lib.pgo_gradient, lib.pgo_gradient_weight, lib.pgo_fd_gradient_frozen):
                 f.restype = ctypes.c_int
             _lib = lib
     return _lib
 
 
 class Problem:
-    """FP64 copy of a batch plus its grid description, kept alive for ctypes."""
+    """FP64 copy of a batch plus its grid description, kept alive for ctypes.
+
+    ``weight`` (per atom) and ``cell`` (per molecule, 3x3 rows = box edges) default to the
+    batch's own (``batch.weight`` / ``batch.cell`` when present); pass them to override."""
 
     def __init__(self, batch, nx, ny, nz, n_channels, sigma, cutoff="sphere", cutoff_k=3.0,
-                 periodic=False, coords=None, form="point"):
+                 periodic=False, coords=None, form="point", weight=None, cell=None):
         self.mol_off = np.ascontiguousarray(batch.mol_off, np.int32)
         src = batch.coords if coords is None else coords
         self.coords = np.ascontiguousarray(np.asarray(src, np.float64).reshape(-1, 3))
@@ -109,6 +116,16 @@ class Problem:
         self.shape = (self.mol_off.shape[0] - 1, int(n_channels), int(nx), int(ny), int(nz))
         if self.sigma.shape[0] != n_channels:
             raise ValueError("sigma must have one entry per channel")
+        w = weight if weight is not None else getattr(batch, "weight", None)
+        m = cell if cell is not None else getattr(batch, "cell", None)
+        self.weight = None if w is None else np.ascontiguousarray(
+            np.asarray(w, np.float64).reshape(-1))
+        self.cell = None if m is None else np.ascontiguousarray(
+            np.asarray(m, np.float64).reshape(-1, 3, 3))
+        if self.weight is not None and self.weight.shape[0] != self.coords.shape[0]:
+            raise ValueError("weight must have one entry per atom")
+        if self.cell is not None and self.cell.shape[0] != self.shape[0]:
+            raise ValueError("cell must have one 3x3 matrix per molecule")
         self.c = _Problem(
             n_mol=self.shape[0],
             mol_off=self.mol_off.ctypes.data,
@@ -122,6 +139,8 @@ class Problem:
             cutoff=CUTOFFS[cutoff],
             periodic=1 if periodic else 0,
             form=FORMS[form],
+            weight=None if self.weight is None else self.weight.ctypes.data,
+            cell=None if self.cell is None else self.cell.ctypes.data,
         )
 
     @classmethod
@@ -164,6 +183,17 @@ def gradient(prob: Problem, W: np.ndarray, mode: str = "bbox", threads: int = 0)
     g = np.empty((prob.coords.shape[0], 3), np.float64)
     _check(_load().pgo_gradient(ctypes.byref(prob.c), 0 if mode == "brute" else 1,
                                 W.ctypes.data, g.ctypes.data, threads), "gradient")
+    return g
+
+
+def gradient_weight(prob: Problem, W: np.ndarray, mode: str = "bbox",
+                    threads: int = 0) -> np.ndarray:
+    """dL/dw_a of L = <W, G> for a weighted grid: each atom's unweighted terms against W."""
+    W = np.ascontiguousarray(W, np.float64).reshape(prob.shape)
+    g = np.empty(prob.coords.shape[0], np.float64)
+    _check(_load().pgo_gradient_weight(ctypes.byref(prob.c), 0 if mode == "brute" else 1,
+                                       W.ctypes.data, g.ctypes.data, threads),
+           "gradient_weight")
     return g
 
 

@@ -44,6 +44,25 @@
  *                                            - exp(-(x_i + h - mu)^2 / 2 sigma^2)],
  *
  * times the other two axes' factors.  This uses d/dt erf(t) = (2 / sqrt(pi)) exp(-t^2).
+ *
+ * Weighted grids (Sec. III-A, the remark that the gridding function extends to weighted
+ * grids): with per-atom weights w_a every term above is multiplied by w_a, so
+ *   G = sum_a w_a chi(d) exp(...),  dL/dx_a = w_a * (the unweighted sum),
+ *   dL/dw_a = sum_v W(v) chi(d) exp(...)   (the atom's own unweighted grid against W).
+ * A null weight array means w_a = 1.
+ *
+ * General cells (Sec. III-A: the box's orientation and size are the user's choice and
+ * voxels need not be cubic; periodic crystals use the nearest image over the lattice
+ * translations).  A molecule may give a 3x3 matrix M whose rows a, b, c are the box edges
+ * along which the grid's x, y and z indices run.  Its voxel centres are then
+ *   v_ijk = o + ((i+1/2)/nx) a + ((j+1/2)/ny) b + ((k+1/2)/nz) c,
+ * and spacing is ignored.  For a periodic cell, d is the displacement to the nearest
+ * image x + t_a a + t_b b + t_c c (t integer).  It is found exactly by enumeration: with
+ * e = (v - x) M^-1 the fractional displacement and R the distance to the image t = round(e),
+ * any image at most R away has |e_k - t_k| <= R |g_k|, where g_k is column k of M^-1.  All
+ * such t are tried and the shortest d wins; among equals the first in (t_a, t_b, t_c)
+ * lexicographic order wins.  chi and the Gaussian are evaluated at that d.  The
+ * voxel-integrated and separable forms assume an axis-aligned box and reject cells.
  */
 #include <math.h>
 #include <stdint.h>
@@ -70,6 +89,8 @@ typedef struct {
     int32_t cutoff;          /* PGO_SPHERE / PGO_NONE / PGO_BOX */
     int32_t periodic;
     int32_t form;            /* PGO_POINT / PGO_INTEGRAL */
+    const double *weight;    /* [N] per-atom weights, or NULL for all ones */
+    const double *cell;      /* [B][3][3] rows = grid box edges a, b, c, or NULL */
 } pgo_problem;
 
 /* Voxel centre along one axis: o + (i + 1/2) h. */
@@ -118,6 +139,122 @@ static double term(const pgo_problem *p, int b, double sigma, double dx, double 
     return exp(-(dx * dx + dy * dy + dz * dz) / (2.0 * sigma * sigma));
 }
 
+/* Weight of atom a (1 without weights). */
+static double weight_of(const pgo_problem *p, int a) { return p->weight ? p->weight[a] : 1.0; }
+
+/* Inverse of the 3x3 row-major matrix M by its adjugate (M non-singular). */
+static void inverse3(const double *M, double *Mi)
+{
+    double det = M[0] * (M[4] * M[8] - M[5] * M[7]) - M[1] * (M[3] * M[8] - M[5] * M[6]) +
+                 M[2] * (M[3] * M[7] - M[4] * M[6]);
+    Mi[0] = (M[4] * M[8] - M[5] * M[7]) / det;
+    Mi[1] = (M[2] * M[7] - M[1] * M[8]) / det;
+    Mi[2] = (M[1] * M[5] - M[2] * M[4]) / det;
+    Mi[3] = (M[5] * M[6] - M[3] * M[8]) / det;
+    Mi[4] = (M[0] * M[8] - M[2] * M[6]) / det;
+    Mi[5] = (M[2] * M[3] - M[0] * M[5]) / det;
+    Mi[6] = (M[3] * M[7] - M[4] * M[6]) / det;
+    Mi[7] = (M[1] * M[6] - M[0] * M[7]) / det;
+    Mi[8] = (M[0] * M[4] - M[1] * M[3]) / det;
+}
+
+/* |g_k| for k = 0, 1, 2: the lengths of the columns of M^-1. */
+static void column_norms(const double *Mi, double *g)
+{
+    for (int k = 0; k < 3; ++k)
+        g[k] = sqrt(Mi[k] * Mi[k] + Mi[3 + k] * Mi[3 + k] + Mi[6 + k] * Mi[6 + k]);
+}
+
+/*
+ * Displacement d from atom position x to voxel (i, j, k) of molecule b in a general cell:
+ * v - x, or for a periodic cell the displacement to the nearest lattice image of the atom
+ * (exact enumeration, see the file header).
+ */
+static void cell_disp(const pgo_problem *p, int b, long i, long j, long k, const double *x,
+                      double *d)
+{
+    const double *M = p->cell + 9 * b, *o = p->origin + 3 * b;
+    const double u[3] = {((double)i + 0.5) / p->nx, ((double)j + 0.5) / p->ny,
+                         ((double)k + 0.5) / p->nz};
+    double d0[3];
+    for (int c = 0; c < 3; ++c)
+        d0[c] = o[c] + u[0] * M[c] + u[1] * M[3 + c] + u[2] * M[6 + c] - x[c];
+    if (!p->periodic) {
+        d[0] = d0[0];
+        d[1] = d0[1];
+        d[2] = d0[2];
+        return;
+    }
+    double Mi[9], g[3], e[3];
+    inverse3(M, Mi);
+    column_norms(Mi, g);
+    for (int c = 0; c < 3; ++c) e[c] = d0[0] * Mi[c] + d0[1] * Mi[3 + c] + d0[2] * Mi[6 + c];
+    long t0[3], lo[3], hi[3];
+    double R2 = 0.0;
+    for (int c = 0; c < 3; ++c) t0[c] = lround(e[c]);
+    for (int c = 0; c < 3; ++c) {
+        double dc = d0[c] - t0[0] * M[c] - t0[1] * M[3 + c] - t0[2] * M[6 + c];
+        R2 += dc * dc;
+    }
+    for (int c = 0; c < 3; ++c) {
+        double w = sqrt(R2) * g[c];
+        lo[c] = (long)ceil(e[c] - w);
+        hi[c] = (long)floor(e[c] + w);
+        if (lo[c] > t0[c]) lo[c] = t0[c];
+        if (hi[c] < t0[c]) hi[c] = t0[c];
+    }
+    double best = INFINITY;
+    for (long ta = lo[0]; ta <= hi[0]; ++ta)
+        for (long tb = lo[1]; tb <= hi[1]; ++tb)
+            for (long tc = lo[2]; tc <= hi[2]; ++tc) {
+                double dt[3], r2 = 0.0;
+                for (int c = 0; c < 3; ++c) {
+                    dt[c] = d0[c] - ta * M[c] - tb * M[3 + c] - tc * M[6 + c];
+                    r2 += dt[c] * dt[c];
+                }
+                if (r2 < best) {
+                    best = r2;
+                    d[0] = dt[0];
+                    d[1] = dt[1];
+                    d[2] = dt[2];
+                }
+            }
+}
+
+/*
+ * Index range [lo, hi] on axis k of a general cell that holds every voxel whose centre can
+ * be within r of the atom: the fractional coordinate of such a centre is within r |g_k| of
+ * the atom's (modulo 1 when periodic), widened by one voxel each side.  Clamped to the grid
+ * when not periodic; at most n consecutive indices when periodic.
+ */
+static void cell_support(const pgo_problem *p, int b, int k, const double *x, double r,
+                         long *lo, long *hi)
+{
+    const int n[3] = {p->nx, p->ny, p->nz};
+    if (p->cutoff == PGO_NONE) {
+        *lo = 0;
+        *hi = n[k] - 1;
+        return;
+    }
+    const double *M = p->cell + 9 * b, *o = p->origin + 3 * b;
+    double Mi[9], g[3];
+    inverse3(M, Mi);
+    column_norms(Mi, g);
+    double f = (x[0] - o[0]) * Mi[k] + (x[1] - o[1]) * Mi[3 + k] + (x[2] - o[2]) * Mi[6 + k];
+    /* The box cutoff reaches sqrt(3) r from the atom. */
+    double reach = (p->cutoff == PGO_BOX ? sqrt(3.0) : 1.0) * r * g[k];
+    long l = (long)floor((f - reach) * n[k] - 0.5) - 1;
+    long u = (long)ceil((f + reach) * n[k] - 0.5) + 1;
+    if (p->periodic) {
+        if (u - l + 1 > n[k]) u = l + n[k] - 1;
+    } else {
+        if (l < 0) l = 0;
+        if (u > n[k] - 1) u = n[k] - 1;
+    }
+    *lo = l;
+    *hi = u;
+}
+
 static long grid_index(const pgo_problem *p, long b, long c, long i, long j, long k)
 {
     return (((b * p->n_channels + c) * p->nx + i) * p->ny + j) * p->nz + k;
@@ -130,6 +267,7 @@ static int check(const pgo_problem *p)
     if (p->cutoff != PGO_SPHERE && p->cutoff != PGO_NONE && p->cutoff != PGO_BOX)
         return PGO_BAD_ARG;
     if (p->form != PGO_POINT && p->form != PGO_INTEGRAL) return PGO_BAD_ARG;
+    if (p->cell && p->form != PGO_POINT) return PGO_UNSUPPORTED;
     for (int b = 0; b < p->n_mol; ++b)
         for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a)
             if (p->elem[a] < 0 || p->elem[a] >= p->n_channels) return PGO_BAD_ELEM;
@@ -160,11 +298,16 @@ static void brute_molecule(const pgo_problem *p, int b, double *out)
                     double s = 0.0;
                     for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a) {
                         if (p->elem[a] != c) continue;
-                        double dx = disp(p, b, 0, i, p->coords[3 * a + 0]);
-                        double dy = disp(p, b, 1, j, p->coords[3 * a + 1]);
-                        double dz = disp(p, b, 2, k, p->coords[3 * a + 2]);
-                        if (inside(p->cutoff, dx, dy, dz, r))
-                            s += term(p, b, p->sigma[c], dx, dy, dz);
+                        double d[3];
+                        if (p->cell) {
+                            cell_disp(p, b, i, j, k, p->coords + 3 * a, d);
+                        } else {
+                            d[0] = disp(p, b, 0, i, p->coords[3 * a + 0]);
+                            d[1] = disp(p, b, 1, j, p->coords[3 * a + 1]);
+                            d[2] = disp(p, b, 2, k, p->coords[3 * a + 2]);
+                        }
+                        if (inside(p->cutoff, d[0], d[1], d[2], r))
+                            s += weight_of(p, a) * term(p, b, p->sigma[c], d[0], d[1], d[2]);
                     }
                     out[grid_index(p, b, c, i, j, k)] = s;
                 }
@@ -216,20 +359,37 @@ static void bbox_molecule(const pgo_problem *p, int b, double *out, double eps, 
     for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a) {
         int c = p->elem[a];
         double r = p->cutoff_k * p->sigma[c];
-        double x = p->coords[3 * a + 0], y = p->coords[3 * a + 1], z = p->coords[3 * a + 2];
+        double wa = weight_of(p, a);
+        const double *xa = p->coords + 3 * a;
+        double x = xa[0], y = xa[1], z = xa[2];
         long ilo, ihi, jlo, jhi, klo, khi;
-        support(p, b, 0, x, r, &ilo, &ihi);
-        support(p, b, 1, y, r, &jlo, &jhi);
-        support(p, b, 2, z, r, &klo, &khi);
+        if (p->cell) {
+            cell_support(p, b, 0, xa, r, &ilo, &ihi);
+            cell_support(p, b, 1, xa, r, &jlo, &jhi);
+            cell_support(p, b, 2, xa, r, &klo, &khi);
+        } else {
+            support(p, b, 0, x, r, &ilo, &ihi);
+            support(p, b, 1, y, r, &jlo, &jhi);
+            support(p, b, 2, z, r, &klo, &khi);
+        }
         for (long iu = ilo; iu <= ihi; ++iu) {
             long i = p->periodic ? wrap_index(iu, p->nx) : iu;
-            double dx = disp(p, b, 0, i, x);
+            double dx = p->cell ? 0.0 : disp(p, b, 0, i, x);
             for (long ju = jlo; ju <= jhi; ++ju) {
                 long j = p->periodic ? wrap_index(ju, p->ny) : ju;
-                double dy = disp(p, b, 1, j, y);
+                double dy = p->cell ? 0.0 : disp(p, b, 1, j, y);
                 for (long ku = klo; ku <= khi; ++ku) {
                     long k = p->periodic ? wrap_index(ku, p->nz) : ku;
-                    double dz = disp(p, b, 2, k, z);
+                    double dz;
+                    if (p->cell) {
+                        double d[3];
+                        cell_disp(p, b, i, j, k, xa, d);
+                        dx = d[0];
+                        dy = d[1];
+                        dz = d[2];
+                    } else {
+                        dz = disp(p, b, 2, k, z);
+                    }
                     double d2 = dx * dx + dy * dy + dz * dz;
                     long v = grid_index(p, b, c, i, j, k);
                     if (eps > 0.0 && p->cutoff != PGO_NONE) {
@@ -239,12 +399,12 @@ static void bbox_molecule(const pgo_problem *p, int b, double *out, double eps, 
                                         ? d2
                                         : fmax(dx * dx, fmax(dy * dy, dz * dz));
                         if (fabs(m2 - r * r) <= eps * r * r) {
-                            band[v] += term(p, b, p->sigma[c], dx, dy, dz);
+                            band[v] += wa * term(p, b, p->sigma[c], dx, dy, dz);
                             continue;
                         }
                     }
                     if (!inside(p->cutoff, dx, dy, dz, r)) continue;
-                    out[v] += term(p, b, p->sigma[c], dx, dy, dz);
+                    out[v] += wa * term(p, b, p->sigma[c], dx, dy, dz);
                 }
             }
         }
@@ -299,13 +459,14 @@ int pgo_voxelize_band(const pgo_problem *p, double eps, double *out_in, double *
  *   g_x[a][i] = [|d_x| <= r] exp(-d_x^2 / 2 sigma^2)  (the bracket is 1 with no cutoff),
  * or [|d_x| <= r] times the erf factor in the voxel-integrated form,
  * and G[c,i,j,k] = sum_{a: elem(a)=c} g_x[a][i] g_y[a][j] g_z[a][k].
- * The spherical indicator does not factor; that case is rejected.
+ * With weights, g_x of atom a is multiplied by w_a.  The spherical indicator does not
+ * factor, and neither does the metric of a general cell; those cases are rejected.
  */
 int pgo_separable(const pgo_problem *p, double *out, int n_threads)
 {
     int st = check(p);
     if (st) return st;
-    if (p->cutoff == PGO_SPHERE) return PGO_UNSUPPORTED;
+    if (p->cutoff == PGO_SPHERE || p->cell) return PGO_UNSUPPORTED;
     int nt = threads_or_default(n_threads);
     (void)nt;
     long per_mol = (long)p->n_channels * p->nx * p->ny * p->nz;
@@ -330,6 +491,7 @@ int pgo_separable(const pgo_problem *p, double *out, int n_threads)
                                    : exp(-d * d / s2);
                     g[ax][i] = keep ? f : 0.0;
                 }
+            for (long i = 0; i < p->nx; ++i) gx[i] *= weight_of(p, a);
             for (long i = 0; i < p->nx; ++i)
                 for (long j = 0; j < p->ny; ++j)
                     for (long k = 0; k < p->nz; ++k)
@@ -350,33 +512,51 @@ int pgo_separable(const pgo_problem *p, double *out, int n_threads)
  * mode 0 visits every voxel of the atom's channel, mode 1 only its cutoff box.
  * W has the grid layout [B][C][nx][ny][nz]; grad is [N][3].
  */
-/* Gradient for the atoms of molecule b (see pgo_gradient). */
+/*
+ * Gradient for the atoms of molecule b (see pgo_gradient); with grad_w non-null it also
+ * writes dL/dw_a, the atom's unweighted terms against W.
+ */
 static void gradient_molecule(const pgo_problem *p, int b, int mode, const double *W,
-                              double *grad)
+                              double *grad, double *grad_w)
 {
     for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a) {
         int c = p->elem[a];
         double sg2 = p->sigma[c] * p->sigma[c];
         double r = p->cutoff_k * p->sigma[c];
-        double x = p->coords[3 * a + 0], y = p->coords[3 * a + 1], z = p->coords[3 * a + 2];
+        const double *xa = p->coords + 3 * a;
+        double x = xa[0], y = xa[1], z = xa[2];
         long ilo = 0, ihi = p->nx - 1, jlo = 0, jhi = p->ny - 1, klo = 0, khi = p->nz - 1;
-        if (mode == 1) {
+        if (mode == 1 && p->cell) {
+            cell_support(p, b, 0, xa, r, &ilo, &ihi);
+            cell_support(p, b, 1, xa, r, &jlo, &jhi);
+            cell_support(p, b, 2, xa, r, &klo, &khi);
+        } else if (mode == 1) {
             support(p, b, 0, x, r, &ilo, &ihi);
             support(p, b, 1, y, r, &jlo, &jhi);
             support(p, b, 2, z, r, &klo, &khi);
         }
-        double gx = 0.0, gy = 0.0, gz = 0.0;
+        double gx = 0.0, gy = 0.0, gz = 0.0, gw = 0.0;
         for (long iu = ilo; iu <= ihi; ++iu) {
             long i = p->periodic ? wrap_index(iu, p->nx) : iu;
-            double dx = disp(p, b, 0, i, x);
+            double dx = p->cell ? 0.0 : disp(p, b, 0, i, x);
             for (long ju = jlo; ju <= jhi; ++ju) {
                 long j = p->periodic ? wrap_index(ju, p->ny) : ju;
-                double dy = disp(p, b, 1, j, y);
+                double dy = p->cell ? 0.0 : disp(p, b, 1, j, y);
                 for (long ku = klo; ku <= khi; ++ku) {
                     long k = p->periodic ? wrap_index(ku, p->nz) : ku;
-                    double dz = disp(p, b, 2, k, z);
+                    double dz;
+                    if (p->cell) {
+                        double d[3];
+                        cell_disp(p, b, i, j, k, xa, d);
+                        dx = d[0];
+                        dy = d[1];
+                        dz = d[2];
+                    } else {
+                        dz = disp(p, b, 2, k, z);
+                    }
                     if (!inside(p->cutoff, dx, dy, dz, r)) continue;
                     double Wv = W[grid_index(p, b, c, i, j, k)];
+                    gw += Wv * term(p, b, p->sigma[c], dx, dy, dz);
                     if (p->form == PGO_INTEGRAL) {
                         const double *h = p->spacing + 3 * b, sg = p->sigma[c];
                         double fx = erf_factor(dx, h[0], sg), fy = erf_factor(dy, h[1], sg);
@@ -393,10 +573,14 @@ static void gradient_molecule(const pgo_problem *p, int b, int mode, const doubl
                 }
             }
         }
-        /* The point form's common 1/sigma^2 is applied once at the end. */
-        grad[3 * a + 0] = p->form == PGO_INTEGRAL ? gx : gx / sg2;
-        grad[3 * a + 1] = p->form == PGO_INTEGRAL ? gy : gy / sg2;
-        grad[3 * a + 2] = p->form == PGO_INTEGRAL ? gz : gz / sg2;
+        /* The point form's common 1/sigma^2 and the weight are applied once at the end. */
+        double wa = weight_of(p, a);
+        if (grad) {
+            grad[3 * a + 0] = wa * (p->form == PGO_INTEGRAL ? gx : gx / sg2);
+            grad[3 * a + 1] = wa * (p->form == PGO_INTEGRAL ? gy : gy / sg2);
+            grad[3 * a + 2] = wa * (p->form == PGO_INTEGRAL ? gz : gz / sg2);
+        }
+        if (grad_w) grad_w[a] = gw;
     }
 }
 
@@ -407,7 +591,20 @@ int pgo_gradient(const pgo_problem *p, int mode, const double *W, double *grad, 
     int nt = threads_or_default(n_threads);
     (void)nt;
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
-    for (int b = 0; b < p->n_mol; ++b) gradient_molecule(p, b, mode, W, grad);
+    for (int b = 0; b < p->n_mol; ++b) gradient_molecule(p, b, mode, W, grad, NULL);
+    return PGO_OK;
+}
+
+/* Weight gradient dL/dw_a of L = <W, G> (weighted grids): grad_w is [N]. */
+int pgo_gradient_weight(const pgo_problem *p, int mode, const double *W, double *grad_w,
+                        int n_threads)
+{
+    int st = check(p);
+    if (st) return st;
+    int nt = threads_or_default(n_threads);
+    (void)nt;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nt)
+    for (int b = 0; b < p->n_mol; ++b) gradient_molecule(p, b, mode, W, NULL, grad_w);
     return PGO_OK;
 }
 
@@ -440,6 +637,7 @@ int pgo_refine(const pgo_problem *p, const double *target, int iters, double lr,
         q.mol_off = p->mol_off + b;
         q.origin = p->origin + 3 * b;
         q.spacing = p->spacing + 3 * b;
+        q.cell = p->cell ? p->cell + 9 * b : NULL;
         q.coords = out_coords;
         double *F = malloc(sizeof(double) * per_mol);
         double *W = malloc(sizeof(double) * per_mol);
@@ -456,7 +654,7 @@ int pgo_refine(const pgo_problem *p, const double *target, int iters, double lr,
                 W[v] = 2.0 * r;
             }
             if (L < eps || t == iters) break;
-            gradient_molecule(&q, 0, 1, W, g);
+            gradient_molecule(&q, 0, 1, W, g, NULL);
             for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a)
                 for (int ax = 0; ax < 3; ++ax) out_coords[3 * a + ax] -= lr * g[3 * a + ax];
             ++t;
@@ -490,16 +688,26 @@ int pgo_fd_gradient_frozen(const pgo_problem *p, const double *W, double step, d
         for (int a = p->mol_off[b]; a < p->mol_off[b + 1]; ++a) {
             int c = p->elem[a];
             double r = p->cutoff_k * p->sigma[c];
-            double x = p->coords[3 * a + 0], y = p->coords[3 * a + 1], z = p->coords[3 * a + 2];
+            const double *xa = p->coords + 3 * a;
+            double x = xa[0], y = xa[1], z = xa[2];
             double lp[3] = {0, 0, 0}, lm[3] = {0, 0, 0};
             for (long i = 0; i < p->nx; ++i) {
-                double dx = disp(p, b, 0, i, x);
+                double dx = p->cell ? 0.0 : disp(p, b, 0, i, x);
                 for (long j = 0; j < p->ny; ++j) {
-                    double dy = disp(p, b, 1, j, y);
+                    double dy = p->cell ? 0.0 : disp(p, b, 1, j, y);
                     for (long k = 0; k < p->nz; ++k) {
-                        double dz = disp(p, b, 2, k, z);
+                        double dz;
+                        if (p->cell) {
+                            double dv[3];
+                            cell_disp(p, b, i, j, k, xa, dv);
+                            dx = dv[0];
+                            dy = dv[1];
+                            dz = dv[2];
+                        } else {
+                            dz = disp(p, b, 2, k, z);
+                        }
                         if (!inside(p->cutoff, dx, dy, dz, r)) continue;
-                        double w = W[grid_index(p, b, c, i, j, k)];
+                        double w = W[grid_index(p, b, c, i, j, k)] * weight_of(p, a);
                         double d[3] = {dx, dy, dz};
                         for (int ax = 0; ax < 3; ++ax) {
                             double e[3] = {d[0], d[1], d[2]};

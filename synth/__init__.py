@@ -37,6 +37,9 @@ class Batch:
     mol_off int32   [B+1]   atoms of molecule b are rows mol_off[b] .. mol_off[b+1]-1
     origin  float32 [B, 3]  lower corner of molecule b's grid box
     spacing float32 [B, 3]  voxel edge lengths of molecule b's grid
+    weight  float32 [N]     optional per-atom weights (weighted grids); None means ones
+    cell    float32 [B,3,3] optional box edges a, b, c (rows) along the grid's x, y, z
+                            axes, replacing the axis-aligned box of `spacing`; None if unused
     """
 
     coords: np.ndarray
@@ -45,6 +48,8 @@ class Batch:
     origin: np.ndarray
     spacing: np.ndarray
     info: dict = field(default_factory=dict)
+    weight: np.ndarray | None = None
+    cell: np.ndarray | None = None
 
     @property
     def n_mol(self) -> int:
@@ -71,6 +76,10 @@ class Batch:
             mol_off=off,
             origin=np.ascontiguousarray(self.origin[idx], dtype=np.float32).reshape(-1, 3),
             spacing=np.ascontiguousarray(self.spacing[idx], dtype=np.float32).reshape(-1, 3),
+            weight=(None if self.weight is None else
+                    np.ascontiguousarray(cat(self.weight), dtype=np.float32)),
+            cell=(None if self.cell is None else
+                  np.ascontiguousarray(self.cell[idx], dtype=np.float32).reshape(-1, 3, 3)),
         )
 
 
