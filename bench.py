@@ -162,7 +162,8 @@ def write_probe_gbs(nbytes=4 << 30, reps=10):
 
 
 KERNEL_SOURCES = {"direct": ("direct_kernel.cuh",), "separable": ("pg_separable.cu",),
-                  "backward": ("pg_backward.cu",)}
+                  "backward": ("pg_backward.cu",), "cell": ("pg_cell.cu",)}
+CELL_WORKLOADS = ("crystal_shaped", "crystal_triclinic")
 
 
 def kernel_source_sha(kernel: str) -> str:
@@ -329,7 +330,7 @@ def run_ours(args):
 
     kw = {"shard": rank if world > 1 else None}
     if args.n_mol:
-        kw["n_cells" if args.workload == "crystal_shaped" else "n_mol"] = args.n_mol
+        kw["n_cells" if args.workload in CELL_WORKLOADS else "n_mol"] = args.n_mol
     wl = synth.workload(args.workload, **kw)
     dtype = args.dtype or wl.out_dtype
     if args.profile:
@@ -412,20 +413,23 @@ def run_ours(args):
     # End to end through the public API: pinned host inputs -> plan (graph: H2D + kernel)
     # -> device error word back to the host, every step.
     b = wl.batch
-    host = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-            for a in (b.coords, b.elem, b.mol_off, b.origin, b.spacing)]
-    h2d = sum(t.numel() * t.element_size() for t in host)
+    pin = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    host = [pin(a) for a in (b.coords, b.elem, b.mol_off, b.origin,
+                             None if b.cell is not None else b.spacing)]
+    extra = {"weight": pin(b.weight), "cell": pin(b.cell)}
+    h2d = sum(t.numel() * t.element_size() for t in host + list(extra.values())
+              if t is not None)
     plan = api.Plan(grid, dtype, max_mol=B, max_atoms=b.n_atoms, path=path)
     with torch.cuda.stream(stream):
         for _ in range(max(3, args.warmup)):
-            plan.run(*host, out=out)
+            plan.run(*host, out=out, **extra)
     e2e_steps = max(3, min(args.steps, 200))
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         for _ in range(e2e_steps):
-            plan.run(*host, out=out)
+            plan.run(*host, out=out, **extra)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if dist:
         t = torch.tensor([e2e_s], device="cuda")
@@ -444,7 +448,8 @@ def run_ours(args):
         return
 
     peak, peak_src = load_peaks()
-    kernel = "separable" if tuning.get("path") == 2 else "direct"
+    kernel = ("separable" if tuning.get("path") == 2
+              else "cell" if wl.batch.cell is not None else "direct")
     launch_ms = statistics.mean(per_step)
     achieved = out_bytes / (launch_ms / 1e3) / 1e9
     traffic = profiled_traffic(wl.name, kernel)
@@ -470,6 +475,8 @@ def run_ours(args):
             "batch_per_gpu": B,
             "grid": [wl.n_channels, wl.nx, wl.ny, wl.nz],
             "voxel_form": wl.form,
+            "cell_matrices": wl.batch.cell is not None,
+            "weighted": wl.batch.weight is not None,
             "out_dtype": dtype,
             "path": kernel,
             "tuning": tuning,
@@ -707,7 +714,7 @@ def main():
     ap.add_argument("--workload", default="qm9_shaped",
                     choices=["qm9_shaped", "plain_small", "precision_form",
                              "precision_form_integral", "crystal_shaped", "differentiation",
-                             "refinement", "pipeline_single_channel"])
+                             "refinement", "pipeline_single_channel", "crystal_triclinic"])
     ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default=None)
     ap.add_argument("--path", choices=["auto", "direct", "separable"], default="auto")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -24,6 +24,23 @@
  * the voxel centre when periodic); chi is still evaluated at the voxel centre.  Each atom
  * then adds exactly one to a grid that covers its support (the conservation law after Eq. 5).
  *
+ * Weighted grids (Sec. III-A, the remark that the gridding function extends to weighted
+ * grids): with per-atom weights w_a (pg_batch.weight) every term is multiplied by w_a.
+ *
+ * General cells (Sec. III-A: the box's orientation and size are the user's choice and
+ * voxels need not be cubic; crystals use the nearest image over lattice translations): a
+ * batch may give per molecule a 3x3 matrix M (pg_batch.cell) whose rows a, b, c are the box
+ * edges along which the grid's x, y and z indices run.  Voxel (i, j, k) then sits at
+ *     v = origin_b + ((i + 1/2) / nx) a + ((j + 1/2) / ny) b + ((k + 1/2) / nz) c,
+ * and spacing is not read.  For a periodic cell, d is the displacement to the nearest
+ * lattice image of the atom.  The kernels find it by rounding the fractional displacement
+ * (v - x) M^-1 per axis.  That is exact when the cutoff region reaches less than half a
+ * cell along every fractional axis: r_c |g_k| < 1/2 for the sphere and sqrt(3) r_c |g_k| <
+ * 1/2 for the box, with g_k column k of M^-1.  The device checks this and sets
+ * PG_DEVERR_PERIODIC where it fails.  Cells take the point form on the direct path.  The
+ * voxel-integrated form, the separable path and a periodic cell without a cutoff return
+ * PG_ERR_UNSUPPORTED.
+ *
  * General conventions
  *  - All buffers belong to the caller.  The library keeps only a small per-device error
  *    word, per-plan buffers (pg_plan_*) and an in-memory tuning cache; pg_shutdown()
@@ -50,7 +67,7 @@
 extern "C" {
 #endif
 
-#define PG_ABI_VERSION 1
+#define PG_ABI_VERSION 2
 #define PG_MAX_CHANNELS 64
 
 typedef enum {
@@ -78,8 +95,8 @@ typedef enum {
 /* Device-error bits reported by pg_sync_status() / pg_plan_run(). */
 #define PG_DEVERR_ELEMENT 0x1u   /* elem[a] outside [0, n_channels) */
 #define PG_DEVERR_OFFSETS 0x2u   /* mol_off not monotone, negative, or > n_atoms */
-#define PG_DEVERR_SPACING 0x4u   /* spacing <= 0 or not finite */
-#define PG_DEVERR_PERIODIC 0x8u  /* periodic cell with r_c >= L/2 on some axis */
+#define PG_DEVERR_SPACING 0x4u   /* spacing <= 0 or not finite, or a singular cell matrix */
+#define PG_DEVERR_PERIODIC 0x8u  /* periodic cell whose cutoff reaches half a cell or more */
 #define PG_DEVERR_TIMEOUT 0x10u  /* a bounded wait on tensor-core completion gave up */
 
 /*
@@ -91,7 +108,13 @@ typedef enum {
  *   mol_off  int32  [n_mol + 1]   atoms of molecule b are mol_off[b] .. mol_off[b+1]-1;
  *                                 mol_off[0] >= 0, non-decreasing, mol_off[n_mol] <= n_atoms
  *   origin   float  [n_mol][3]    lower corner of molecule b's grid box
- *   spacing  float  [n_mol][3]    voxel edges (h_x, h_y, h_z) of molecule b, > 0
+ *   spacing  float  [n_mol][3]    voxel edges (h_x, h_y, h_z) of molecule b, > 0; not read
+ *                                 (may be NULL) when `cell` is given
+ *   weight   float  [n_atoms]     optional per-atom weights (weighted grids); NULL = all 1
+ *   cell     float  [n_mol][3][3] optional box edges of molecule b, row-major, rows a, b, c
+ *                                 along the grid's x, y, z axes (non-singular); NULL = the
+ *                                 axis-aligned box of `spacing`
+ * A zero-initialised pg_batch leaves weight and cell NULL (ABI version 1 behaviour).
  */
 typedef struct {
     int32_t n_mol;
@@ -101,6 +124,8 @@ typedef struct {
     const int32_t *mol_off;
     const float *origin;
     const float *spacing;
+    const float *weight;
+    const float *cell;
 } pg_batch;
 
 /*
@@ -113,8 +138,10 @@ typedef struct {
  *                > 0; the paper's "variance" parameter, Sec. III-A / Sec. V)
  *   cutoff_k     r_c = cutoff_k * sigma_c (> 0; ignored for PG_CUTOFF_NONE)
  *   cutoff       pg_cutoff
- *   periodic     0: open boundaries; 1: orthorhombic cell of edges n*h with nearest-image
- *                distances (requires r_c < L/2 on every axis, checked on the device)
+ *   periodic     0: open boundaries; 1: periodic cell (edges n*h, or the batch's cell
+ *                matrix) with nearest-image distances (requires r_c < L/2 on every axis of
+ *                an axis-aligned cell, the reach condition above for a cell matrix; checked
+ *                on the device)
  *   voxel_form   pg_form (0 = point sample; zero-initialised grids keep the point form)
  */
 typedef struct {
@@ -196,6 +223,19 @@ pg_status pg_voxelize_backward(const pg_batch *batch, const pg_grid *grid, int32
                                const void *grad_out, float *grad_coords, void *stream);
 
 /*
+ * pg_voxelize_backward with the weight gradient of a weighted grid as well:
+ *     grad_weight[a] = sum_v grad_out[b][elem[a]][v] * (atom a's unweighted term at v),
+ * and grad_coords[a] as above (times w_a when batch->weight is given).
+ *   grad_coords  DEVICE float [n_atoms][3] or NULL (not computed)
+ *   grad_weight  DEVICE float [n_atoms] or NULL (not computed); atoms outside every
+ *                molecule get 0
+ * At least one of the two must be non-NULL when n_atoms > 0.
+ */
+pg_status pg_voxelize_backward_ex(const pg_batch *batch, const pg_grid *grid,
+                                  int32_t grad_dtype, const void *grad_out, float *grad_coords,
+                                  float *grad_weight, void *stream);
+
+/*
  * Grid reversal by gradient descent (Sec. IV-A steps 2-5, Sec. IV-C).  For each molecule,
  * from the coordinates in `coords`, repeat on the stream (no host synchronisation):
  *     F = grid of x (FP32, as pg_voxelize on the direct path);
@@ -203,8 +243,8 @@ pg_status pg_voxelize_backward(const pg_batch *batch, const pg_grid *grid, int32
  *     stop if L < eps;  otherwise  x <- x - lr * dL/dx,
  * with dL/dx = sum_v 2 (F - target) dF/dx, the adjoint of pg_voxelize_backward for the
  * upstream gradient 2 (F - target), for at most `iters` updates.
- *   batch    DEVICE CSR batch (elem, mol_off, origin, spacing, counts); batch->coords is not
- *            read, the coordinates come from `coords`
+ *   batch    DEVICE CSR batch (elem, mol_off, origin, spacing, optional weight and cell,
+ *            counts); batch->coords is not read, the coordinates come from `coords`
  *   target   DEVICE float[n_mol][C][nx][ny][nz]: the grid to reverse
  *   coords   DEVICE float[n_atoms][3]: starting coordinates, overwritten with the result
  *   work     DEVICE float workspace of pg_refine_work_floats(batch, grid) floats (the
@@ -252,7 +292,8 @@ pg_status pg_tuning_load(const char *file);
  * (the data-loader use of Sec. V / Sec. VI-D).
  *   pg_plan_create  capacity max_mol molecules / max_atoms atoms; grid and dtype fixed.
  *   pg_plan_run     batch holds HOST pointers (pinned memory is copied directly;
- *                   pageable memory is first packed into the plan's pinned staging);
+ *                   pageable memory is first packed into the plan's pinned staging),
+ *                   weight and cell included when given;
  *                   replays the graph on `stream`, writes `out` (DEVICE), then copies the
  *                   4-byte device error word back and synchronizes the stream.  Returns
  *                   PG_ERR_DEVICE_VALIDATION if it was set.  Not thread-safe per plan.

@@ -62,18 +62,26 @@ def _ptr(t):
 
 
 class DeviceBatch:
-    """CSR batch held in device tensors (float32 coords/origin/spacing, int32 ids/offsets)."""
+    """CSR batch held in device tensors (float32 coords/origin/spacing, int32 ids/offsets),
+    with optional per-atom weights (float32 [N]) and per-molecule cell matrices (float32
+    [B, 3, 3], rows = the box edges along the grid's x, y, z axes)."""
 
-    def __init__(self, coords, elem, mol_off, origin, spacing):
+    def __init__(self, coords, elem, mol_off, origin, spacing, weight=None, cell=None):
         self.coords = coords.reshape(-1, 3)
         self.elem = elem.reshape(-1)
         self.mol_off = mol_off.reshape(-1)
         self.origin = origin.reshape(-1, 3)
         self.spacing = spacing.reshape(-1, 3)
-        for name, t, dt in (("coords", self.coords, torch.float32), ("elem", self.elem, torch.int32),
-                            ("mol_off", self.mol_off, torch.int32),
-                            ("origin", self.origin, torch.float32),
-                            ("spacing", self.spacing, torch.float32)):
+        self.weight = None if weight is None else weight.reshape(-1)
+        self.cell = None if cell is None else cell.reshape(-1, 3, 3)
+        checks = [("coords", self.coords, torch.float32), ("elem", self.elem, torch.int32),
+                  ("mol_off", self.mol_off, torch.int32), ("origin", self.origin, torch.float32),
+                  ("spacing", self.spacing, torch.float32)]
+        if self.weight is not None:
+            checks.append(("weight", self.weight, torch.float32))
+        if self.cell is not None:
+            checks.append(("cell", self.cell, torch.float32))
+        for name, t, dt in checks:
             if t.dtype != dt:
                 raise TypeError(f"{name} must be {dt}, got {t.dtype}")
             if not t.is_cuda:
@@ -84,9 +92,13 @@ class DeviceBatch:
     @classmethod
     def from_numpy(cls, batch, device="cuda") -> "DeviceBatch":
         f = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a)).to(device=device, dtype=dt)
+        w = getattr(batch, "weight", None)
+        m = getattr(batch, "cell", None)
         return cls(f(batch.coords, torch.float32), f(batch.elem, torch.int32),
                    f(batch.mol_off, torch.int32), f(batch.origin, torch.float32),
-                   f(batch.spacing, torch.float32))
+                   f(batch.spacing, torch.float32),
+                   None if w is None else f(w, torch.float32),
+                   None if m is None else f(m, torch.float32))
 
     @property
     def n_mol(self) -> int:
@@ -100,7 +112,9 @@ class DeviceBatch:
         c = self.coords if coords is None else coords
         return B.pg_batch(n_mol=self.n_mol, n_atoms=self.n_atoms, coords=_ptr(c),
                           elem=_ptr(self.elem), mol_off=_ptr(self.mol_off),
-                          origin=_ptr(self.origin), spacing=_ptr(self.spacing))
+                          origin=_ptr(self.origin), spacing=_ptr(self.spacing),
+                          weight=None if self.weight is None else _ptr(self.weight),
+                          cell=None if self.cell is None else _ptr(self.cell))
 
 
 def _stream(stream=None) -> int:
@@ -143,6 +157,22 @@ def voxelize_backward(batch: DeviceBatch, grid: Grid, grad_out: torch.Tensor,
     B.check(B.pg_voxelize_backward(batch.to_c(coords), grid.to_c(), TORCH_TO_PG[grad_out.dtype],
                                    _ptr(grad_out), _ptr(grad_coords), _stream(stream)))
     return grad_coords
+
+
+def voxelize_backward_weights(batch: DeviceBatch, grid: Grid, grad_out: torch.Tensor,
+                              with_coords: bool = True, stream=None, coords=None):
+    """pg_voxelize_backward_ex: (dL/dx [N, 3] or None, dL/dw [N]) for upstream dL/dG."""
+    if grad_out.dtype not in TORCH_TO_PG:
+        raise TypeError(f"unsupported grad dtype {grad_out.dtype}")
+    grad_out = grad_out.contiguous()
+    dev = batch.coords.device
+    gc = torch.empty((batch.n_atoms, 3), dtype=torch.float32, device=dev) if with_coords else None
+    gw = torch.empty(batch.n_atoms, dtype=torch.float32, device=dev)
+    B.check(B.pg_voxelize_backward_ex(batch.to_c(coords), grid.to_c(),
+                                      TORCH_TO_PG[grad_out.dtype], _ptr(grad_out),
+                                      None if gc is None else _ptr(gc), _ptr(gw),
+                                      _stream(stream)))
+    return gc, gw
 
 
 def refine(batch: DeviceBatch, grid: Grid, target: torch.Tensor, coords: torch.Tensor,
@@ -203,9 +233,11 @@ class Plan:
         B.check(st)
         self._h = h
 
-    def run(self, coords, elem, mol_off, origin, spacing, out: torch.Tensor, stream=None):
-        """Host arrays (numpy or CPU tensors, pinned or pageable) -> `out` on the device.
-        Synchronous: returns after the device error word has been read back."""
+    def run(self, coords, elem, mol_off, origin, spacing, out: torch.Tensor, stream=None,
+            weight=None, cell=None):
+        """Host arrays (numpy or CPU tensors, pinned or pageable) -> `out` on the device;
+        `spacing` may be None when `cell` is given.  Synchronous: returns after the device
+        error word has been read back."""
         keep = []
 
         def host(a, dt):
@@ -219,9 +251,11 @@ class Plan:
 
         n_atoms = int(len(elem))
         n_mol = int(len(mol_off) - 1)
+        opt = lambda a: None if a is None else host(a, np.float32)
         hb = B.pg_batch(n_mol=n_mol, n_atoms=n_atoms, coords=host(coords, np.float32),
                         elem=host(elem, np.int32), mol_off=host(mol_off, np.int32),
-                        origin=host(origin, np.float32), spacing=host(spacing, np.float32))
+                        origin=host(origin, np.float32), spacing=opt(spacing),
+                        weight=opt(weight), cell=opt(cell))
         B.check(B.pg_plan_run(self._h, hb, _ptr(out), _stream(stream)))
         return out
 

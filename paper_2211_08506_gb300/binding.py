@@ -35,6 +35,7 @@ EXPORTED = (
     "pg_voxelize_backward", "pg_sync_status", "pg_autotune", "pg_get_tuning",
     "pg_tuning_save", "pg_tuning_load", "pg_plan_create", "pg_plan_run", "pg_plan_destroy",
     "pg_shutdown", "pg_voxelize_noalloc", "pg_refine", "pg_refine_work_floats",
+    "pg_voxelize_backward_ex",
 )
 
 
@@ -47,6 +48,8 @@ class pg_batch(ctypes.Structure):
         ("mol_off", ctypes.c_void_p),
         ("origin", ctypes.c_void_p),
         ("spacing", ctypes.c_void_p),
+        ("weight", ctypes.c_void_p),
+        ("cell", ctypes.c_void_p),
     ]
 
 
@@ -113,6 +116,7 @@ def load() -> ctypes.CDLL:
         lib.pg_voxelize.argtypes = [P(pg_batch), P(pg_grid), i32, vp, i32, vp]
         lib.pg_voxelize_tuned.argtypes = [P(pg_batch), P(pg_grid), i32, vp, P(pg_tuning), vp]
         lib.pg_voxelize_backward.argtypes = [P(pg_batch), P(pg_grid), i32, vp, vp, vp]
+        lib.pg_voxelize_backward_ex.argtypes = [P(pg_batch), P(pg_grid), i32, vp, vp, vp, vp]
         lib.pg_sync_status.argtypes = [vp, P(ctypes.c_uint32)]
         lib.pg_autotune.argtypes = [P(pg_batch), P(pg_grid), i32, vp, i32, vp, P(pg_tuning)]
         lib.pg_get_tuning.argtypes = [P(pg_batch), P(pg_grid), i32, i32, P(pg_tuning)]
@@ -175,6 +179,12 @@ def pg_voxelize_tuned(batch, grid, out_dtype, out, tuning, stream):
 def pg_voxelize_backward(batch, grid, grad_dtype, grad_out, grad_coords, stream):
     return load().pg_voxelize_backward(ctypes.byref(batch), ctypes.byref(grid), grad_dtype,
                                        grad_out, grad_coords, stream)
+
+
+def pg_voxelize_backward_ex(batch, grid, grad_dtype, grad_out, grad_coords, grad_weight,
+                            stream):
+    return load().pg_voxelize_backward_ex(ctypes.byref(batch), ctypes.byref(grid), grad_dtype,
+                                          grad_out, grad_coords, grad_weight, stream)
 
 
 def pg_refine(batch, grid, target, coords, work, loss, steps, iters, lr, eps, stream):

@@ -133,24 +133,24 @@ __device__ __forceinline__ float row_factor(float fx, float dy, float dx2, float
 }
 
 // Per-lane accumulation of one atom's contribution into the lane's VEC voxels: each term is
-// the product of the atom's row factor and the voxel's z factor, under the exact per-voxel
-// cutoff test for a sphere.
+// the product of the atom's row factor (times its weight w, exactly 1 for unweighted grids)
+// and the voxel's z factor, under the exact per-voxel cutoff test for a sphere.
 template <int VEC, int CUT, bool PER, int FORM>
 struct LaneVoxels {
     float vy;        // voxel-centre y of the lane's row
     float vz[VEC];   // voxel-centre z of the lane's voxels
     float acc[VEC];
 
-    __device__ __forceinline__ void add(float dx, float ay, float az, float q, float r2, float kf,
-                                        float hx, float hy, float hz, float Ly, float iLy,
-                                        float Lz, float iLz)
+    __device__ __forceinline__ void add(float dx, float ay, float az, float w, float q, float r2,
+                                        float kf, float hx, float hy, float hz, float Ly,
+                                        float iLy, float Lz, float iLz)
     {
         float dy = vy - ay;
         if (PER) dy = wrap(dy, Ly, iLy);
         const float dx2 = dx * dx;
         const float dxy2 = fmaf(dy, dy, dx2);
         const float fx = FORM ? erf_axis(dx, hx, kf) : 0.0f;
-        const float exy = row_factor<CUT, FORM>(fx, dy, dx2, dxy2, q, r2, kf, hy);
+        const float exy = w * row_factor<CUT, FORM>(fx, dy, dx2, dxy2, q, r2, kf, hy);
 #pragma unroll
         for (int k = 0; k < VEC; ++k) {
             float dz = vz[k] - az;
@@ -209,9 +209,9 @@ __device__ __forceinline__ void store_lane(T *out, int v, const float (&acc)[VEC
 // from group to group: with lpr = nz / VEC lanes per row, lane l < act = rpg * lpr owns the
 // columns z0 .. z0 + VEC - 1 of rows y0 + l / lpr and y0 + l / lpr + rpg of each pass of
 // 2 * rpg rows.  Each surviving atom's z factors are computed once per pass and shared by both
-// rows.  for_each(cy, wy, cz, wz, f) calls f(dx, ay, az) for the candidates that can reach
-// the pass's box of voxel centres, in atom order.  Every voxel adds the same terms in the same
-// order as LaneVoxels::add does (atoms culled for one of the two rows add exact zeros or are
+// rows.  for_each(cy, wy, cz, wz, f) calls f(dx, ay, az, w), w the atom's weight, for the
+// candidates that can reach the pass's box of voxel centres, in atom order.  Every voxel adds
+// the same terms in the same order as LaneVoxels::add does (atoms culled for one of the two rows add exact zeros or are
 // skipped by the same test), so both give identical bits.
 template <typename T, int VEC, int CUT, bool PER, int HINT, int FORM, typename ForEach>
 __device__ __forceinline__ void blocked_plane(T *out, int ny, int nz, int rpg, int act,
@@ -235,7 +235,7 @@ __device__ __forceinline__ void blocked_plane(T *out, int ny, int nz, int rpg, i
         float acc0[VEC], acc1[VEC];
 #pragma unroll
         for (int k = 0; k < VEC; ++k) acc0[k] = acc1[k] = 0.0f;
-        for_each(cy, wy, cz, wz, [&](float dx, float ay, float az) {
+        for_each(cy, wy, cz, wz, [&](float dx, float ay, float az, float w) {
             const float dx2 = dx * dx;
             float dya = vya - ay, dyb = vyb - ay;
             if (PER) {
@@ -244,8 +244,8 @@ __device__ __forceinline__ void blocked_plane(T *out, int ny, int nz, int rpg, i
             }
             const float dxya = fmaf(dya, dya, dx2), dxyb = fmaf(dyb, dyb, dx2);
             const float fx = FORM ? erf_axis(dx, hx, kf) : 0.0f;
-            const float ea = row_factor<CUT, FORM>(fx, dya, dx2, dxya, q, r2, kf, hy);
-            const float eb = row_factor<CUT, FORM>(fx, dyb, dx2, dxyb, q, r2, kf, hy);
+            const float ea = w * row_factor<CUT, FORM>(fx, dya, dx2, dxya, q, r2, kf, hy);
+            const float eb = w * row_factor<CUT, FORM>(fx, dyb, dx2, dxyb, q, r2, kf, hy);
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
                 float dz = vz[k] - az;
@@ -480,7 +480,7 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
     float Lx = 1.f, Ly = 1.f, Lz = 1.f, iLx = 1.f, iLy = 1.f, iLz = 1.f;
     bool small = true;
     // Lane-held atom of a small molecule (lane < a1 - a0).
-    float my_x = 0.f, my_y = 0.f, my_z = 0.f;
+    float my_x = 0.f, my_y = 0.f, my_z = 0.f, my_w = 1.f;
     int my_e = -1;
 
     while (true) {
@@ -525,6 +525,7 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
             if (small && a0 + lane < a1) {
                 const int ai = a0 + lane;
                 my_e = __ldg(A.in.elem + ai);
+                my_w = A.in.weight ? __ldg(A.in.weight + ai) : 1.0f;
                 my_x = __ldg(A.in.coords + 3 * ai);
                 my_y = __ldg(A.in.coords + 3 * ai + 1);
                 my_z = __ldg(A.in.coords + 3 * ai + 2);
@@ -543,14 +544,16 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
             // 64 atoms per step, all loads issued before any is used.
             for (int base = a0; base < a1; base += 64) {
                 int e[2];
-                float ax[2], ay[2], az[2];
+                float ax[2], ay[2], az[2], aw[2];
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int ai = base + 32 * h + lane;
                     e[h] = -1;
                     ax[h] = ay[h] = az[h] = 0.0f;
+                    aw[h] = 1.0f;
                     if (ai < a1) {
                         e[h] = __ldg(A.in.elem + ai);
+                        if (A.in.weight) aw[h] = __ldg(A.in.weight + ai);
                         ax[h] = __ldg(A.in.coords + 3 * ai);
                         ay[h] = __ldg(A.in.coords + 3 * ai + 1);
                         az[h] = __ldg(A.in.coords + 3 * ai + 2);
@@ -564,7 +567,7 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                     const unsigned m = __ballot_sync(0xffffffffu, ok);
                     if (ok) {
                         const int pos = cnt + __popc(m & lt_mask);
-                        if (pos < kChanCap) chan[pos] = make_float4(ax[h], ay[h], az[h], 0.0f);
+                        if (pos < kChanCap) chan[pos] = make_float4(ax[h], ay[h], az[h], aw[h]);
                     }
                     cnt += __popc(m);
                 }
@@ -602,7 +605,8 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                                 m &= m - 1;
                                 f(__shfl_sync(0xffffffffu, dx, src),
                                   __shfl_sync(0xffffffffu, my_y, src),
-                                  __shfl_sync(0xffffffffu, my_z, src));
+                                  __shfl_sync(0xffffffffu, my_z, src),
+                                  __shfl_sync(0xffffffffu, my_w, src));
                             }
                         });
                 } else {
@@ -637,7 +641,9 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                                 const float sdx = __shfl_sync(0xffffffffu, dx, src);
                                 const float sy = __shfl_sync(0xffffffffu, my_y, src);
                                 const float sz = __shfl_sync(0xffffffffu, my_z, src);
-                                lv.add(sdx, sy, sz, q, r2, kf, hx, hy, hz, Ly, iLy, Lz, iLz);
+                                const float sw = __shfl_sync(0xffffffffu, my_w, src);
+                                lv.add(sdx, sy, sz, sw, q, r2, kf, hx, hy, hz, Ly, iLy, Lz,
+                                       iLz);
                             }
                         }
                         if (g + lane < nvec) store_lane<T, VEC, HINT>(out, g + lane, lv.acc);
@@ -656,26 +662,28 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                 for (int cb = 0; cb < n_chan; cb += 32) {
                     const int j = cb + lane;
                     bool ok = false;
-                    float dx = 0.0f, ay = 0.0f, az = 0.0f;
+                    float dx = 0.0f, ay = 0.0f, az = 0.0f, aw = 1.0f;
                     if (j < n_chan) {
                         const float4 a = chan[j];
                         ay = a.y;
                         az = a.z;
+                        aw = a.w;
                         dx = vx - a.x;
                         if (PER) dx = wrap(dx, Lx, iLx);
                         ok = (CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc);
                     }
                     const unsigned m = __ballot_sync(0xffffffffu, ok);
-                    if (ok) stage[count + __popc(m & lt_mask)] = make_float4(dx, ay, az, 0.0f);
+                    if (ok) stage[count + __popc(m & lt_mask)] = make_float4(dx, ay, az, aw);
                     count += __popc(m);
                 }
                 for (int base = n_chan >= 0 ? a1 : a0; base < a1; base += 32) {
                     const int ai = base + lane;
                     bool ok = false;
-                    float dx = 0.0f, ay = 0.0f, az = 0.0f;
+                    float dx = 0.0f, ay = 0.0f, az = 0.0f, aw = 1.0f;
                     if (ai < a1) {
                         // Loads issued together, used after.
                         const int e = __ldg(A.in.elem + ai);
+                        if (A.in.weight) aw = __ldg(A.in.weight + ai);
                         const float ax = __ldg(A.in.coords + 3 * ai);
                         ay = __ldg(A.in.coords + 3 * ai + 1);
                         az = __ldg(A.in.coords + 3 * ai + 2);
@@ -690,7 +698,7 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                     const unsigned m = __ballot_sync(0xffffffffu, ok);
                     if (ok) {
                         const int pos = count + __popc(m & lt_mask);
-                        if (pos < kStageCap) stage[pos] = make_float4(dx, ay, az, 0.0f);
+                        if (pos < kStageCap) stage[pos] = make_float4(dx, ay, az, aw);
                     }
                     count += __popc(m);
                 }
@@ -718,7 +726,7 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                                     const int src = __ffs(m) - 1;
                                     m &= m - 1;
                                     const float4 st = stage[cb + src];
-                                    f(st.x, st.y, st.z);
+                                    f(st.x, st.y, st.z, st.w);
                                 }
                             }
                         });
@@ -759,7 +767,8 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                                     const int src = __ffs(m) - 1;
                                     m &= m - 1;
                                     const float4 st = stage[cb + src];
-                                    lv.add(st.x, st.y, st.z, q, r2, kf, hx, hy, hz, Ly, iLy, Lz, iLz);
+                                    lv.add(st.x, st.y, st.z, st.w, q, r2, kf, hx, hy, hz, Ly, iLy,
+                                           Lz, iLz);
                                 }
                             }
                         } else {
@@ -767,8 +776,9 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                             for (int base = a0; base < a1; base += 32) {
                                 const int ai = base + lane;
                                 bool ok = false;
-                                float dx = 0.0f, ay = 0.0f, az = 0.0f;
+                                float dx = 0.0f, ay = 0.0f, az = 0.0f, aw = 1.0f;
                                 if (ai < a1 && __ldg(A.in.elem + ai) == c) {
+                                    if (A.in.weight) aw = __ldg(A.in.weight + ai);
                                     const float ax = __ldg(A.in.coords + 3 * ai);
                                     ay = __ldg(A.in.coords + 3 * ai + 1);
                                     az = __ldg(A.in.coords + 3 * ai + 2);
@@ -785,7 +795,9 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                                     const float sdx = __shfl_sync(0xffffffffu, dx, src);
                                     const float sy = __shfl_sync(0xffffffffu, ay, src);
                                     const float sz = __shfl_sync(0xffffffffu, az, src);
-                                    lv.add(sdx, sy, sz, q, r2, kf, hx, hy, hz, Ly, iLy, Lz, iLz);
+                                    const float sw = __shfl_sync(0xffffffffu, aw, src);
+                                    lv.add(sdx, sy, sz, sw, q, r2, kf, hx, hy, hz, Ly, iLy, Lz,
+                                           iLz);
                                 }
                             }
                         }

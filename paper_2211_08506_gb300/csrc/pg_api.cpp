@@ -109,8 +109,9 @@ pg_status validate(const pg_batch *b, const pg_grid *g)
     if (b->n_mol < 0 || b->n_atoms < 0)
         return fail(PG_ERR_INVALID_ARG, "negative n_mol (%d) or n_atoms (%d)", b->n_mol,
                     b->n_atoms);
-    if (b->n_mol > 0 && (!b->mol_off || !b->origin || !b->spacing))
-        return fail(PG_ERR_INVALID_ARG, "mol_off, origin and spacing are required when n_mol > 0");
+    if (b->n_mol > 0 && (!b->mol_off || !b->origin || (!b->spacing && !b->cell)))
+        return fail(PG_ERR_INVALID_ARG,
+                    "mol_off, origin and spacing (or cell) are required when n_mol > 0");
     if (b->n_atoms > 0 && (!b->coords || !b->elem))
         return fail(PG_ERR_INVALID_ARG, "coords and elem are required when n_atoms > 0");
     if (g->nx < 1 || g->ny < 1 || g->nz < 1)
@@ -132,6 +133,13 @@ pg_status validate(const pg_batch *b, const pg_grid *g)
         return fail(PG_ERR_INVALID_ARG, "periodic must be 0 or 1");
     if (g->voxel_form != PG_FORM_POINT && g->voxel_form != PG_FORM_INTEGRAL)
         return fail(PG_ERR_INVALID_ARG, "unknown voxel_form %d", g->voxel_form);
+    if (b->cell && g->voxel_form != PG_FORM_POINT)
+        return fail(PG_ERR_UNSUPPORTED, "the voxel-integrated form needs an axis-aligned box "
+                                        "(cell must be NULL)");
+    if (b->cell && g->periodic && g->cutoff == PG_CUTOFF_NONE)
+        return fail(PG_ERR_UNSUPPORTED, "a periodic cell matrix needs a cutoff (SPHERE or BOX): "
+                                        "without one the nearest image is not found by "
+                                        "rounding");
     const long long plane = (long long)g->ny * g->nz;
     if (plane > INT32_MAX || (long long)g->nx * plane > INT32_MAX)
         return fail(PG_ERR_INVALID_ARG, "one channel grid must hold fewer than 2^31 voxels");
@@ -181,7 +189,7 @@ void make_geometry(const pg_batch *b, const pg_grid *g, Geometry *G)
 
 Inputs make_inputs(const pg_batch *b)
 {
-    return Inputs{b->coords, b->elem, b->mol_off, b->origin, b->spacing};
+    return Inputs{b->coords, b->elem, b->mol_off, b->origin, b->spacing, b->weight, b->cell};
 }
 
 pg_tuning default_tuning(int path)
@@ -212,8 +220,9 @@ int direct_plane_stride(const pg_grid *g)
 // whose mean is that small keeps the gather-only instantiation and its higher occupancy.
 bool direct_scatter_on(const pg_batch *b, const pg_grid *g, const pg_tuning &t)
 {
-    return !t.gather_only && g->voxel_form == PG_FORM_POINT && direct_plane_stride(g) > 0 &&
-           b->n_atoms > 32LL * b->n_mol;
+    // The fixed-point accumulator is scaled for unit terms: weighted grids gather in float.
+    return !t.gather_only && g->voxel_form == PG_FORM_POINT && !b->weight && !b->cell &&
+           direct_plane_stride(g) > 0 && b->n_atoms > 32LL * b->n_mol;
 }
 
 bool vec_stores_ok(const void *out, const pg_grid *g, int dtype)
@@ -229,6 +238,9 @@ pg_status plan_forward(const pg_batch *b, const pg_grid *g, int dtype, void *out
     Geometry G;
     make_geometry(b, g, &G);
     if (t.path == PG_PATH_SEPARABLE) {
+        if (b->cell)
+            return fail(PG_ERR_UNSUPPORTED, "the separable path needs an axis-aligned box; a "
+                                            "cell matrix's metric does not factor per axis");
         if (g->cutoff == PG_CUTOFF_SPHERE)
             return fail(PG_ERR_UNSUPPORTED,
                         "the separable path needs a separable cutoff (NONE or BOX); the "
@@ -257,7 +269,14 @@ pg_status plan_forward(const pg_batch *b, const pg_grid *g, int dtype, void *out
     a.plane_stride = direct_scatter_on(b, g, t) ? direct_plane_stride(g) : 0;
     a.chunk_planes = (t.chunk_planes >= 1 && t.chunk_planes <= 64) ? t.chunk_planes : 8;
     a.geo = G;
-    cudaError_t e = direct_plan(a, dtype, vec_stores_ok(out, g, dtype) ? 1 : 0, t, d.sms, kl);
+    const int vec = vec_stores_ok(out, g, dtype) ? 1 : 0;
+    if (b->cell) {
+        a.plane_stride = 0;
+        cudaError_t e = cell_plan(a, dtype, vec, t, d.sms, kl);
+        if (e != cudaSuccess) return cuda_fail(e, "cell_plan");
+        return PG_OK;
+    }
+    cudaError_t e = direct_plan(a, dtype, vec, t, d.sms, kl);
     if (e != cudaSuccess) return cuda_fail(e, "direct_plan");
     return PG_OK;
 }
@@ -293,9 +312,10 @@ std::string bucket_key(const pg_batch *b, const pg_grid *g, int dtype, int path,
     const double apm = b->n_mol > 0 ? (double)b->n_atoms / b->n_mol : 0.0;
     const int bucket = apm >= 1.0 ? (int)std::floor(std::log2(apm)) : 0;
     char buf[256];
-    snprintf(buf, sizeof buf, "%s|%dx%dx%d|C%d|dt%d|cut%d|per%d|apm%d|path%d%s", d.name.c_str(),
-             g->nx, g->ny, g->nz, g->n_channels, dtype, g->cutoff, g->periodic, bucket, path,
-             g->voxel_form == PG_FORM_INTEGRAL ? "|form1" : "");
+    snprintf(buf, sizeof buf, "%s|%dx%dx%d|C%d|dt%d|cut%d|per%d|apm%d|path%d%s%s%s",
+             d.name.c_str(), g->nx, g->ny, g->nz, g->n_channels, dtype, g->cutoff, g->periodic,
+             bucket, path, g->voxel_form == PG_FORM_INTEGRAL ? "|form1" : "",
+             b->cell ? "|cell" : "", b->weight ? "|wgt" : "");
     return buf;
 }
 
@@ -321,6 +341,9 @@ bool is_pinned(const void *p)
 
 }  // namespace
 
+// Host-to-device copies of a plan run: coords, elem, mol_off, origin, spacing, weight, cell.
+constexpr int kPlanCopies = 7;
+
 struct pg_plan {
     int device = -1;
     pg_grid grid;
@@ -333,18 +356,21 @@ struct pg_plan {
     int *d_moloff = nullptr;
     float *d_origin = nullptr;
     float *d_spacing = nullptr;
+    float *d_weight = nullptr;
+    float *d_cell = nullptr;
     unsigned *d_err = nullptr;
     unsigned long long *d_sched = nullptr;
     unsigned char *h_stage = nullptr;
-    size_t stage_off[5] = {0, 0, 0, 0, 0};
+    size_t stage_off[kPlanCopies] = {};
     unsigned *h_err = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t n_memset = nullptr, n_copy[5] = {}, n_kernel = nullptr, n_errcopy = nullptr;
+    cudaGraphNode_t n_memset = nullptr, n_copy[kPlanCopies] = {}, n_kernel = nullptr,
+                    n_errcopy = nullptr;
     const void *kernel_func = nullptr;
     // What the executable graph currently holds, so that an unchanged run skips the update.
-    const void *cur_src[5] = {};
-    size_t cur_cnt[5] = {};
+    const void *cur_src[kPlanCopies] = {};
+    size_t cur_cnt[kPlanCopies] = {};
     KernelLaunch cur_kl;
     bool cur_valid = false;
 };
@@ -360,6 +386,8 @@ void plan_free(pg_plan *p)
     cudaFree(p->d_moloff);
     cudaFree(p->d_origin);
     cudaFree(p->d_spacing);
+    cudaFree(p->d_weight);
+    cudaFree(p->d_cell);
     cudaFree(p->d_err);
     cudaFree(p->d_sched);
     if (p->h_stage) cudaFreeHost(p->h_stage);
@@ -367,8 +395,8 @@ void plan_free(pg_plan *p)
     delete p;
 }
 
-pg_status plan_build_graph(pg_plan *p, const void *const src[5], const size_t bytes[5],
-                           void *const dst[5], KernelLaunch &kl)
+pg_status plan_build_graph(pg_plan *p, const void *const src[kPlanCopies], const size_t bytes[kPlanCopies],
+                           void *const dst[kPlanCopies], KernelLaunch &kl)
 {
     if (p->exec) {
         cudaGraphExecDestroy(p->exec);
@@ -388,9 +416,9 @@ pg_status plan_build_graph(pg_plan *p, const void *const src[5], const size_t by
     ms.height = 1;
     ms.pitch = sizeof(unsigned);
     PG_CUDA(cudaGraphAddMemsetNode(&p->n_memset, p->graph, nullptr, 0, &ms), "add memset node");
-    cudaGraphNode_t deps[6];
+    cudaGraphNode_t deps[kPlanCopies + 1];
     deps[0] = p->n_memset;
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < kPlanCopies; ++i) {
         PG_CUDA(cudaGraphAddMemcpyNode1D(&p->n_copy[i], p->graph, nullptr, 0, dst[i], src[i],
                                          bytes[i], cudaMemcpyHostToDevice),
                 "add H2D node");
@@ -404,7 +432,8 @@ pg_status plan_build_graph(pg_plan *p, const void *const src[5], const size_t by
     kp.blockDim = kl.block;
     kp.sharedMemBytes = (unsigned)kl.smem;
     kp.kernelParams = kl.params;
-    PG_CUDA(cudaGraphAddKernelNode(&p->n_kernel, p->graph, deps, 6, &kp), "add kernel node");
+    PG_CUDA(cudaGraphAddKernelNode(&p->n_kernel, p->graph, deps, kPlanCopies + 1, &kp),
+            "add kernel node");
     PG_CUDA(cudaGraphAddMemcpyNode1D(&p->n_errcopy, p->graph, &p->n_kernel, 1, p->h_err,
                                      p->d_err, sizeof(unsigned), cudaMemcpyDeviceToHost),
             "add D2H node");
@@ -421,22 +450,22 @@ bool same_launch(const KernelLaunch &a, const KernelLaunch &b)
            std::memcmp(a.args, b.args, a.args_size) == 0;
 }
 
-pg_status plan_update_graph_nodes(pg_plan *p, const void *const src[5], const size_t bytes[5],
-                                  void *const dst[5], KernelLaunch &kl);
+pg_status plan_update_graph_nodes(pg_plan *p, const void *const src[kPlanCopies], const size_t bytes[kPlanCopies],
+                                  void *const dst[kPlanCopies], KernelLaunch &kl);
 
 // Bring the executable graph in line with this run; nothing to do when the copies and the
 // launch are those of the previous run.
-pg_status plan_update_graph(pg_plan *p, const void *const src[5], const size_t bytes[5],
-                            void *const dst[5], KernelLaunch &kl)
+pg_status plan_update_graph(pg_plan *p, const void *const src[kPlanCopies], const size_t bytes[kPlanCopies],
+                            void *const dst[kPlanCopies], KernelLaunch &kl)
 {
     bool same = p->exec && p->cur_valid && same_launch(kl, p->cur_kl);
-    for (int i = 0; same && i < 5; ++i)
+    for (int i = 0; same && i < kPlanCopies; ++i)
         same = src[i] == p->cur_src[i] && bytes[i] == p->cur_cnt[i];
     if (same) return PG_OK;
     pg_status st = plan_update_graph_nodes(p, src, bytes, dst, kl);
     p->cur_valid = st == PG_OK;
     if (st == PG_OK) {
-        for (int i = 0; i < 5; ++i) {
+        for (int i = 0; i < kPlanCopies; ++i) {
             p->cur_src[i] = src[i];
             p->cur_cnt[i] = bytes[i];
         }
@@ -445,11 +474,11 @@ pg_status plan_update_graph(pg_plan *p, const void *const src[5], const size_t b
     return st;
 }
 
-pg_status plan_update_graph_nodes(pg_plan *p, const void *const src[5], const size_t bytes[5],
-                                  void *const dst[5], KernelLaunch &kl)
+pg_status plan_update_graph_nodes(pg_plan *p, const void *const src[kPlanCopies], const size_t bytes[kPlanCopies],
+                                  void *const dst[kPlanCopies], KernelLaunch &kl)
 {
     if (!p->exec || kl.func != p->kernel_func) return plan_build_graph(p, src, bytes, dst, kl);
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < kPlanCopies; ++i) {
         if (cudaGraphExecMemcpyNodeSetParams1D(p->exec, p->n_copy[i], dst[i], src[i], bytes[i],
                                                cudaMemcpyHostToDevice) != cudaSuccess) {
             (void)cudaGetLastError();
@@ -531,7 +560,9 @@ pg_status direct_launch_with_scratch(const pg_batch *b, const pg_grid *g, int dt
     a.plane_stride = direct_scatter_on(b, g, t) ? direct_plane_stride(g) : 0;
     a.chunk_planes = 8;
     make_geometry(b, g, &a.geo);
-    cudaError_t e = direct_plan(a, dtype, vec_stores_ok(out, g, dtype) ? 1 : 0, t, sm_count, kl);
+    const int vec = vec_stores_ok(out, g, dtype) ? 1 : 0;
+    cudaError_t e = b->cell ? cell_plan(a, dtype, vec, t, sm_count, kl)
+                            : direct_plan(a, dtype, vec, t, sm_count, kl);
     if (e != cudaSuccess) return cuda_fail(e, "direct_plan");
     return PG_OK;
 }
@@ -576,7 +607,8 @@ pg_status pg_voxelize(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
     Device *d = nullptr;
     if ((st = get_device(&d))) return st;
     pg_tuning t = resolve(batch, grid, out_dtype, path, *d);
-    if (path == PG_PATH_AUTO && t.path == PG_PATH_SEPARABLE && grid->cutoff == PG_CUTOFF_SPHERE)
+    if (path == PG_PATH_AUTO && t.path == PG_PATH_SEPARABLE &&
+        (grid->cutoff == PG_CUTOFF_SPHERE || batch->cell))
         t = default_tuning(PG_PATH_DIRECT);
     return forward(batch, grid, out_dtype, out, t, (cudaStream_t)stream);
 }
@@ -585,15 +617,27 @@ pg_status pg_voxelize_backward(const pg_batch *batch, const pg_grid *grid, int32
                                const void *grad_out, float *grad_coords, void *stream)
 {
     t_last_error.clear();
+    if (batch && batch->n_atoms > 0 && !grad_coords)
+        return fail(PG_ERR_INVALID_ARG, "grad_coords must not be NULL");
+    return pg_voxelize_backward_ex(batch, grid, grad_dtype, grad_out, grad_coords, nullptr,
+                                   stream);
+}
+
+pg_status pg_voxelize_backward_ex(const pg_batch *batch, const pg_grid *grid,
+                                  int32_t grad_dtype, const void *grad_out, float *grad_coords,
+                                  float *grad_weight, void *stream)
+{
+    t_last_error.clear();
     pg_status st = validate(batch, grid);
     if (st) return st;
     if ((st = check_dtype(grad_dtype))) return st;
     if (batch->n_mol > 0 && !grad_out)
         return fail(PG_ERR_INVALID_ARG, "grad_out must not be NULL");
-    if (batch->n_atoms > 0 && !grad_coords)
-        return fail(PG_ERR_INVALID_ARG, "grad_coords must not be NULL");
-    if ((uintptr_t)grad_out % dtype_size(grad_dtype) != 0 || (uintptr_t)grad_coords % 4 != 0)
-        return fail(PG_ERR_INVALID_ARG, "grad_out / grad_coords misaligned");
+    if (batch->n_atoms > 0 && !grad_coords && !grad_weight)
+        return fail(PG_ERR_INVALID_ARG, "grad_coords and grad_weight must not both be NULL");
+    if ((uintptr_t)grad_out % dtype_size(grad_dtype) != 0 || (uintptr_t)grad_coords % 4 != 0 ||
+        (uintptr_t)grad_weight % 4 != 0)
+        return fail(PG_ERR_INVALID_ARG, "grad_out / grad_coords / grad_weight misaligned");
     Device *d = nullptr;
     if ((st = get_device(&d))) return st;
     if (batch->n_atoms == 0) return PG_OK;
@@ -602,11 +646,15 @@ pg_status pg_voxelize_backward(const pg_batch *batch, const pg_grid *grid, int32
     a.in = make_inputs(batch);
     a.grad_out = grad_out;
     a.grad_coords = grad_coords;
+    a.grad_weight = grad_weight;
     a.err = d->err;
     a.sched = d->take_slot();
     make_geometry(batch, grid, &a.geo);
     KernelLaunch kl;
-    PG_CUDA(backward_plan(a, grad_dtype, d->sms, &kl), "backward_plan");
+    cudaError_t be = backward_plan(a, grad_dtype, d->sms, &kl);
+    if (be == cudaErrorNotSupported)
+        return fail(PG_ERR_UNSUPPORTED, "the adjoint does not cover this cell/cutoff");
+    PG_CUDA(be, "backward_plan");
     PG_CUDA(launch(kl, (cudaStream_t)stream), "backward launch");
     return PG_OK;
 }
@@ -716,11 +764,21 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
         // the reference every other candidate must match bit for bit.
         cands.push_back(default_tuning(PG_PATH_DIRECT));
         const int go_max = direct_scatter_on(batch, grid, default_tuning(PG_PATH_DIRECT)) ? 1 : 0;
+        // The general-cell kernel has a fixed block and no store hint or scatter mode: only
+        // the residency and the chunk size vary.
+        if (batch->cell)
+            for (int bps : {0, 1, 2})
+                for (int cp : {1, 2, 4, 8, 16}) {
+                    pg_tuning t = default_tuning(PG_PATH_DIRECT);
+                    t.blocks_per_sm = bps;
+                    t.chunk_planes = cp;
+                    cands.push_back(t);
+                }
         for (int threads : {256, 512})
             for (int bps : {0, 1, 2})
                 for (int hint : {0, 1})
                     for (int cp : {1, 2, 4, 8})
-                        for (int go = 0; go <= go_max; ++go) {
+                        for (int go = 0; go <= go_max && !batch->cell; ++go) {
                             pg_tuning t = default_tuning(PG_PATH_DIRECT);
                             t.block_threads = threads;
                             t.blocks_per_sm = bps;
@@ -732,7 +790,8 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
     }
     Geometry G;
     make_geometry(batch, grid, &G);
-    const bool sep_ok = grid->cutoff != PG_CUTOFF_SPHERE && separable_supported(G, out_dtype);
+    const bool sep_ok = grid->cutoff != PG_CUTOFF_SPHERE && !batch->cell &&
+                        separable_supported(G, out_dtype);
     if (path != PG_PATH_DIRECT && sep_ok) {
         for (int simple : {0, 1})
             for (int nt : {128, 256, 64}) {
@@ -960,9 +1019,10 @@ pg_status pg_plan_create(pg_plan **plan, const pg_grid *grid, int32_t out_dtype,
     if (p->tuning.path == PG_PATH_SEPARABLE && grid->cutoff == PG_CUTOFF_SPHERE)
         p->tuning = default_tuning(PG_PATH_DIRECT);
     const size_t A = (size_t)std::max(max_atoms, 1), M = (size_t)max_mol;
-    const size_t sizes[5] = {A * 3 * 4, A * 4, (M + 1) * 4, M * 3 * 4, M * 3 * 4};
+    const size_t sizes[kPlanCopies] = {A * 3 * 4, A * 4,      (M + 1) * 4, M * 3 * 4,
+                                       M * 3 * 4, A * 4, M * 9 * 4};
     size_t total = 0;
-    for (int i = 0; i < 5; ++i) {
+    for (int i = 0; i < kPlanCopies; ++i) {
         p->stage_off[i] = total;
         total += (sizes[i] + 255) / 256 * 256;
     }
@@ -976,6 +1036,8 @@ pg_status pg_plan_create(pg_plan **plan, const pg_grid *grid, int32_t out_dtype,
     if ((e = cudaMalloc(&p->d_moloff, sizes[2])) != cudaSuccess) return bad(e, "cudaMalloc");
     if ((e = cudaMalloc(&p->d_origin, sizes[3])) != cudaSuccess) return bad(e, "cudaMalloc");
     if ((e = cudaMalloc(&p->d_spacing, sizes[4])) != cudaSuccess) return bad(e, "cudaMalloc");
+    if ((e = cudaMalloc(&p->d_weight, sizes[5])) != cudaSuccess) return bad(e, "cudaMalloc");
+    if ((e = cudaMalloc(&p->d_cell, sizes[6])) != cudaSuccess) return bad(e, "cudaMalloc");
     if ((e = cudaMalloc(&p->d_err, sizeof(unsigned))) != cudaSuccess) return bad(e, "cudaMalloc");
     if ((e = cudaMalloc(&p->d_sched, 4 * sizeof(unsigned long long))) != cudaSuccess)
         return bad(e, "cudaMalloc");
@@ -1013,14 +1075,23 @@ pg_status pg_plan_run(pg_plan *p, const pg_batch *hb, void *out, void *stream)
     Device *d = nullptr;
     if ((st = get_device(&d))) return st;
 
-    const void *host[5] = {hb->coords, hb->elem, hb->mol_off, hb->origin, hb->spacing};
-    const size_t bytes[5] = {(size_t)hb->n_atoms * 12, (size_t)hb->n_atoms * 4,
-                             (size_t)(hb->n_mol + 1) * 4, (size_t)hb->n_mol * 12,
-                             (size_t)hb->n_mol * 12};
-    void *const dst[5] = {p->d_coords, p->d_elem, p->d_moloff, p->d_origin, p->d_spacing};
-    const void *src[5];
-    size_t cnt[5];
-    for (int i = 0; i < 5; ++i) {
+    // Absent optional arrays (spacing with a cell, weight, cell) copy 16 dummy bytes, so the
+    // graph keeps one shape; the launch reads them as NULL.
+    const void *host[kPlanCopies] = {hb->coords, hb->elem,   hb->mol_off, hb->origin,
+                                     hb->spacing, hb->weight, hb->cell};
+    const size_t nA = (size_t)hb->n_atoms, nM = (size_t)hb->n_mol;
+    const size_t bytes[kPlanCopies] = {nA * 12,
+                                       nA * 4,
+                                       (nM + 1) * 4,
+                                       nM * 12,
+                                       hb->spacing ? nM * 12 : 0,
+                                       hb->weight ? nA * 4 : 0,
+                                       hb->cell ? nM * 36 : 0};
+    void *const dst[kPlanCopies] = {p->d_coords,  p->d_elem,   p->d_moloff, p->d_origin,
+                                    p->d_spacing, p->d_weight, p->d_cell};
+    const void *src[kPlanCopies];
+    size_t cnt[kPlanCopies];
+    for (int i = 0; i < kPlanCopies; ++i) {
         unsigned char *slot = p->h_stage + p->stage_off[i];
         if (bytes[i] == 0) {  // graphs take no zero-length copies: move 16 dummy bytes
             src[i] = slot;
@@ -1039,10 +1110,15 @@ pg_status pg_plan_run(pg_plan *p, const pg_batch *hb, void *out, void *stream)
     db.elem = p->d_elem;
     db.mol_off = p->d_moloff;
     db.origin = p->d_origin;
-    db.spacing = p->d_spacing;
+    db.spacing = hb->spacing ? p->d_spacing : nullptr;
+    db.weight = hb->weight ? p->d_weight : nullptr;
+    db.cell = hb->cell ? p->d_cell : nullptr;
     KernelLaunch kl;
-    if ((st = plan_forward(&db, &p->grid, p->dtype, out, p->tuning, *d, p->d_err, p->d_sched,
-                           &kl)))
+    // A batch with cell matrices always takes the general-cell kernel.
+    const pg_tuning t = (hb->cell && p->tuning.path == PG_PATH_SEPARABLE)
+                            ? default_tuning(PG_PATH_DIRECT)
+                            : p->tuning;
+    if ((st = plan_forward(&db, &p->grid, p->dtype, out, t, *d, p->d_err, p->d_sched, &kl)))
         return st;
     if ((st = plan_update_graph(p, src, cnt, dst, kl))) return st;
     cudaStream_t s = (cudaStream_t)stream;

@@ -12,6 +12,10 @@
 // derivative (Sec. IV-C's separable-product rule), which is a difference of the Gaussian at
 // the voxel's two edges.
 //
+// With per-atom weights w_a (weighted grids) the coordinate gradient is w_a times the sum
+// above, and the weight gradient dL/dw_a is the same sum of g times the atom's unweighted
+// terms, without the factor d / sigma^2.
+//
 // One warp owns one atom at a time (atoms handed out from a per-launch counter) and walks the
 // voxels of the atom's cutoff box (clamped to the grid, or wrapped for periodic cells), 32
 // voxels per step with z fastest so the reads of g are coalesced.  Each lane keeps a partial sum; a fixed butterfly reduction combines them.  Each
@@ -90,24 +94,23 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
     const int warp = threadIdx.x >> 5;
     const int warps = blockDim.x >> 5;
     const GT *gout = reinterpret_cast<const GT *>(A.grad_out);
+    // Either output may be absent (null).
+    auto put = [&](int a, float gx, float gy, float gz, float gw) {
+        if (A.grad_coords) {
+            A.grad_coords[3 * a] = gx;
+            A.grad_coords[3 * a + 1] = gy;
+            A.grad_coords[3 * a + 2] = gz;
+        }
+        if (A.grad_weight) A.grad_weight[a] = gw;
+    };
 
     // Atoms before the first molecule or after the last one belong to no molecule.
-    if (G.n_mol > 0) {
-        const int first = __ldg(A.in.mol_off), last = __ldg(A.in.mol_off + G.n_mol);
+    {
+        const int first = G.n_mol > 0 ? __ldg(A.in.mol_off) : 0;
+        const int last = G.n_mol > 0 ? __ldg(A.in.mol_off + G.n_mol) : 0;
         for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < G.n_atoms;
              a += gridDim.x * blockDim.x)
-            if (a < first || a >= last) {
-                A.grad_coords[3 * a] = 0.0f;
-                A.grad_coords[3 * a + 1] = 0.0f;
-                A.grad_coords[3 * a + 2] = 0.0f;
-            }
-    } else {
-        for (int a = blockIdx.x * blockDim.x + threadIdx.x; a < G.n_atoms;
-             a += gridDim.x * blockDim.x) {
-            A.grad_coords[3 * a] = 0.0f;
-            A.grad_coords[3 * a + 1] = 0.0f;
-            A.grad_coords[3 * a + 2] = 0.0f;
-        }
+            if (G.n_mol == 0 || a < first || a >= last) put(a, 0.0f, 0.0f, 0.0f, 0.0f);
     }
 
     const long long plane = (long long)G.ny * G.nz;
@@ -149,9 +152,7 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
                 if (lane == 0) {
                     atomicOr(A.err, !off_ok ? PG_DEVERR_OFFSETS
                                             : (sp_ok ? PG_DEVERR_ELEMENT : PG_DEVERR_SPACING));
-                    A.grad_coords[3 * a] = 0.0f;
-                    A.grad_coords[3 * a + 1] = 0.0f;
-                    A.grad_coords[3 * a + 2] = 0.0f;
+                    put(a, 0.0f, 0.0f, 0.0f, 0.0f);
                 }
                 continue;
             }
@@ -183,10 +184,12 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
                 sj = (32 - si * njk) / nk;
                 sk = 32 - si * njk - sj * nk;
             }
-            float sx = 0.0f, sy = 0.0f, sz = 0.0f;
+            float sx = 0.0f, sy = 0.0f, sz = 0.0f, sw = 0.0f;
             constexpr int U = 4;  // voxels in flight per lane
             for (long long f0 = lane; f0 < total; f0 += 32 * U) {
-                float gv[U], dxv[U], dyv[U], dzv[U];  // FORM 1: gv unused, d*v hold terms
+                // gv: g times the term (FORM 0); FORM 1 keeps the derivative terms in d*v
+                // and g times the term in tv.
+                float gv[U], dxv[U], dyv[U], dzv[U], tv[U];
                 bool inv[U];
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
@@ -222,10 +225,12 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
                                   : 0.0f;
                     if (FORM == 0) {
                         gv[u] *= inv[u] ? ex2_approx(-q * d2) : 0.0f;
+                        tv[u] = gv[u];
                     } else {
                         const float w = inv[u] ? gv[u] : 0.0f;
                         const float fx = erf_axis(dx, hx, kf), fy = erf_axis(dy, hy, kf),
                                     fz = erf_axis(dz, hz, kf);
+                        tv[u] = w * fx * fy * fz;
                         dxv[u] = w * erf_axis_dmu(dx, hx, kf, kd) * fy * fz;
                         dyv[u] = w * fx * erf_axis_dmu(dy, hy, kf, kd) * fz;
                         dzv[u] = w * fx * fy * erf_axis_dmu(dz, hz, kf, kd);
@@ -254,6 +259,7 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
                         sy += dyv[u];
                         sz += dzv[u];
                     }
+                    sw += tv[u];
                 }
             }
 #pragma unroll
@@ -261,12 +267,12 @@ __global__ void __launch_bounds__(256) backward_kernel(const BackwardArgs A)
                 sx += __shfl_xor_sync(0xffffffffu, sx, o);
                 sy += __shfl_xor_sync(0xffffffffu, sy, o);
                 sz += __shfl_xor_sync(0xffffffffu, sz, o);
+                sw += __shfl_xor_sync(0xffffffffu, sw, o);
             }
             if (lane == 0) {
-                const float s = FORM == 0 ? G.inv_s2[c] : 1.0f;
-                A.grad_coords[3 * a] = sx * s;
-                A.grad_coords[3 * a + 1] = sy * s;
-                A.grad_coords[3 * a + 2] = sz * s;
+                const float w = A.in.weight ? __ldg(A.in.weight + a) : 1.0f;
+                const float s = w * (FORM == 0 ? G.inv_s2[c] : 1.0f);
+                put(a, sx * s, sy * s, sz * s, sw);
             }
         }
     }
@@ -310,6 +316,7 @@ const void *pick(int cutoff, int periodic, int form)
 
 cudaError_t backward_plan(const BackwardArgs &a, int grad_dtype, int sm_count, KernelLaunch *kl)
 {
+    if (a.in.cell) return cell_backward_plan(a, grad_dtype, sm_count, kl);
     const int cut = a.geo.cutoff, per = a.geo.periodic, form = a.geo.form;
     const void *f = grad_dtype == PG_F32   ? pick<float>(cut, per, form)
                     : grad_dtype == PG_F16 ? pick<__half>(cut, per, form)

@@ -59,6 +59,8 @@ struct Inputs {
     const int *mol_off;
     const float *origin;
     const float *spacing;
+    const float *weight;  // per-atom weights, or null (all ones)
+    const float *cell;    // per-molecule 3x3 box edges (rows), or null (axis-aligned box)
 };
 
 // 32-bit words of dynamic shared memory per warp of the direct kernel: kStageCap staged
@@ -89,7 +91,8 @@ constexpr int kSchedSlots = 64;
 struct BackwardArgs {
     Inputs in;
     const void *grad_out;
-    float *grad_coords;
+    float *grad_coords;  // [n_atoms][3], or null
+    float *grad_weight;  // [n_atoms] dL/dw, or null
     unsigned *err;
     unsigned long long *sched;  // {next atom, retired warps}; zero between launches
     Geometry geo;
@@ -133,8 +136,16 @@ const void *pick_direct_integral(int dtype, bool vec_ok, int cutoff, int periodi
 cudaError_t direct_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tuning &t,
                         int sm_count, KernelLaunch *kl);
 
-// Coordinate adjoint (pg_backward.cu).
+// Coordinate (and weight) adjoint (pg_backward.cu); batches with cells go to the general-cell
+// adjoint.
 cudaError_t backward_plan(const BackwardArgs &a, int grad_dtype, int sm_count, KernelLaunch *kl);
+
+// General cells (pg_cell.cu): forward over a DirectArgs description (plane_stride unused) and
+// the adjoint.  cudaErrorNotSupported for a periodic cell without a cutoff.
+cudaError_t cell_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tuning &t,
+                      int sm_count, KernelLaunch *kl);
+cudaError_t cell_backward_plan(const BackwardArgs &a, int grad_dtype, int sm_count,
+                               KernelLaunch *kl);
 
 // Separable tcgen05 contraction (pg_separable.cu).  Returns cudaErrorNotSupported for
 // shapes it does not cover.

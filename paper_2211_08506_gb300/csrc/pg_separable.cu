@@ -477,7 +477,8 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                                 pos = make_float4(__ldg(A.in.coords + 3 * ai),
                                                   __ldg(A.in.coords + 3 * ai + 1),
                                                   __ldg(A.in.coords + 3 * ai + 2), G.q[e]);
-                                aux = make_float4(G.r2[e], (float)e, G.kerf[e], 0.f);
+                                aux = make_float4(G.r2[e], (float)e, G.kerf[e],
+                                                  A.in.weight ? __ldg(A.in.weight + ai) : 1.0f);
                             } else if (m0 == 0) {
                                 atomicOr(A.err, PG_DEVERR_ELEMENT);
                             }
@@ -510,7 +511,7 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                         }
                         tgz[z * kTab + j] = v;
                     }
-                    // A row `tid`: [elem a == c] g_x(a, x), 4 core-matrix chunks of 8 atoms.
+                    // A row `tid`: [elem a == c] w_a g_x(a, x), 4 core-matrix chunks of 8 atoms.
 #pragma unroll
                     for (int jg = 0; jg < kKC / 8; ++jg) {
                         float v[8];
@@ -523,7 +524,7 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                             if (row_ok && (int)aux.y == row_c) {
                                 float d = vx - p.x;
                                 if (PER) d = wrap(d, Lx, iLx);
-                                v[t] = axis_factor<CUT, FORM>(d, p.w, aux.x, hx, aux.z);
+                                v[t] = aux.w * axis_factor<CUT, FORM>(d, p.w, aux.x, hx, aux.z);
                             }
                         }
                         const uint4 w = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
@@ -820,7 +821,8 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
         // ------------------------------------------------------------------ producer
         const int p = tid - 128;
         // Per atom of the K chunk: {x, y, z, q}, {r2, elem, k_erf, molecule within the tile},
-        // and its molecule's grid geometry {ox, oy, oz, hx}, {hy, hz, -, -}.
+        // and its molecule's grid geometry {ox, oy, oz, hx} with {hy, hz, weight, -}.  The
+        // weight scales the atom's A entries (its g_x), exactly 1 for unweighted grids.
         // Tables of up to A.kslots K chunks stay resident for a tile, so a tile with several
         // chunks builds each once instead of once per N chunk.
         float4 *const atoms0 = reinterpret_cast<float4 *>(smem + L.atoms);
@@ -874,7 +876,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             float4 pos = make_float4(0.f, 0.f, 0.f, 0.f);
                             float4 aux = make_float4(0.f, -1.f, 0.f, 0.f);
                             float4 g0 = make_float4(0.f, 0.f, 0.f, 1.f);
-                            float4 g1 = make_float4(1.f, 1.f, 0.f, 0.f);
+                            float4 g1 = make_float4(1.f, 1.f, 1.f, 0.f);
                             if (ai < it.a1) {
                                 // The atom's molecule: the item's, or in a packed tile the last
                                 // k with mol_off[b + k] <= ai.
@@ -895,10 +897,10 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                                                      __ldg(A.in.origin + 3 * mb + 2),
                                                      __ldg(A.in.spacing + 3 * mb));
                                     g1 = make_float4(__ldg(A.in.spacing + 3 * mb + 1),
-                                                     __ldg(A.in.spacing + 3 * mb + 2), 0.f, 0.f);
+                                                     __ldg(A.in.spacing + 3 * mb + 2), 1.f, 0.f);
                                 } else {
                                     g0 = make_float4(it.ox, it.oy, it.oz, it.hx);
-                                    g1 = make_float4(it.hy, it.hz, 0.f, 0.f);
+                                    g1 = make_float4(it.hy, it.hz, 1.f, 0.f);
                                 }
                                 const bool sp_ok = g0.w > 0.0f && g1.x > 0.0f && g1.y > 0.0f &&
                                                    g0.w < INFINITY && g1.x < INFINITY &&
@@ -912,6 +914,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                                                       __ldg(A.in.coords + 3 * ai + 1),
                                                       __ldg(A.in.coords + 3 * ai + 2), G.q[e]);
                                     aux = make_float4(G.r2[e], (float)e, G.kerf[e], (float)k);
+                                    if (A.in.weight) g1.z = __ldg(A.in.weight + ai);
                                 } else if (it.m0 == 0) {
                                     atomicOr(A.err, PG_DEVERR_ELEMENT);
                                 }
@@ -948,6 +951,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                                     const float d = fmaf((float)i + 0.5f, h, o) - mu;
                                     if (aux.y < 0.0f || (CUT == PG_CUTOFF_BOX && d * d > aux.x))
                                         v = 0.0f;
+                                    if (axis == 0) v *= g1.z;
                                     if (i < n) tab[i * stride + j] = v;
                                 }
                             };
@@ -967,8 +971,8 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                                     const float Lx = G.nx * g0.w;
                                     d = wrap(d, Lx, 1.0f / Lx);
                                 }
-                                v = axis_factor<CUT, FORM>(d, q4.w, atom_aux[j].x, g0.w,
-                                                     atom_aux[j].z);
+                                v = atom_g1[j].z * axis_factor<CUT, FORM>(d, q4.w, atom_aux[j].x,
+                                                                          g0.w, atom_aux[j].z);
                             }
                             tgx[x * kTabX + j] = v;
                         }
@@ -1033,8 +1037,9 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                                             const float Lx = G.nx * hx;
                                             d = wrap(d, Lx, 1.0f / Lx);
                                         }
-                                        v[t] = axis_factor<CUT, FORM>(d, atom_pos[j].w, aux.x,
-                                                                      hx, aux.z);
+                                        v[t] = atom_g1[j].z *
+                                               axis_factor<CUT, FORM>(d, atom_pos[j].w, aux.x, hx,
+                                                                      aux.z);
                                     }
                                 }
                             }

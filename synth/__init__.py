@@ -311,6 +311,109 @@ def crystal_shaped(shard: int | None = None, n_cells: int = 512, grid: int = 48)
                     f"{n_cells} periodic orthorhombic cells 5-15A, 20-500 atoms, 10ch Zipf1.2, 48^3, sigma .5, sphere 3sigma")
 
 
+def _random_rotation(rng: np.random.Generator) -> np.ndarray:
+    """Uniform random rotation (QR of a Gaussian matrix, signs fixed, det +1)."""
+    q, r = np.linalg.qr(rng.standard_normal((3, 3)))
+    q = q * np.sign(np.diag(r))
+    if np.linalg.det(q) < 0:
+        q[:, 0] = -q[:, 0]
+    return q
+
+
+def triclinic_cell(rng: np.random.Generator, n_atoms: int, edge_lo=5.0, edge_hi=15.0,
+                   angle_lo=60.0, angle_hi=120.0, min_width=3.2, min_sep=1.2,
+                   max_tries=1000):
+    """Random triclinic cell with n_atoms atoms placed by random sequential addition.
+
+    Edge lengths a, b, c are U[edge_lo, edge_hi] A and the angles alpha, beta, gamma
+    U[angle_lo, angle_hi] degrees.  Cells that are not valid, or whose distance between
+    opposite faces is below min_width on some axis, are redrawn.  The cell is then turned
+    by a uniform random rotation.  Fractional coordinates are uniform; a proposal closer
+    than min_sep to a placed atom is rejected, and after max_tries rejections for one atom
+    the cell is redrawn.  Since every width exceeds 2 min_sep, only the image at the rounded
+    fractional difference can come that close.
+    Returns (M [3, 3] with rows a, b, c, frac [n, 3], redraws)."""
+    redraws = 0
+    v_excl = math.pi / 6.0 * min_sep ** 3
+    assert min_width > 2.0 * min_sep
+    while True:
+        a, b, c = rng.uniform(edge_lo, edge_hi, size=3)
+        al, be, ga = np.radians(rng.uniform(angle_lo, angle_hi, size=3))
+        cy = (math.cos(al) - math.cos(be) * math.cos(ga)) / math.sin(ga)
+        cz2 = 1.0 - math.cos(be) ** 2 - cy ** 2
+        if cz2 <= 0.0:
+            redraws += 1
+            continue
+        M = np.array([[a, 0.0, 0.0],
+                      [b * math.cos(ga), b * math.sin(ga), 0.0],
+                      [c * math.cos(be), c * cy, c * math.sqrt(cz2)]])
+        width = 1.0 / np.linalg.norm(np.linalg.inv(M), axis=0)
+        vol = abs(float(np.linalg.det(M)))
+        if width.min() < min_width or n_atoms * v_excl / vol > JAMMING_SKIP:
+            redraws += 1
+            continue
+        M = M @ _random_rotation(rng).T
+        placed = np.zeros((n_atoms, 3))
+        ok = True
+        for i in range(n_atoms):
+            tries = 0
+            done = False
+            while tries < max_tries:
+                m = min(4 if tries == 0 else 64, max_tries - tries)
+                cand = rng.uniform(0.0, 1.0, size=(m, 3))
+                if i == 0:
+                    placed[0] = cand[0]
+                    done = True
+                    break
+                diff = cand[:, None, :] - placed[None, :i, :]
+                diff -= np.round(diff)
+                dist2 = ((diff @ M) ** 2).sum(axis=2).min(axis=1)
+                good = np.nonzero(dist2 >= min_sep * min_sep)[0]
+                if good.size:
+                    placed[i] = cand[good[0]]
+                    done = True
+                    break
+                tries += m
+            if not done:
+                ok = False
+                break
+        if ok:
+            return M, placed, redraws
+        redraws += 1
+
+
+def crystal_triclinic(shard: int | None = None, n_cells: int = 512, grid: int = 48) -> Workload:
+    """Weighted triclinic crystal batch: cells with edges U[5,15] A, angles U[60,120] deg,
+    every face-to-face width at least 3.2 A, random orientation; atom counts log-uniform in
+    20..500; 10 element channels with Zipf(1.2) frequencies; 1.2 A minimum separation;
+    per-atom weights U[0.5,1.5]; periodic nearest image; sigma 0.5 A; spherical cutoff
+    3 sigma; a 48^3 grid along the cell edges; FP16 output."""
+    rng = _rng(7, shard)
+    p = (np.arange(1, CRYSTAL_ELEMENTS + 1, dtype=float)) ** (-ZIPF_EXPONENT)
+    p /= p.sum()
+    coords, elems, origins, spacings, cells, weights = [], [], [], [], [], []
+    redraws = 0
+    for _ in range(n_cells):
+        na = int(round(math.exp(rng.uniform(math.log(20.0), math.log(500.0)))))
+        M, frac, r = triclinic_cell(rng, na)
+        redraws += r
+        M32 = M.astype(np.float32)
+        cells.append(M32)
+        coords.append(frac @ M32.astype(np.float64))
+        elems.append(rng.choice(CRYSTAL_ELEMENTS, size=na, p=p))
+        weights.append(rng.uniform(0.5, 1.5, size=na))
+        origins.append(np.zeros(3))
+        spacings.append(np.linalg.norm(M32, axis=1) / grid)
+    batch = _pack(coords, elems, origins, spacings, info={"cell_redraws": redraws})
+    batch.cell = np.ascontiguousarray(np.stack(cells), dtype=np.float32)
+    batch.weight = np.ascontiguousarray(np.concatenate(weights), dtype=np.float32)
+    return Workload("crystal_triclinic", batch, grid, grid, grid, CRYSTAL_ELEMENTS,
+                    np.full(CRYSTAL_ELEMENTS, 0.5, np.float32), CUTOFF_SPHERE, 3.0, True,
+                    "f16",
+                    f"{n_cells} weighted periodic triclinic cells 5-15A 60-120deg, 20-500 atoms, "
+                    "10ch Zipf1.2, 48^3, sigma .5, sphere 3sigma")
+
+
 def differentiation(shard: int | None = None, n_mol: int = 1024) -> Workload:
     """Differentiation workload: 1024 QM9-shaped molecules on 5ch 32^3 @0.5 A, per-element
     sigma, spherical cutoff 3 sigma; the loss is <W, G> with W from ``loss_weights``."""
@@ -407,6 +510,7 @@ WORKLOADS = {
     "differentiation": differentiation,
     "refinement": refinement,
     "pipeline_single_channel": pipeline_single_channel,
+    "crystal_triclinic": crystal_triclinic,
 }
 
 

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_function(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert lib.pg_version() == 1
+    assert lib.pg_version() == 2
     assert lib.status_name(lib.PG_ERR_UNSUPPORTED) == "PG_ERR_UNSUPPORTED"
     assert lib.status_name(99) == "PG_ERR_UNKNOWN"
 
@@ -90,6 +90,8 @@ def test_null_arguments_do_not_crash(lib):
     assert L.pg_voxelize(None, None, 0, None, 0, None) == lib.PG_ERR_INVALID_ARG
     assert L.pg_voxelize_tuned(None, None, 0, None, None, None) == lib.PG_ERR_INVALID_ARG
     assert L.pg_voxelize_backward(None, None, 0, None, None, None) == lib.PG_ERR_INVALID_ARG
+    assert L.pg_voxelize_backward_ex(None, None, 0, None, None, None, None) == \
+        lib.PG_ERR_INVALID_ARG
     assert L.pg_plan_create(None, None, 0, 0, 0, 0) == lib.PG_ERR_INVALID_ARG
     assert L.pg_plan_run(None, None, None, None) == lib.PG_ERR_INVALID_ARG
     assert L.pg_tuning_save(None) == lib.PG_ERR_INVALID_ARG
@@ -123,3 +125,25 @@ def test_refine_rejects_bad_arguments_on_the_host(lib):
         assert st == lib.PG_ERR_INVALID_ARG and needle in lib.last_error(), (kw, lib.last_error())
     assert L.pg_refine_work_floats(b, g) == 5 * 32 ** 3 + 3
 
+
+
+def test_cells_and_weights_are_validated_on_the_host(lib):
+    L = lib.load()
+    fake = ctypes.c_void_p(16)  # never dereferenced: every case fails before any launch
+    cell = dict(n_mol=1, n_atoms=1, coords=fake, elem=fake, mol_off=fake, origin=fake,
+                cell=fake)
+    g, keep = _grid(lib, voxel_form=1)
+    st = L.pg_voxelize(lib.pg_batch(**cell), g, 0, fake, 0, None)
+    assert st == lib.PG_ERR_UNSUPPORTED and "axis-aligned" in lib.last_error()
+    g, keep = _grid(lib, periodic=1, cutoff=1)
+    st = L.pg_voxelize(lib.pg_batch(**cell), g, 0, fake, 0, None)
+    assert st == lib.PG_ERR_UNSUPPORTED and "cutoff" in lib.last_error()
+    # Spacing may be absent only when a cell replaces it.
+    nocell = dict(cell)
+    nocell.pop("cell")
+    g, keep = _grid(lib)
+    st = L.pg_voxelize(lib.pg_batch(**nocell), g, 0, fake, 0, None)
+    assert st == lib.PG_ERR_INVALID_ARG and "spacing" in lib.last_error()
+    # The weight adjoint needs at least one output.
+    st = L.pg_voxelize_backward_ex(lib.pg_batch(**cell), g, 0, fake, None, None, None)
+    assert st == lib.PG_ERR_INVALID_ARG and "both" in lib.last_error()
