@@ -142,10 +142,14 @@ __global__ void __launch_bounds__(kCellThreads) cell_kernel(const DirectArgs A)
         if (lane == 0) chunk = atomicAdd(A.sched, 1ull);
         chunk = __shfl_sync(0xffffffffu, chunk, 0);
         if (chunk >= n_chunks) break;
-        const unsigned long long bc = chunk / (unsigned)x_chunks;
-        const int xc = (int)(chunk - bc * x_chunks);
-        const int b = (int)(bc / (unsigned)G.C);
-        const int c = (int)(bc - (unsigned long long)b * G.C);
+        // Chunks run channel-major: channel 0 of every molecule first.  Channels listed by
+        // decreasing atom frequency then hand out the largest chunks first, which shortens
+        // the tail of uneven batches.  The output item is still (molecule, channel, x).
+        const unsigned long long cb = chunk / (unsigned)x_chunks;
+        const int xc = (int)(chunk - cb * x_chunks);
+        const int c = (int)(cb / (unsigned)G.n_mol);
+        const int b = (int)(cb - (unsigned long long)c * G.n_mol);
+        const unsigned long long bc = (unsigned long long)b * G.C + c;
         const int x_begin = xc * chunk_planes;
         const int x_end = min(G.nx, x_begin + chunk_planes);
         if (b != cur_b) {
