@@ -158,7 +158,8 @@ typedef struct {
  * Launch choice for one problem bucket.  Zeros mean "library default".
  *   path           pg_path (DIRECT or SEPARABLE; AUTO resolves through the tuning cache)
  *   block_threads  threads per CTA of the direct kernel: 128, 256 or 512
- *   blocks_per_sm  persistent CTAs per SM (0 = as many as fit)
+ *   blocks_per_sm  persistent CTAs per SM (0 = as many as fit); on the pipelined separable
+ *                  path 2 also sizes its resident K chunks so that two CTAs fit an SM
  *   store_hint     0: default global stores; 1: streaming (evict-first) stores
  *   n_tile         separable path: output columns per tensor-core tile (64, 128 or 256)
  *   gather_only    direct path: 0 lets planes with many candidate atoms accumulate in

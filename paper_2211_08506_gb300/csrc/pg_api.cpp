@@ -793,13 +793,18 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
     const bool sep_ok = grid->cutoff != PG_CUTOFF_SPHERE && !batch->cell &&
                         separable_supported(G, out_dtype);
     if (path != PG_PATH_DIRECT && sep_ok) {
+        // The pipelined kernel also tries a footprint of two CTAs per SM (fewer resident K
+        // chunks) against the default of as many resident chunks as one CTA holds.
         for (int simple : {0, 1})
-            for (int nt : {128, 256, 64}) {
-                pg_tuning t = default_tuning(PG_PATH_SEPARABLE);
-                t.n_tile = nt;
-                t.separable_simple = simple;
-                cands.push_back(t);
-            }
+            for (int nt : {128, 256, 64})
+                for (int bps : {0, 2}) {
+                    if (simple && bps) continue;
+                    pg_tuning t = default_tuning(PG_PATH_SEPARABLE);
+                    t.n_tile = nt;
+                    t.separable_simple = simple;
+                    t.blocks_per_sm = bps;
+                    cands.push_back(t);
+                }
     }
     if (cands.empty())
         return fail(PG_ERR_UNSUPPORTED, "no eligible candidate for path %d (separable needs a "

@@ -607,7 +607,10 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
 //              (tcgen05.ld -> output type -> staging row -> coalesced stores) while the other
 //              fills;
 //   warps 4-7  producer: per item builds atoms and per-axis tables, then for every step
-//              (N tile, K chunk) writes the A and B operands of one of two shared-memory stages;
+//              (N tile, K chunk) writes the B operand into one of two shared-memory stages.
+//              The A operand does not depend on the N tile: when the item's K chunks fit the
+//              resident slots it is written once per K chunk into a slot of its own, else
+//              into the stage with B at every step;
 //   warp 8     MMA: one thread issues the tcgen05.mma pair of each step and commits to the
 //              stage's "empty" barrier and, after a tile's last K chunk, to the accumulator's
 //              "full" barrier.
@@ -619,7 +622,8 @@ constexpr int kPipeStages = 2;
 constexpr int kPipeThreads = 288;  // 9 warps
 
 struct PipeLayout {
-    int bars, tmem, flag, atoms, stage0, stage_bytes, a_bytes, gx, gy, gz, out, out_stride, total;
+    int bars, tmem, flag, atoms, stage0, stage_bytes, a_bytes, aslots, gx, gy, gz, out, out_stride,
+        total;
 };
 
 __host__ __device__ inline PipeLayout pipe_layout(int nx, int ny, int nz, int n_tile, int esz,
@@ -635,14 +639,16 @@ __host__ __device__ inline PipeLayout pipe_layout(int nx, int ny, int nz, int n_
     o += 8;
     o = align_up(o, 128);
     L.atoms = o;
-    o += kslots * kKC * 4 * 16;  // per slot: pos, aux, geometry (2)
+    o += kKC * 4 * 16;  // the K chunk being built: pos, aux, geometry (2)
     o = align_up(o, 1024);
     L.a_bytes = kRows * kKC * 2;
     L.stage_bytes = align_up(L.a_bytes + n_tile * kKC * 2, 1024);
     L.stage0 = o;
     o += kPipeStages * L.stage_bytes;
+    L.aslots = o;  // resident A tiles, one per K chunk slot
+    o += kslots * L.a_bytes;
     L.gx = o;
-    o += kslots * nx * kTabX * 4;
+    o += nx * kTabX * 4;  // read only while the chunk's A tile is built
     o = align_up(o, 128);
     L.gy = o;
     o += kslots * ny * kTab * 4;
@@ -823,13 +829,14 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
         // Per atom of the K chunk: {x, y, z, q}, {r2, elem, k_erf, molecule within the tile},
         // and its molecule's grid geometry {ox, oy, oz, hx} with {hy, hz, weight, -}.  The
         // weight scales the atom's A entries (its g_x), exactly 1 for unweighted grids.
-        // Tables of up to A.kslots K chunks stay resident for a tile, so a tile with several
-        // chunks builds each once instead of once per N chunk.
+        // The g_y, g_z tables and the A tiles of up to A.kslots K chunks stay resident for a
+        // tile, so a tile with several chunks builds each once instead of once per N chunk.
+        // The atoms and g_x are only read while a chunk's A tile is built, in the step that
+        // builds its tables, so one copy serves every slot.
         float4 *const atoms0 = reinterpret_cast<float4 *>(smem + L.atoms);
         float *const tgx0 = reinterpret_cast<float *>(smem + L.gx);
         float *const tgy0 = reinterpret_cast<float *>(smem + L.gy);
         float *const tgz0 = reinterpret_cast<float *>(smem + L.gz);
-        long long stage_item[kPipeStages] = {-1, -1};
         const int dy32 = 32 / G.nz, dz32 = 32 - (32 / G.nz) * G.nz;
         unsigned step = 0;
         bool ok = true;
@@ -860,11 +867,24 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                     unsigned char *sb = sa + L.a_bytes;
                     const bool resident = it.n_kc <= A.kslots;
                     const int slot = resident ? kc : 0;
-                    float4 *atom_pos = atoms0 + slot * 4 * kKC;
+                    // Resident tiles keep each K chunk's A in a slot of its own, written at the
+                    // first N chunk.  Before a tile overwrites the slots, every MMA of the
+                    // previous tile (up to the step just handed over) must have completed.
+                    if (resident && nc == 0 && kc == 0 && step > 0) {
+                        const unsigned u = step - 1;
+                        const bool done = warp_wait(b_empty((int)(u % kPipeStages)),
+                                                    (u / kPipeStages) & 1u, flag);
+                        if (!producers_all(done)) {
+                            ok = false;
+                            break;
+                        }
+                    }
+                    unsigned char *a_dst = resident ? smem + L.aslots + kc * L.a_bytes : sa;
+                    float4 *atom_pos = atoms0;
                     float4 *atom_aux = atom_pos + kKC;
                     float4 *atom_g0 = atom_pos + 2 * kKC;
                     float4 *atom_g1 = atom_pos + 3 * kKC;
-                    float *tgx = tgx0 + slot * G.nx * kTabX;
+                    float *tgx = tgx0;
                     float *tgy = tgy0 + slot * G.ny * kTab;
                     float *tgz = tgz0 + slot * G.nz * kTab;
                     const bool new_atoms =
@@ -1012,9 +1032,8 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                         }
                         producer_sync();
                     }
-                    // A tile: rewritten unless this stage already holds this item's A (one
-                    // K chunk per item).
-                    if (it.n_kc > 1 || stage_item[s] != item) {
+                    // A tile: once per K chunk of a resident tile, else every step.
+                    if (!resident || nc == 0) {
 #pragma unroll
                         for (int jg = 0; jg < kKC / 8; ++jg) {
                             float v[8];
@@ -1043,12 +1062,11 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                                     }
                                 }
                             }
-                            *reinterpret_cast<uint4 *>(sa + (p >> 3) * 512 + jg * 128 +
+                            *reinterpret_cast<uint4 *>(a_dst + (p >> 3) * 512 + jg * 128 +
                                                        (p & 7) * 16) =
                                 make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
                                            pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
                         }
-                        stage_item[s] = it.n_kc > 1 ? -1 : item;
                     }
                     // B tile (layout as in the single-stage kernel).  Producer p always
                     // writes atom group kg = (p/8)%4 of columns nl = (p/32)*8 + p%8 + 32i, so
@@ -1108,8 +1126,11 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t sa = smem_u32(smem + L.stage0 + s * L.stage_bytes);
-                        const uint32_t sb = sa + L.a_bytes;
+                        const uint32_t st = smem_u32(smem + L.stage0 + s * L.stage_bytes);
+                        const uint32_t sb = st + L.a_bytes;
+                        const uint32_t sa = it.n_kc <= A.kslots
+                                                ? smem_u32(smem + L.aslots + kc * L.a_bytes)
+                                                : st;
 #pragma unroll
                         for (int k = 0; k < kKC / 16; ++k)
                             mma_bf16_f32(tmem + buf * n_tile, smem_desc(sa + k * 256, 128, 512),
@@ -1284,16 +1305,19 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
     // Molecules with fewer than 128 (channel, x) rows share a tile when their rows divide it.
     const int Mrows = a.geo.C * a.geo.nx;
     a.pack = (pipe && Mrows < kRows && kRows % Mrows == 0) ? kRows / Mrows : 0;
-    // Resident K-chunk tables: enough for a tile of average atoms with headroom, at most 8.
+    // Resident K chunks: enough for a tile of twice the average atoms, at most 8, within the
+    // shared memory of one CTA, or of blocks_per_sm CTAs per SM when the tuning asks for more.
     const double atoms_per_tile = (a.pack > 0 ? a.pack : 1) * (a.geo.n_mol > 0
                                       ? (double)a.geo.n_atoms / a.geo.n_mol : 0.0);
-    int kslots = (int)std::ceil(1.5 * atoms_per_tile / kKC);
+    int kslots = (int)std::ceil(2.0 * atoms_per_tile / kKC);
     kslots = kslots < 1 ? 1 : (kslots > 8 ? 8 : kslots);
     auto bytes = [&](int nt, int ks) {
         return pipe ? pipe_layout(a.geo.nx, a.geo.ny, a.geo.nz, nt, esz, ks).total
                     : sep_layout(a.geo.ny, a.geo.nz, nt, esz).total;
     };
-    while (kslots > 1 && bytes(n_tile, kslots) > 227 * 1024) --kslots;
+    const int budget = (pipe && t.blocks_per_sm >= 2) ? 228 * 1024 / t.blocks_per_sm - 1024
+                                                      : 227 * 1024;
+    while (kslots > 1 && bytes(n_tile, kslots) > budget) --kslots;
     // Largest requested tile whose shared-memory footprint fits one SM's 227 KB.
     while (n_tile > 64 && bytes(n_tile, kslots) > 227 * 1024) n_tile /= 2;
     const int smem = bytes(n_tile, kslots);
