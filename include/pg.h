@@ -169,6 +169,10 @@ typedef struct {
  *   chunk_planes   direct path: x-planes per dynamically scheduled work chunk (1..64; 0 = 8)
  *   separable_simple  separable path: 0 = warp-specialized pipeline (default), 1 = one-stage
  *                  kernel.  Both accumulate the same BF16 products in the same order.
+ *   chunk_order    direct and general-cell kernels: 0 = chunks in (molecule, channel) order,
+ *                  so concurrent stores stay close in memory; 1 = channel-major, which hands
+ *                  out the largest chunks first when channels are listed by decreasing atom
+ *                  frequency.  Results are identical bit for bit.
  */
 typedef struct {
     int32_t path;
@@ -179,6 +183,7 @@ typedef struct {
     int32_t gather_only;
     int32_t chunk_planes;
     int32_t separable_simple;
+    int32_t chunk_order;
 } pg_tuning;
 
 /* Library ABI version (PG_ABI_VERSION). */
@@ -272,7 +277,10 @@ pg_status pg_sync_status(void *stream, uint32_t *bits_out);
  * periodicity, atoms-per-molecule bucket), check each against the first candidate's
  * output (bitwise for the direct kernel's launch shapes, 1e-2 of the grid maximum for
  * the separable path), and record the fastest passing one for PG_PATH_AUTO.
- * `out` is used as scratch and holds an arbitrary candidate's result afterwards.
+ * Each candidate is timed as the median of single launches that each follow an unrelated
+ * 32 MB device fill, as a launch runs inside a larger step.
+ * `out` is used as scratch and holds an arbitrary candidate's result afterwards; the call
+ * also allocates and frees a 32 MB spacer buffer.
  * `path` restricts the search (AUTO = all eligible paths).  Synchronizes `stream`.
  * The chosen tuning is written to *chosen if non-NULL.
  */

@@ -20,7 +20,8 @@ LIBDIR = os.path.join(HERE, "_lib")
 LIB_PATH = os.path.join(LIBDIR, "libpg.so")
 
 SOURCES = ["pg_api.cpp", "pg_direct.cu", "pg_direct_integral.cu", "pg_backward.cu",
-           "pg_separable.cu", "pg_tune.cu", "pg_noalloc.cu", "pg_refine.cu", "pg_cell.cu"]
+           "pg_separable.cu", "pg_tune.cu", "pg_noalloc.cu", "pg_refine.cu", "pg_cell.cu",
+           "pg_direct_weighted.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

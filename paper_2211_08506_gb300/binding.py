@@ -77,13 +77,15 @@ class pg_tuning(ctypes.Structure):
         ("gather_only", ctypes.c_int32),
         ("chunk_planes", ctypes.c_int32),
         ("separable_simple", ctypes.c_int32),
+        ("chunk_order", ctypes.c_int32),
     ]
 
     def as_dict(self):
         return {"path": self.path, "block_threads": self.block_threads,
                 "blocks_per_sm": self.blocks_per_sm, "store_hint": self.store_hint,
                 "n_tile": self.n_tile, "gather_only": self.gather_only,
-                "chunk_planes": self.chunk_planes, "separable_simple": self.separable_simple}
+                "chunk_planes": self.chunk_planes, "separable_simple": self.separable_simple,
+                "chunk_order": self.chunk_order}
 
 
 _lock = threading.Lock()

@@ -431,7 +431,9 @@ __device__ __forceinline__ void scatter_plane(T *out, int *acc_i, int *run_off, 
     __syncwarp();
 }
 
-template <typename T, int VEC, int CUT, bool PER, int HINT, bool SCAT, int FORM>
+// WGT: per-atom weights (weighted grids).  Unweighted batches run the instantiation without
+// them, which carries no weight loads, shuffles or multiplies.
+template <typename T, int VEC, int CUT, bool PER, int HINT, bool SCAT, int FORM, bool WGT>
 __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel(const DirectArgs A)
 {
     extern __shared__ float4 smem_all[];
@@ -488,13 +490,20 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
         if (lane == 0) chunk = atomicAdd(A.sched, 1ull);
         chunk = __shfl_sync(0xffffffffu, chunk, 0);
         if (chunk >= n_chunks) break;
-        // Chunks run channel-major: channel 0 of every molecule first.  Channels listed by
-        // decreasing atom frequency then hand out the largest chunks first, which shortens
-        // the tail of uneven batches.  The output item is still (molecule, channel, x).
-        const unsigned long long cb = chunk / (unsigned)x_chunks;
-        const int xc = (int)(chunk - cb * x_chunks);
-        const int c = (int)(cb / (unsigned)G.n_mol);
-        const int b = (int)(cb - (unsigned long long)c * G.n_mol);
+        // Chunk order 0 walks (molecule, channel) in memory order, so concurrent stores stay
+        // close together; order 1 runs channel-major (channel 0 of every molecule first),
+        // which hands out the largest chunks first when channels are listed by decreasing
+        // atom frequency.  The output item is (molecule, channel, x) either way.
+        const unsigned long long grid_q = chunk / (unsigned)x_chunks;
+        const int xc = (int)(chunk - grid_q * x_chunks);
+        int b, c;
+        if (A.chunk_order) {
+            c = (int)(grid_q / (unsigned)G.n_mol);
+            b = (int)(grid_q - (unsigned long long)c * G.n_mol);
+        } else {
+            b = (int)(grid_q / (unsigned)G.C);
+            c = (int)(grid_q - (unsigned long long)b * G.C);
+        }
         const unsigned long long bc = (unsigned long long)b * G.C + c;
         const int x_begin = xc * chunk_planes;
         const int x_end = min(G.nx, x_begin + chunk_planes);
@@ -529,7 +538,7 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
             if (small && a0 + lane < a1) {
                 const int ai = a0 + lane;
                 my_e = __ldg(A.in.elem + ai);
-                my_w = A.in.weight ? __ldg(A.in.weight + ai) : 1.0f;
+                if (WGT) my_w = __ldg(A.in.weight + ai);
                 my_x = __ldg(A.in.coords + 3 * ai);
                 my_y = __ldg(A.in.coords + 3 * ai + 1);
                 my_z = __ldg(A.in.coords + 3 * ai + 2);
@@ -557,7 +566,7 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                     aw[h] = 1.0f;
                     if (ai < a1) {
                         e[h] = __ldg(A.in.elem + ai);
-                        if (A.in.weight) aw[h] = __ldg(A.in.weight + ai);
+                        if (WGT) aw[h] = __ldg(A.in.weight + ai);
                         ax[h] = __ldg(A.in.coords + 3 * ai);
                         ay[h] = __ldg(A.in.coords + 3 * ai + 1);
                         az[h] = __ldg(A.in.coords + 3 * ai + 2);
@@ -610,7 +619,7 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                                 f(__shfl_sync(0xffffffffu, dx, src),
                                   __shfl_sync(0xffffffffu, my_y, src),
                                   __shfl_sync(0xffffffffu, my_z, src),
-                                  __shfl_sync(0xffffffffu, my_w, src));
+                                  WGT ? __shfl_sync(0xffffffffu, my_w, src) : 1.0f);
                             }
                         });
                 } else {
@@ -645,7 +654,7 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                                 const float sdx = __shfl_sync(0xffffffffu, dx, src);
                                 const float sy = __shfl_sync(0xffffffffu, my_y, src);
                                 const float sz = __shfl_sync(0xffffffffu, my_z, src);
-                                const float sw = __shfl_sync(0xffffffffu, my_w, src);
+                                const float sw = WGT ? __shfl_sync(0xffffffffu, my_w, src) : 1.0f;
                                 lv.add(sdx, sy, sz, sw, q, r2, kf, hx, hy, hz, Ly, iLy, Lz,
                                        iLz);
                             }
@@ -671,7 +680,7 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                         const float4 a = chan[j];
                         ay = a.y;
                         az = a.z;
-                        aw = a.w;
+                        if (WGT) aw = a.w;
                         dx = vx - a.x;
                         if (PER) dx = wrap(dx, Lx, iLx);
                         ok = (CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc);
@@ -687,7 +696,7 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                     if (ai < a1) {
                         // Loads issued together, used after.
                         const int e = __ldg(A.in.elem + ai);
-                        if (A.in.weight) aw = __ldg(A.in.weight + ai);
+                        if (WGT) aw = __ldg(A.in.weight + ai);
                         const float ax = __ldg(A.in.coords + 3 * ai);
                         ay = __ldg(A.in.coords + 3 * ai + 1);
                         az = __ldg(A.in.coords + 3 * ai + 2);
@@ -730,7 +739,7 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                                     const int src = __ffs(m) - 1;
                                     m &= m - 1;
                                     const float4 st = stage[cb + src];
-                                    f(st.x, st.y, st.z, st.w);
+                                    f(st.x, st.y, st.z, WGT ? st.w : 1.0f);
                                 }
                             }
                         });
@@ -771,8 +780,8 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                                     const int src = __ffs(m) - 1;
                                     m &= m - 1;
                                     const float4 st = stage[cb + src];
-                                    lv.add(st.x, st.y, st.z, st.w, q, r2, kf, hx, hy, hz, Ly, iLy,
-                                           Lz, iLz);
+                                    lv.add(st.x, st.y, st.z, WGT ? st.w : 1.0f, q, r2, kf, hx, hy,
+                                           hz, Ly, iLy, Lz, iLz);
                                 }
                             }
                         } else {
@@ -782,7 +791,7 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                                 bool ok = false;
                                 float dx = 0.0f, ay = 0.0f, az = 0.0f, aw = 1.0f;
                                 if (ai < a1 && __ldg(A.in.elem + ai) == c) {
-                                    if (A.in.weight) aw = __ldg(A.in.weight + ai);
+                                    if (WGT) aw = __ldg(A.in.weight + ai);
                                     const float ax = __ldg(A.in.coords + 3 * ai);
                                     ay = __ldg(A.in.coords + 3 * ai + 1);
                                     az = __ldg(A.in.coords + 3 * ai + 2);
@@ -799,7 +808,7 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                                     const float sdx = __shfl_sync(0xffffffffu, dx, src);
                                     const float sy = __shfl_sync(0xffffffffu, ay, src);
                                     const float sz = __shfl_sync(0xffffffffu, az, src);
-                                    const float sw = __shfl_sync(0xffffffffu, aw, src);
+                                    const float sw = WGT ? __shfl_sync(0xffffffffu, aw, src) : 1.0f;
                                     lv.add(sdx, sy, sz, sw, q, r2, kf, hx, hy, hz, Ly, iLy, Lz,
                                            iLz);
                                 }
@@ -840,8 +849,8 @@ template <typename T, int VEC, int CUT, bool PER, int HINT, int FORM>
 const void *pick_scat(bool scat)
 {
     if constexpr (CUT != PG_CUTOFF_NONE && FORM == 0)
-        if (scat) return (const void *)direct_kernel<T, VEC, CUT, PER, HINT, true, FORM>;
-    return (const void *)direct_kernel<T, VEC, CUT, PER, HINT, false, FORM>;
+        if (scat) return (const void *)direct_kernel<T, VEC, CUT, PER, HINT, true, FORM, false>;
+    return (const void *)direct_kernel<T, VEC, CUT, PER, HINT, false, FORM, false>;
 }
 
 template <typename T, int VEC, int CUT, bool PER, int FORM>
@@ -864,6 +873,37 @@ const void *pick_shape(int cutoff, int periodic, int hint, bool scat)
         return pick_hint<T, VEC, PG_CUTOFF_SPHERE, false, FORM>(hint, scat);
     if (cutoff == PG_CUTOFF_BOX) return pick_hint<T, VEC, PG_CUTOFF_BOX, false, FORM>(hint, scat);
     return pick_hint<T, VEC, PG_CUTOFF_NONE, false, FORM>(hint, scat);
+}
+
+// Weighted instantiations: gather mode (scatter mode assumes unit terms) and default stores.
+template <typename T, int VEC, int FORM>
+const void *pick_weighted_shape(int cutoff, int periodic)
+{
+    if (periodic) {
+        if (cutoff == PG_CUTOFF_SPHERE)
+            return (const void *)direct_kernel<T, VEC, PG_CUTOFF_SPHERE, true, 0, false, FORM, true>;
+        if (cutoff == PG_CUTOFF_BOX)
+            return (const void *)direct_kernel<T, VEC, PG_CUTOFF_BOX, true, 0, false, FORM, true>;
+        return (const void *)direct_kernel<T, VEC, PG_CUTOFF_NONE, true, 0, false, FORM, true>;
+    }
+    if (cutoff == PG_CUTOFF_SPHERE)
+        return (const void *)direct_kernel<T, VEC, PG_CUTOFF_SPHERE, false, 0, false, FORM, true>;
+    if (cutoff == PG_CUTOFF_BOX)
+        return (const void *)direct_kernel<T, VEC, PG_CUTOFF_BOX, false, 0, false, FORM, true>;
+    return (const void *)direct_kernel<T, VEC, PG_CUTOFF_NONE, false, 0, false, FORM, true>;
+}
+
+template <int FORM>
+const void *pick_weighted(int dtype, bool vec_ok, int cut, int per)
+{
+    if (dtype == PG_F32)
+        return vec_ok ? pick_weighted_shape<float, 4, FORM>(cut, per)
+                      : pick_weighted_shape<float, 1, FORM>(cut, per);
+    if (dtype == PG_F16)
+        return vec_ok ? pick_weighted_shape<__half, 8, FORM>(cut, per)
+                      : pick_weighted_shape<__half, 1, FORM>(cut, per);
+    return vec_ok ? pick_weighted_shape<__nv_bfloat16, 8, FORM>(cut, per)
+                  : pick_weighted_shape<__nv_bfloat16, 1, FORM>(cut, per);
 }
 
 // The instantiation for one launch: dtype, vector stores, cutoff, boundary, store hint,

@@ -268,6 +268,7 @@ pg_status plan_forward(const pg_batch *b, const pg_grid *g, int dtype, void *out
     a.sched = sched;
     a.plane_stride = direct_scatter_on(b, g, t) ? direct_plane_stride(g) : 0;
     a.chunk_planes = (t.chunk_planes >= 1 && t.chunk_planes <= 64) ? t.chunk_planes : 8;
+    a.chunk_order = t.chunk_order == 1 ? 1 : 0;
     a.geo = G;
     const int vec = vec_stores_ok(out, g, dtype) ? 1 : 0;
     if (b->cell) {
@@ -767,26 +768,30 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
         // The general-cell kernel has a fixed block and no store hint or scatter mode: only
         // the residency and the chunk size vary.
         if (batch->cell)
-            for (int bps : {0, 1, 2})
-                for (int cp : {1, 2, 4, 8, 16}) {
-                    pg_tuning t = default_tuning(PG_PATH_DIRECT);
-                    t.blocks_per_sm = bps;
-                    t.chunk_planes = cp;
-                    cands.push_back(t);
-                }
-        for (int threads : {256, 512})
-            for (int bps : {0, 1, 2})
-                for (int hint : {0, 1})
-                    for (int cp : {1, 2, 4, 8})
-                        for (int go = 0; go <= go_max && !batch->cell; ++go) {
-                            pg_tuning t = default_tuning(PG_PATH_DIRECT);
-                            t.block_threads = threads;
-                            t.blocks_per_sm = bps;
-                            t.store_hint = hint;
-                            t.chunk_planes = cp;
-                            t.gather_only = go;
-                            cands.push_back(t);
-                        }
+            for (int order : {0, 1})
+                for (int bps : {0, 1, 2})
+                    for (int cp : {1, 2, 4, 8, 16}) {
+                        pg_tuning t = default_tuning(PG_PATH_DIRECT);
+                        t.blocks_per_sm = bps;
+                        t.chunk_planes = cp;
+                        t.chunk_order = order;
+                        cands.push_back(t);
+                    }
+        for (int order : {0, 1})
+            for (int threads : {256, 512})
+                for (int bps : {0, 1, 2})
+                    for (int hint : {0, 1})
+                        for (int cp : {1, 2, 4, 8})
+                            for (int go = 0; go <= go_max && !batch->cell; ++go) {
+                                pg_tuning t = default_tuning(PG_PATH_DIRECT);
+                                t.block_threads = threads;
+                                t.blocks_per_sm = bps;
+                                t.store_hint = hint;
+                                t.chunk_planes = cp;
+                                t.gather_only = go;
+                                t.chunk_order = order;
+                                cands.push_back(t);
+                            }
     }
     Geometry G;
     make_geometry(batch, grid, &G);
@@ -817,12 +822,15 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
     const size_t sample_elems = per_mol * n_sample;
     const size_t esz = dtype_size(out_dtype);
     void *sample = nullptr;
+    void *spacer = nullptr;
+    constexpr size_t kSpacerBytes = 32u << 20;
     unsigned long long *d_hash = nullptr;
     float *d_cmp = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     std::vector<float> times(cands.size(), INFINITY);
     auto cleanup = [&]() {
         cudaFree(sample);
+        cudaFree(spacer);
         cudaFree(d_hash);
         cudaFree(d_cmp);
         if (e0) cudaEventDestroy(e0);
@@ -834,6 +842,7 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
         return cuda_fail(e, what);
     };
     if ((st = cu(cudaMalloc(&sample, sample_elems * esz), "cudaMalloc(tune sample)"))) return st;
+    if ((st = cu(cudaMalloc(&spacer, kSpacerBytes), "cudaMalloc(tune spacer)"))) return st;
     if ((st = cu(cudaMalloc(&d_hash, sizeof(unsigned long long)), "cudaMalloc"))) return st;
     if ((st = cu(cudaMalloc(&d_cmp, 2 * sizeof(float)), "cudaMalloc"))) return st;
     if ((st = cu(cudaEventCreate(&e0), "cudaEventCreate"))) return st;
@@ -891,24 +900,20 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
             pass = cmp[0] <= tol * cmp[1];
         }
         if (!pass) continue;
-        // Time: median over 5 batches of back-to-back launches, each batch >= ~0.5 ms.
-        float first = 0.0f;
-        if ((st = cu(cudaEventRecord(e0, s), "event"))) return st;
-        if ((st = cu(launch(kl, s), "tune launch"))) return st;
-        if ((st = cu(cudaEventRecord(e1, s), "event"))) return st;
-        if ((st = cu(cudaEventSynchronize(e1), "event sync"))) return st;
-        if ((st = cu(cudaEventElapsedTime(&first, e0, e1), "elapsed"))) return st;
-        const int per_batch = std::max(1, std::min(64, (int)(0.5f / std::max(first, 1e-3f))));
+        // Time: median of 7 single launches, each after an unrelated fill of the spacer
+        // buffer (outside the timed events).  That is how a launch runs in a training step,
+        // a graph replay between other kernels or a plan run.  Back-to-back launches of one
+        // candidate measured small chunks faster than they run there.
         std::vector<float> ms;
-        for (int r = 0; r < 5; ++r) {
+        for (int r = 0; r < 7; ++r) {
+            if ((st = cu(cudaMemsetAsync(spacer, r, kSpacerBytes, s), "spacer"))) return st;
             if ((st = cu(cudaEventRecord(e0, s), "event"))) return st;
-            for (int k = 0; k < per_batch; ++k)
-                if ((st = cu(launch(kl, s), "tune launch"))) return st;
+            if ((st = cu(launch(kl, s), "tune launch"))) return st;
             if ((st = cu(cudaEventRecord(e1, s), "event"))) return st;
             if ((st = cu(cudaEventSynchronize(e1), "event sync"))) return st;
             float t = 0;
             if ((st = cu(cudaEventElapsedTime(&t, e0, e1), "elapsed"))) return st;
-            ms.push_back(t / per_batch);
+            ms.push_back(t);
         }
         std::sort(ms.begin(), ms.end());
         times[i] = ms[ms.size() / 2];
@@ -960,7 +965,7 @@ pg_status pg_tuning_save(const char *file)
         f << kv.first << ' ' << kv.second.path << ' ' << kv.second.block_threads << ' '
           << kv.second.blocks_per_sm << ' ' << kv.second.store_hint << ' ' << kv.second.n_tile
           << ' ' << kv.second.gather_only << ' ' << kv.second.chunk_planes << ' '
-          << kv.second.separable_simple << '\n';
+          << kv.second.separable_simple << ' ' << kv.second.chunk_order << '\n';
     return PG_OK;
 }
 
@@ -984,6 +989,7 @@ pg_status pg_tuning_load(const char *file)
         if (!(is >> t.gather_only)) t.gather_only = 0;
         if (!(is >> t.chunk_planes)) t.chunk_planes = 8;
         if (!(is >> t.separable_simple)) t.separable_simple = 0;
+        if (!(is >> t.chunk_order)) t.chunk_order = 0;
         add[key] = t;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);

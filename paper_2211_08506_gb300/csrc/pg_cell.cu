@@ -15,7 +15,7 @@
 // nearest image is not found by rounding in a skewed cell, and the host rejects that case.
 //
 // Forward kernel.  Work items are (molecule, channel, x-plane) as in the direct kernel,
-// handed out in chunks of planes from a per-launch counter.  Per chunk a warp stages the
+// handed out in chunks of planes from a per-launch counter, in either chunk order.  Per chunk a warp stages the
 // channel's atoms as {p, w}.  Per plane it keeps the candidates within the cutoff's
 // fractional reach of the plane as {e_x a, w} and {p_y, p_z}.  For a lane's voxels of row j
 // the displacement is d = base + e_z c with base = e_x a + e_y b, so
@@ -142,13 +142,20 @@ __global__ void __launch_bounds__(kCellThreads) cell_kernel(const DirectArgs A)
         if (lane == 0) chunk = atomicAdd(A.sched, 1ull);
         chunk = __shfl_sync(0xffffffffu, chunk, 0);
         if (chunk >= n_chunks) break;
-        // Chunks run channel-major: channel 0 of every molecule first.  Channels listed by
-        // decreasing atom frequency then hand out the largest chunks first, which shortens
-        // the tail of uneven batches.  The output item is still (molecule, channel, x).
-        const unsigned long long cb = chunk / (unsigned)x_chunks;
-        const int xc = (int)(chunk - cb * x_chunks);
-        const int c = (int)(cb / (unsigned)G.n_mol);
-        const int b = (int)(cb - (unsigned long long)c * G.n_mol);
+        // Chunk order 0 walks (molecule, channel) in memory order, so concurrent stores stay
+        // close together; order 1 runs channel-major (channel 0 of every molecule first),
+        // which hands out the largest chunks first when channels are listed by decreasing
+        // atom frequency.  The output item is (molecule, channel, x) either way.
+        const unsigned long long grid_q = chunk / (unsigned)x_chunks;
+        const int xc = (int)(chunk - grid_q * x_chunks);
+        int b, c;
+        if (A.chunk_order) {
+            c = (int)(grid_q / (unsigned)G.n_mol);
+            b = (int)(grid_q - (unsigned long long)c * G.n_mol);
+        } else {
+            b = (int)(grid_q / (unsigned)G.C);
+            c = (int)(grid_q - (unsigned long long)b * G.C);
+        }
         const unsigned long long bc = (unsigned long long)b * G.C + c;
         const int x_begin = xc * chunk_planes;
         const int x_end = min(G.nx, x_begin + chunk_planes);

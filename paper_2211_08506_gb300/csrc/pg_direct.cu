@@ -11,7 +11,8 @@ cudaError_t direct_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tun
     const int hint = t.store_hint == 1 ? 1 : 0;
     const bool scat = a.plane_stride > 0 && a.geo.cutoff != PG_CUTOFF_NONE;
     const int cut = a.geo.cutoff, per = a.geo.periodic;
-    const void *f = a.geo.form == PG_FORM_INTEGRAL
+    const void *f = a.in.weight ? pick_direct_weighted(dtype, vec_ok != 0, cut, per, a.geo.form)
+                    : a.geo.form == PG_FORM_INTEGRAL
                         ? pick_direct_integral(dtype, vec_ok != 0, cut, per, hint)
                         : pick_direct<0>(dtype, vec_ok != 0, cut, per, hint, scat);
 

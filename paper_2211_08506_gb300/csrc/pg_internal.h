@@ -81,6 +81,7 @@ struct DirectArgs {
     unsigned long long *sched;  // {next chunk, retired warps}; zero between launches
     int plane_stride;           // floats of per-warp plane buffer for scatter mode (0: off)
     int chunk_planes;           // x-planes per dynamically scheduled chunk (>= 1)
+    int chunk_order;            // 0: (molecule, channel) order; 1: channel-major
     Geometry geo;
 };
 
@@ -131,8 +132,10 @@ cudaError_t refine_update(float *coords, const float *grad, const int *mol_off, 
                           int n_atoms, const float *loss, int *steps, float lr, float eps,
                           cudaStream_t s);
 
-// The direct kernel's voxel-integrated instantiation for one launch (pg_direct_integral.cu).
+// The direct kernel's voxel-integrated instantiation for one launch (pg_direct_integral.cu),
+// and its weighted instantiations, either voxel form (pg_direct_weighted.cu).
 const void *pick_direct_integral(int dtype, bool vec_ok, int cutoff, int periodic, int hint);
+const void *pick_direct_weighted(int dtype, bool vec_ok, int cutoff, int periodic, int form);
 cudaError_t direct_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tuning &t,
                         int sm_count, KernelLaunch *kl);
 

@@ -103,7 +103,7 @@ def test_tuning_cache_file_round_trip(lib, tmp_path):
     assert lib.pg_tuning_load(str(f)) == 0
     out = tmp_path / "out.txt"
     assert lib.pg_tuning_save(str(out)) == 0
-    assert "path0 1 256 2 1 128 0 8 0" in out.read_text()
+    assert "path0 1 256 2 1 128 0 8 0 0" in out.read_text()
     bad = tmp_path / "bad.txt"
     bad.write_text("key only\n")
     assert lib.pg_tuning_load(str(bad)) == lib.PG_ERR_INVALID_ARG
