@@ -689,7 +689,8 @@ def run_profile(args, wl, dtype):
     out = torch.empty(grid.out_shape(wl.batch.n_mol), dtype=api.DTYPES[dtype][1], device="cuda")
     tuning = {"path": 2 if args.path == "separable" else 1, "block_threads": args.threads,
               "blocks_per_sm": 0, "store_hint": args.store_hint, "n_tile": args.n_tile,
-              "chunk_planes": args.chunk_planes, "gather_only": args.gather_only}
+              "chunk_planes": args.chunk_planes, "gather_only": args.gather_only,
+              "chunk_order": args.chunk_order}
     W = grad = None
     if wl.name == "differentiation":
         W = torch.from_numpy(synth.loss_weights(wl)).cuda()
@@ -724,6 +725,8 @@ def main():
     ap.add_argument("--threads", type=int, default=512, help="--profile: threads per CTA")
     ap.add_argument("--store-hint", type=int, default=1, help="--profile: 1 = streaming stores")
     ap.add_argument("--chunk-planes", type=int, default=8, help="--profile: planes per chunk")
+    ap.add_argument("--chunk-order", type=int, default=0,
+                    help="--profile: 0 = molecule-major chunks, 1 = channel-major")
     ap.add_argument("--gather-only", type=int, default=0, help="--profile: 1 = no scatter mode")
     ap.add_argument("--n-tile", type=int, default=128, help="--profile: separable tile width")
     args = ap.parse_args()
