@@ -296,3 +296,21 @@ def test_scatter_and_gather_modes_on_dense_cells(pg):
         assert np.array_equal(gather, g512)
     grid_check(auto[:6], oracle.Problem.from_workload(wl, batch=wl.batch.subset(range(6))),
                TOL["f16"], abs_tol=ABS_TOL["f16"])
+
+
+@pytest.mark.parametrize("kind", ["qm9", "crystal", "triclinic"])
+def test_chunk_orders_give_identical_bits(pg, kind):
+    # Molecule-major and channel-major chunk orders visit each voxel's atoms in the same
+    # order, so the grids are bitwise equal (direct and general-cell kernels).
+    wl = {"qm9": lambda: synth.qm9_shaped(n_mol=32),
+          "crystal": lambda: synth.crystal_shaped(n_cells=6, grid=24),
+          "triclinic": lambda: synth.crystal_triclinic(n_cells=6)}[kind]()
+    db = pg.DeviceBatch.from_numpy(wl.batch)
+    grid = pg.Grid.from_workload(wl)
+    outs = []
+    for order in (0, 1):
+        outs.append(pg.voxelize_tuned(db, grid, {"path": 1, "block_threads": 256,
+                                                 "chunk_planes": 4, "chunk_order": order},
+                                      dtype="f16"))
+    assert pg.sync_status() == 0
+    assert torch.equal(outs[0], outs[1])
