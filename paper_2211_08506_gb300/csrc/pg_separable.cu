@@ -622,12 +622,12 @@ constexpr int kPipeStages = 2;
 constexpr int kPipeThreads = 288;  // 9 warps
 
 struct PipeLayout {
-    int bars, tmem, flag, atoms, stage0, stage_bytes, a_bytes, aslots, gx, gy, gz, out, out_stride,
-        total;
+    int bars, tmem, flag, tile, atoms, stage0, stage_bytes, a_bytes, aslots, gx, gy, gz, out,
+        out_stride, total;
 };
 
 __host__ __device__ inline PipeLayout pipe_layout(int nx, int ny, int nz, int n_tile, int esz,
-                                               int kslots)
+                                               int kslots, int pack)
 {
     PipeLayout L;
     int o = 0;
@@ -637,6 +637,10 @@ __host__ __device__ inline PipeLayout pipe_layout(int nx, int ny, int nz, int n_
     o += 8;
     L.flag = o;
     o += 8;
+    o = align_up(o, 16);
+    // Packed tiles: the tile's CSR offsets (pack + 1) and each molecule's origin and spacing.
+    L.tile = o;
+    o += pack > 0 ? (pack + 1) * 4 + pack * 24 : 0;
     o = align_up(o, 128);
     L.atoms = o;
     o += kKC * 4 * 16;  // the K chunk being built: pos, aux, geometry (2)
@@ -789,7 +793,8 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
     const int warp = tid >> 5;
     const int lane = tid & 31;
     const int n_tile = A.n_tile;
-    const PipeLayout L = pipe_layout(G.nx, G.ny, G.nz, n_tile, (int)sizeof(T), A.kslots);
+    const PipeLayout L = pipe_layout(G.nx, G.ny, G.nz, n_tile, (int)sizeof(T), A.kslots,
+                                     PACK ? A.pack : 0);
     const uint32_t bars = smem_u32(smem + L.bars);
     auto b_full = [&](int s) { return bars + 8u * s; };
     auto b_empty = [&](int s) { return bars + 8u * (2 + s); };
@@ -853,6 +858,21 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
             // The row's voxel-centre x for a one-molecule tile (packed tiles take it from the
             // atom's own molecule below).
             const float vx_item = fmaf((float)row_x + 0.5f, it.hx, it.ox);
+            // Packed tiles: the molecules' offsets and geometry, read once per tile so that
+            // staging a K chunk needs no dependent global loads.  The barrier orders these
+            // writes after every producer's use of the previous tile's; the barrier that opens
+            // the first chunk's staging orders them before the reads.
+            int *const t_off = reinterpret_cast<int *>(smem + L.tile);
+            float *const t_geo = reinterpret_cast<float *>(t_off + (PACK ? A.pack + 1 : 0));
+            if (PACK) {
+                producer_sync();
+                for (int k = p; k <= it.nb; k += 128) t_off[k] = __ldg(A.in.mol_off + it.b + k);
+                for (int k = p; k < 6 * it.nb; k += 128) {
+                    const int m = it.b + k / 6, f = k % 6;
+                    t_geo[k] = f < 3 ? __ldg(A.in.origin + 3 * m + f)
+                                     : __ldg(A.in.spacing + 3 * m + f - 3);
+                }
+            }
             for (int nc = 0; nc < n_chunks && ok; ++nc) {
                 const int n0 = nc * n_tile;
                 for (int kc = 0; kc < it.n_kc && ok; ++kc, ++step) {
@@ -898,6 +918,12 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             float4 g0 = make_float4(0.f, 0.f, 0.f, 1.f);
                             float4 g1 = make_float4(1.f, 1.f, 1.f, 0.f);
                             if (ai < it.a1) {
+                                // Loads issued together, used after.
+                                const int e = __ldg(A.in.elem + ai);
+                                const float cx = __ldg(A.in.coords + 3 * ai),
+                                            cy = __ldg(A.in.coords + 3 * ai + 1),
+                                            cz = __ldg(A.in.coords + 3 * ai + 2);
+                                const float wgt = A.in.weight ? __ldg(A.in.weight + ai) : 1.0f;
                                 // The atom's molecule: the item's, or in a packed tile the last
                                 // k with mol_off[b + k] <= ai.
                                 int k = 0;
@@ -905,19 +931,15 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                                     int lo = 0, hi = it.nb - 1;
                                     while (lo < hi) {
                                         const int mid = (lo + hi + 1) >> 1;
-                                        if (__ldg(A.in.mol_off + it.b + mid) <= ai) lo = mid;
+                                        if (t_off[mid] <= ai) lo = mid;
                                         else hi = mid - 1;
                                     }
                                     k = lo;
                                 }
-                                const int mb = it.b + k;
                                 if (PACK) {
-                                    g0 = make_float4(__ldg(A.in.origin + 3 * mb),
-                                                     __ldg(A.in.origin + 3 * mb + 1),
-                                                     __ldg(A.in.origin + 3 * mb + 2),
-                                                     __ldg(A.in.spacing + 3 * mb));
-                                    g1 = make_float4(__ldg(A.in.spacing + 3 * mb + 1),
-                                                     __ldg(A.in.spacing + 3 * mb + 2), 1.f, 0.f);
+                                    const float *gk = t_geo + 6 * k;
+                                    g0 = make_float4(gk[0], gk[1], gk[2], gk[3]);
+                                    g1 = make_float4(gk[4], gk[5], 1.f, 0.f);
                                 } else {
                                     g0 = make_float4(it.ox, it.oy, it.oz, it.hx);
                                     g1 = make_float4(it.hy, it.hz, 1.f, 0.f);
@@ -925,16 +947,13 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                                 const bool sp_ok = g0.w > 0.0f && g1.x > 0.0f && g1.y > 0.0f &&
                                                    g0.w < INFINITY && g1.x < INFINITY &&
                                                    g1.y < INFINITY;
-                                const int e = __ldg(A.in.elem + ai);
                                 if (!sp_ok) {
-                                    if (ai == __ldg(A.in.mol_off + mb))
+                                    if (ai == (PACK ? t_off[k] : it.a0))
                                         atomicOr(A.err, PG_DEVERR_SPACING);
                                 } else if ((unsigned)e < (unsigned)G.C) {
-                                    pos = make_float4(__ldg(A.in.coords + 3 * ai),
-                                                      __ldg(A.in.coords + 3 * ai + 1),
-                                                      __ldg(A.in.coords + 3 * ai + 2), G.q[e]);
+                                    pos = make_float4(cx, cy, cz, G.q[e]);
                                     aux = make_float4(G.r2[e], (float)e, G.kerf[e], (float)k);
-                                    if (A.in.weight) g1.z = __ldg(A.in.weight + ai);
+                                    g1.z = wgt;
                                 } else if (it.m0 == 0) {
                                     atomicOr(A.err, PG_DEVERR_ELEMENT);
                                 }
@@ -955,6 +974,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             const int pw = p >> 5;
                             auto erf_table = [&](float *tab, int n, int stride, int axis) {
                                 const int blocks = (n + 31) >> 5;
+#pragma unroll 2
                                 for (int task = pw; task < kKC * blocks; task += 4) {
                                     const int j = task % kKC, i = (task / kKC) * 32 + lane;
                                     const float4 q4 = atom_pos[j];
@@ -1312,7 +1332,7 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
     int kslots = (int)std::ceil(2.0 * atoms_per_tile / kKC);
     kslots = kslots < 1 ? 1 : (kslots > 8 ? 8 : kslots);
     auto bytes = [&](int nt, int ks) {
-        return pipe ? pipe_layout(a.geo.nx, a.geo.ny, a.geo.nz, nt, esz, ks).total
+        return pipe ? pipe_layout(a.geo.nx, a.geo.ny, a.geo.nz, nt, esz, ks, a.pack).total
                     : sep_layout(a.geo.ny, a.geo.nz, nt, esz).total;
     };
     const int budget = (pipe && t.blocks_per_sm >= 2) ? 228 * 1024 / t.blocks_per_sm - 1024
