@@ -100,6 +100,11 @@ class DeviceBatch:
                    None if w is None else f(w, torch.float32),
                    None if m is None else f(m, torch.float32))
 
+    def with_weight(self, weight) -> "DeviceBatch":
+        """The same batch with other per-atom weights (float32 [N], CUDA), tensors shared."""
+        return DeviceBatch(self.coords, self.elem, self.mol_off, self.origin, self.spacing,
+                           weight, self.cell)
+
     @property
     def n_mol(self) -> int:
         return int(self.mol_off.numel() - 1)
@@ -272,26 +277,35 @@ class Plan:
 
 
 class Voxelize(torch.autograd.Function):
-    """G = voxelize(coords); dL/dcoords through the hand-written adjoint kernel.  The grid
-    is recomputed from the saved inputs, nothing else is kept."""
+    """G = voxelize(coords, weight); dL/dcoords (and dL/dweight for a weighted grid) through
+    the hand-written adjoint kernel.  Only the inputs are saved."""
 
     @staticmethod
-    def forward(ctx, coords, batch: DeviceBatch, grid: Grid, dtype: str, path: str):
+    def forward(ctx, coords, weight, batch: DeviceBatch, grid: Grid, dtype: str, path: str):
         coords = coords.contiguous()
+        if weight is not None:
+            batch = batch.with_weight(weight.contiguous())
         out = voxelize(batch, grid, dtype=dtype, path=path, coords=coords)
         ctx.save_for_backward(coords)
         ctx.batch = batch
         ctx.grid = grid
+        ctx.weighted = weight is not None
         return out
 
     @staticmethod
     def backward(ctx, grad_out):
         (coords,) = ctx.saved_tensors
+        if ctx.weighted and ctx.needs_input_grad[1]:
+            g, gw = voxelize_backward_weights(ctx.batch, ctx.grid, grad_out,
+                                              with_coords=ctx.needs_input_grad[0], coords=coords)
+            return g, gw, None, None, None, None
         g = voxelize_backward(ctx.batch, ctx.grid, grad_out, coords=coords)
-        return g, None, None, None, None
+        return g, None, None, None, None, None
 
 
 def voxelize_autograd(coords: torch.Tensor, batch: DeviceBatch, grid: Grid,
-                      dtype: str = "f32", path: str = "auto") -> torch.Tensor:
-    """Differentiable voxelization with respect to `coords` ([N, 3] float32, CUDA)."""
-    return Voxelize.apply(coords, batch, grid, dtype, path)
+                      dtype: str = "f32", path: str = "auto",
+                      weight: torch.Tensor | None = None) -> torch.Tensor:
+    """Differentiable voxelization with respect to `coords` ([N, 3] float32, CUDA) and, when
+    given, the per-atom `weight` ([N] float32, CUDA; it replaces the batch's own weights)."""
+    return Voxelize.apply(coords, weight, batch, grid, dtype, path)

@@ -266,3 +266,26 @@ def test_full_size_triclinic_batch_sampled(pg):
     sub = wl.batch.subset(idx)
     grid_check(G[idx].float().cpu().numpy(), oracle.Problem.from_workload(wl, batch=sub),
                TOL["f16"], abs_tol=ABS_TOL["f16"])
+
+
+@pytest.mark.parametrize("kind", ["molecules", "triclinic"])
+def test_autograd_through_learnable_weights(pg, kind):
+    # L = <W, G(x, w)>: autograd returns dL/dx and dL/dw from the adjoint kernel, equal to the
+    # oracle's gradient and weight gradient.
+    if kind == "molecules":
+        wl = weighted(synth.qm9_shaped(n_mol=8), lo=-1.0, hi=2.0)
+    else:
+        wl = triclinic(n_cells=2, shape=(20, 20, 24))
+    db = pg.DeviceBatch.from_numpy(wl.batch)
+    grid = pg.Grid.from_workload(wl)
+    x = db.coords.clone().requires_grad_(True)
+    w = torch.as_tensor(wl.batch.weight, device="cuda").clone().requires_grad_(True)
+    prob = oracle.Problem.from_workload(wl)
+    W = np.random.default_rng(21).standard_normal(prob.shape).astype(np.float32)
+    G = pg.voxelize_autograd(x, db, grid, dtype="f32", path="direct", weight=w)
+    (torch.as_tensor(W, device="cuda") * G).sum().backward()
+    assert pg.sync_status() == 0
+    grad_check(x.grad.cpu().numpy(), oracle.gradient(prob, W.astype(np.float64)),
+               wl.batch.mol_off)
+    ref_w = oracle.gradient_weight(prob, W.astype(np.float64))
+    assert np.max(np.abs(w.grad.cpu().numpy() - ref_w)) <= GRAD_TOL * np.abs(ref_w).max()
