@@ -7,7 +7,7 @@ Tolerances (per molecule, relative to that molecule's largest oracle voxel value
               (~3e-7 relative), and fp32 summation of a handful of terms.
   f16  1e-3   round-to-nearest-even on store adds 2^-11 = 4.9e-4 relative per voxel.
   bf16 5e-3   round-to-nearest-even on store adds 2^-8 = 3.9e-3 relative per voxel.
-The spec bar for the half formats is 1e-2; these are tighter.
+The stated bar for the half formats is 1e-2; these are tighter.
 Voxels within a relative 1e-5 of the cutoff surface (the "band") may legitimately flip
 between inside and outside in fp32; each voxel is accepted anywhere in
 [G_in - tol, G_in + G_band + tol] and the band population is reported.
