@@ -214,9 +214,21 @@ def cpu_baseline(wl, budget_s=12.0, reps_cap=4):
         if sum(times) > budget_s:
             break
     best = min(times)
+    # The same oracle on one core, on a sample of about 3 s.
+    probe = wl.batch.subset(range(min(n, 4)))
+    t = time.perf_counter()
+    oracle.voxelize(oracle.Problem.from_workload(wl, batch=probe), "bbox", 1)
+    per_mol_1 = (time.perf_counter() - t) / max(1, probe.n_mol)
+    n1 = max(1, min(n, int(3.0 / max(per_mol_1, 1e-9))))
+    sub1 = wl.batch.subset(range(n1))
+    t = time.perf_counter()
+    oracle.voxelize(oracle.Problem.from_workload(wl, batch=sub1), "bbox", 1)
+    one = n1 / (time.perf_counter() - t)
     return {"value": n_sample / best, "unit": "grids/s", "cores": threads, "kind": "oracle",
             "sample": f"first {n_sample} molecules of the {wl.name} batch, FP64 support-box "
-                      f"oracle, OpenMP over molecules, best of {len(times)}"}
+                      f"oracle, OpenMP over molecules, best of {len(times)}",
+            "single_core": {"value": one, "unit": "grids/s", "cores": 1,
+                            "sample": f"first {n1} molecules, one thread"}}
 
 
 def run_reference(args):
