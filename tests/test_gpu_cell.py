@@ -289,3 +289,26 @@ def test_autograd_through_learnable_weights(pg, kind):
                wl.batch.mol_off)
     ref_w = oracle.gradient_weight(prob, W.astype(np.float64))
     assert np.max(np.abs(w.grad.cpu().numpy() - ref_w)) <= GRAD_TOL * np.abs(ref_w).max()
+
+
+def test_empty_cell_and_atoms_lattice_vectors_away(pg):
+    # A cell with no atoms writes zeros; atoms moved by whole lattice vectors (several cells
+    # away from the grid) give the same periodic grid.
+    wl = triclinic(n_cells=3, shape=(20, 24, 16))
+    b = wl.batch
+    keep = [0, 2]
+    atoms = np.concatenate([np.arange(b.mol_off[m], b.mol_off[m + 1]) for m in keep])
+    off = np.array([0, b.mol_off[1] - b.mol_off[0], b.mol_off[1] - b.mol_off[0],
+                    len(atoms)], np.int32)
+    shift = np.zeros((len(atoms), 3), np.float64)
+    n0 = int(off[1])
+    shift[n0:] = np.array([2.0, -3.0, 1.0]) @ b.cell[2].astype(np.float64)
+    wl.batch = synth.Batch(coords=(b.coords[atoms] + shift).astype(np.float32),
+                           elem=b.elem[atoms], mol_off=off, origin=b.origin, spacing=b.spacing,
+                           weight=b.weight[atoms], cell=b.cell)
+    G = run(pg, wl)
+    assert float(G[1].abs().max()) == 0.0
+    check(G, wl, "f32")
+    wl.batch.coords = (b.coords[atoms]).astype(np.float32)
+    G0 = run(pg, wl)
+    assert float((G - G0).abs().max()) <= 2 * TOL["f32"] * float(G0.abs().max())
