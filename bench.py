@@ -423,7 +423,8 @@ def run_ours(args):
     voxels = world * B * wl.voxels_per_grid / (ms / 1e3)
 
     # End to end through the public API: pinned host inputs -> plan (graph: H2D + kernel)
-    # -> device error word back to the host, every step.
+    # -> device error word back to the host, every step.  A differentiation step then runs
+    # the adjoint and reads the coordinate gradient back into pinned host memory.
     b = wl.batch
     pin = lambda a: None if a is None else torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
     host = [pin(a) for a in (b.coords, b.elem, b.mol_off, b.origin,
@@ -432,16 +433,29 @@ def run_ours(args):
     h2d = sum(t.numel() * t.element_size() for t in host + list(extra.values())
               if t is not None)
     plan = api.Plan(grid, dtype, max_mol=B, max_atoms=b.n_atoms, path=path)
+    grad_host = None
+    d2h = 4
+    if W is not None:
+        grad_host = torch.empty((b.n_atoms, 3), dtype=torch.float32).pin_memory()
+        d2h += grad_host.numel() * grad_host.element_size()
+
+    def e2e_step():
+        plan.run(*host, out=out, **extra)
+        if W is not None:
+            api.voxelize_backward(db, grid, W, grad_coords=grad, stream=stream)
+            grad_host.copy_(grad, non_blocking=True)
+            stream.synchronize()
+
     with torch.cuda.stream(stream):
         for _ in range(max(3, args.warmup)):
-            plan.run(*host, out=out, **extra)
+            e2e_step()
     e2e_steps = max(3, min(args.steps, 200))
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
         for _ in range(e2e_steps):
-            plan.run(*host, out=out, **extra)
+            e2e_step()
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     if dist:
         t = torch.tensor([e2e_s], device="cuda")
@@ -517,8 +531,9 @@ def run_ours(args):
             "value": world * B / e2e_s,
             "unit": "grids/s",
             "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": 4,
-            "api": "pg_plan_run (pinned host CSR batch -> graph: H2D + kernel -> error word D2H)",
+            "d2h_bytes_per_step": d2h,
+            "api": "pg_plan_run (pinned host CSR batch -> graph: H2D + kernel -> error word D2H)"
+                   + (" + pg_voxelize_backward -> gradient D2H" if W is not None else ""),
         },
         "gpu_launches": args.steps * (2 if graph_bwd is not None else 1),
         "clocks": sampler.summary(),
