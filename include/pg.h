@@ -98,6 +98,9 @@ typedef enum {
 #define PG_DEVERR_SPACING 0x4u   /* spacing <= 0 or not finite, or a singular cell matrix */
 #define PG_DEVERR_PERIODIC 0x8u  /* periodic cell whose cutoff reaches half a cell or more */
 #define PG_DEVERR_TIMEOUT 0x10u  /* a bounded wait on tensor-core completion gave up */
+#define PG_DEVERR_TMEM_HELD 0x20u /* with 0x10: a CTA could not confirm that its MMAs had
+                                     finished and kept its tensor memory instead of freeing it;
+                                     separable launches on the device are then refused */
 
 /*
  * A batch of B molecules in CSR form (Sec. V: points carry (channel, x, y, z); Sec. III-A:
@@ -322,24 +325,36 @@ void pg_shutdown(void);
  *
  * The paper has no counterpart: this serves callers that cannot let a library allocate.
  * The other entry points cudaMalloc a small per-device state the first time they run on a
- * device.  That is not possible while a stream capture in global mode is open elsewhere in
- * the process, nor acceptable when a framework's caching allocator or an external budget
- * owns all device memory, or when a host freezes its device-memory footprint after
- * start-up.  This call runs the direct kernel (same results, bit for bit, as
- * pg_voxelize with PG_PATH_DIRECT) with its scratch - the work counter and the error word -
- * in a fixed PG_NOALLOC_SCRATCH_BYTES array compiled into the library, which every GPU that
- * loads the library holds until the process exits.  A launch needs 20 bytes of it whatever
- * the batch size; a launch that needed more than the array holds would be rejected with
+ * device.  That is not possible while another thread holds a stream capture open in global
+ * mode (cudaMalloc is then refused and the capture is invalidated), and it is not acceptable
+ * when a framework's caching allocator or an external budget owns all device memory, or when
+ * a host freezes its device-memory footprint after start-up.  This call runs the direct
+ * kernel with its scratch - the work counter and the error word - in a fixed
+ * PG_NOALLOC_SCRATCH_BYTES array compiled into the library, which every GPU that loads the
+ * library holds until the process exits.  A launch needs 24 bytes of it whatever the batch
+ * size; a launch that needed more than the array holds would be rejected with
  * PG_ERR_INVALID_ARG.
+ * Results are identical, bit for bit, to pg_voxelize_tuned with the default launch of the
+ * direct path (a zeroed pg_tuning with path = PG_PATH_DIRECT), and so to pg_voxelize with
+ * PG_PATH_DIRECT: every launch choice of the direct path gives the same bits.
  *   batch, grid, out_dtype, out   as for pg_voxelize (DEVICE buffers, caller-owned)
- *   stream                        cudaStream_t as void* (NULL: legacy default stream)
+ *   stream                        cudaStream_t as void*, not capturing (a capturing stream
+ *                                 returns PG_ERR_INVALID_ARG: the call waits for its own
+ *                                 work).  While another thread holds a capture open, pass a
+ *                                 stream created with cudaStreamNonBlocking: work on the
+ *                                 legacy default stream (NULL) would depend implicitly on the
+ *                                 capturing stream and invalidate that capture.
  *   bits_out                      if non-NULL, receives the device error bits (PG_DEVERR_*)
- * Synchronous: clears the scratch, launches, copies the error word back into a host stack
- * variable and synchronizes `stream`; returns PG_ERR_DEVICE_VALIDATION if a bit was set.
+ * Synchronous without synchronizing calls (which a global-mode capture held by another thread
+ * refuses): it clears the scratch, launches, and copies the error word together with a
+ * completion marker into a static page-locked host word, then waits on the host until the
+ * marker arrives.  Returns PG_ERR_DEVICE_VALIDATION if an error bit was set, PG_ERR_TIMEOUT
+ * if the work has not finished after 600 s (it may still be running then).
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
- * with that device current; make that first call before any stream capture.  All calls
- * share the one array: calls that overlap on the GPU (different streams or threads) race
- * on it and must be serialized by the caller.
+ * with that device current, and the first call in the process page-locks (cudaHostRegister,
+ * no allocation) the 256 bytes of static host words; make that first call before any stream
+ * capture.  All calls share the one device array and host word: calls that overlap
+ * (different streams or threads) race on them and must be serialized by the caller.
  */
 #define PG_NOALLOC_SCRATCH_BYTES 256
 pg_status pg_voxelize_noalloc(const pg_batch *batch, const pg_grid *grid, int32_t out_dtype,

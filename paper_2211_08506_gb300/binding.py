@@ -29,6 +29,7 @@ PG_DEVERR_OFFSETS = 0x2
 PG_DEVERR_SPACING = 0x4
 PG_DEVERR_PERIODIC = 0x8
 PG_DEVERR_TIMEOUT = 0x10
+PG_DEVERR_TMEM_HELD = 0x20
 
 EXPORTED = (
     "pg_version", "pg_last_error", "pg_status_string", "pg_voxelize", "pg_voxelize_tuned",

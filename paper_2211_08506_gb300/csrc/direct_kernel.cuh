@@ -25,11 +25,10 @@
 // across block sizes, occupancy, store hints and chunk sizes, and equal to the unstaged
 // fallback used when an item has more than kStageCap candidates.
 //
-// Dense planes (kScatterMin or more staged candidates) can instead be accumulated in scatter
-// mode (see scatter_plane), in a kernel instantiation of its own.  Scatter mode adds the same
-// terms in exact fixed point, so its results differ from the gather's float sums only by the
-// rounding of those sums (a few units in the last place of FP32); across launch shapes they are
-// again bitwise identical.
+// Dense planes (kDiscMin or more staged candidates) can instead be accumulated in dense-plane
+// mode (see disc_plane), in a kernel instantiation of its own: the warp visits each
+// candidate's disc in the plane rather than every voxel for every candidate.  It adds the same
+// terms in the same order, so its results are bitwise identical to the gather's.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -41,8 +40,8 @@ namespace pgi {
 
 namespace {
 
-// Staged candidates from which a plane is accumulated in scatter mode instead of gathered.
-constexpr int kScatterMin = 6;
+// Staged candidates from which a plane is accumulated in dense-plane mode instead of gathered.
+constexpr int kDiscMin = 2;
 
 __device__ __forceinline__ float ex2_approx(float x)
 {
@@ -267,6 +266,79 @@ __device__ __forceinline__ void blocked_plane(T *out, int ny, int nz, int rpg, i
     }
 }
 
+// Voxel-integrated form with a separable cutoff (none or box), molecules of at most 32 atoms:
+// the per-axis factors do not depend on the plane, so the warp computes them once per chunk
+// into a table in shared memory (Sec. VI-A's per-axis tables): for the channel's i-th atom,
+// row i of the table (erf_table_stride floats) holds its y factor on each row y and then its
+// z factor on each column z, each exactly the value erf_axis gives for that row or column,
+// zeroed outside a box cutoff.  A plane is then walked in the passes of blocked_plane, and every term is the
+// atom's x factor times its table entries in the same order of operations as blocked_plane
+// uses, so the two give identical bits.  cand / dx / fx / ti are the lane's own atom's plane
+// candidacy, x displacement, x factor and table row.
+template <typename T, int VEC, int CUT, bool PER, int HINT, bool WGT>
+__device__ __forceinline__ void table_plane(T *out, const float *tab, int ny, int nz, int rpg,
+                                            int act, int my_row, int z0, int lane, float r2,
+                                            float rc, bool cand, float dx, float fx, int ti,
+                                            float ay, float az, float aw, float oy, float oz,
+                                            float hy, float hz, float Ly, float iLy, float Lz,
+                                            float iLz)
+{
+    const int tw = erf_table_stride(ny, nz);
+    const int tyw = (ny + 3) & ~3;
+    const float cz = fmaf(0.5f * (float)(nz - 1) + 0.5f, hz, oz);
+    const float wz = 0.5f * (float)(nz - 1) * hz;
+    for (int y0 = 0; y0 < ny; y0 += 2 * rpg) {
+        const int y_end = min(y0 + 2 * rpg, ny) - 1;
+        const float cy = fmaf(0.5f * (float)(y0 + y_end) + 0.5f, hy, oy);
+        const float wy = 0.5f * (float)(y_end - y0) * hy;
+        const int ya = y0 + my_row, yb = ya + rpg;
+        // Rows past the grid are computed but not stored; read a valid entry for them.
+        const int ra = min(ya, ny - 1), rb = min(yb, ny - 1);
+        float acc0[VEC], acc1[VEC];
+#pragma unroll
+        for (int k = 0; k < VEC; ++k) acc0[k] = acc1[k] = 0.0f;
+        const bool hit = cand && reaches<CUT, PER>(dx, ay, az, cy, wy, cz, wz, rc, Ly, iLy, Lz,
+                                                   iLz);
+        unsigned m = __ballot_sync(0xffffffffu, hit);
+        while (m) {
+            const int src = __ffs(m) - 1;
+            m &= m - 1;
+            const float sdx = __shfl_sync(0xffffffffu, dx, src);
+            const float sfx = __shfl_sync(0xffffffffu, fx, src);
+            const float sw = WGT ? __shfl_sync(0xffffffffu, aw, src) : 1.0f;
+            const int sti = __shfl_sync(0xffffffffu, ti, src);
+            const float *ty = tab + sti * tw;
+            const float *tz = ty + tyw;
+            const bool xout = CUT == PG_CUTOFF_BOX && sdx * sdx > r2;
+            const float ea = sw * (xout ? 0.0f : sfx * ty[ra]);
+            const float eb = sw * (xout ? 0.0f : sfx * ty[rb]);
+            float ez[VEC];
+            if constexpr (VEC % 4 == 0) {
+#pragma unroll
+                for (int k = 0; k < VEC; k += 4) {
+                    const float4 f = *reinterpret_cast<const float4 *>(tz + z0 + k);
+                    ez[k] = f.x;
+                    ez[k + 1] = f.y;
+                    ez[k + 2] = f.z;
+                    ez[k + 3] = f.w;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) ez[k] = tz[z0 + k];
+            }
+#pragma unroll
+            for (int k = 0; k < VEC; ++k) {
+                acc0[k] = fmaf(ea, ez[k], acc0[k]);
+                acc1[k] = fmaf(eb, ez[k], acc1[k]);
+            }
+        }
+        if (lane < act) {
+            if (ya < ny) store_lane<T, VEC, HINT>(out, (ya * nz + z0) / VEC, acc0);
+            if (yb < ny) store_lane<T, VEC, HINT>(out, (yb * nz + z0) / VEC, acc1);
+        }
+    }
+}
+
 __device__ __forceinline__ int wrap_index(int i, int n)
 {
     if (i >= 0 && i < n) return i;
@@ -293,137 +365,114 @@ __device__ __forceinline__ void disc_range(float a, float rho, float o, float in
     }
 }
 
-// Scatter mode for dense planes (Sec. VI-A visits each atom's non-zero box; here the box is cut
-// down to the exact disc row by row).  Work unit: one "run", the voxels of one row of one
-// candidate's disc in this plane.  The runs of all candidates are numbered consecutively
-// (per-candidate row counts, prefix-summed across the warp), and lane i takes runs i, i+32, ...
-// so lanes stay busy however many rows a disc has.  For its run a lane finds the exact z span
-// of the disc in that row and adds each in-cutoff term to the warp's plane accumulator with a
-// shared-memory integer atomic.  The accumulator is fixed point, scaled so that a voxel's sum
-// of at most `count` terms (each <= 1) stays below 2^30: integer addition is exact and
-// associative, so the result does not depend on the order in which lanes and runs land, and
-// every term is the same ex2 of the same d^2 as in the gather mode.
-template <typename T, int VEC, int CUT, bool PER, int HINT>
-__device__ __forceinline__ void scatter_plane(T *out, int *acc_i, int *run_off, int *run_ylo,
-                                              const float4 *stage, int count, int ny, int nz,
-                                              int lane, float q, float r2, float rc, float oy,
-                                              float oz, float hy, float hz, float Ly, float iLy,
-                                              float Lz, float iLz)
+// Dense-plane mode (Sec. VI-A/VI-B visit only each atom's non-zero box; here the box is cut
+// down to the candidate's disc in the plane).  The warp takes the staged candidates one at a
+// time, in atom order, and for each visits only the voxels of its disc's bounding square,
+// adding the candidate's terms to a per-warp FP32 plane accumulator in shared memory; then it
+// converts and stores the whole plane and leaves the accumulator zeroed.  Every term is the
+// same row factor times the same z factor, under the same exact cutoff test, as in the
+// gather, and every voxel receives its terms in atom order: the plane is bitwise identical to
+// the gathered one, whatever the launch shape.
+//
+// Per candidate the lanes first build a table of the square's rows (row factor, dx^2 + dy^2,
+// row offset in the plane), kDiscRows rows at a time.  Each lane then owns one column of the
+// square and keeps its z factor and dz in registers; a square of W <= 32 columns splits the
+// warp into 32 / W groups of W lanes, and the groups step through the rows together, two rows
+// per step so that both accumulator loads are in flight at once.  Wider squares take their
+// columns 32 at a time.
+template <typename T, int VEC, int CUT, bool PER, int HINT, bool WGT>
+__device__ __forceinline__ void disc_plane(T *out, float *acc, float4 *rowtab, const float4 *stage,
+                                           int count, int ny, int nz, int lane, float q, float r2,
+                                           float rc, float oy, float oz, float hy, float hz,
+                                           float Ly, float iLy, float Lz, float iLz)
 {
-    const int nvec = ny * nz / VEC;
     const float inv_hy = 1.0f / hy, inv_hz = 1.0f / hz;
-    // count < 2^bits, so a voxel's scaled sum is below 2^30.
-    const int bits = 32 - __clz(count);
-    const float scale = __int_as_float((127 + 30 - bits) << 23);
-    const float inv_scale = __int_as_float((127 - 30 + bits) << 23);
-
-    // 1. Row range of each candidate's disc, and the prefix offsets of its runs.
-    int total = 0;
-    for (int cb = 0; cb < count; cb += 32) {
-        const int j = cb + lane;
-        int nrows = 0, ylo = 0;
-        if (j < count) {
-            const float4 st = stage[j];
-            float rho = rc;
-            if (CUT == PG_CUTOFF_SPHERE) rho = sqrtf(fmaxf(fmaf(-st.x, st.x, rc * rc), 0.0f));
-            int lo, hi;
-            disc_range<PER>(st.y, rho, oy, inv_hy, ny, lo, hi);
-            nrows = max(hi - lo + 1, 0);
-            ylo = PER ? wrap_index(lo, ny) : lo;
-        }
-        int incl = nrows;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        if (j < count) {
-            run_off[j] = total + incl - nrows;
-            run_ylo[j] = ylo;
-        }
-        total += __shfl_sync(0xffffffffu, incl, 31);
-    }
-    if (lane == 0) run_off[count] = total;
-    __syncwarp();
-
-    // 2. Runs.
-    int j = 0;
-    for (int u = lane; u < total; u += 32) {
-        while (run_off[j + 1] <= u) ++j;
+    for (int j = 0; j < count; ++j) {
         const float4 st = stage[j];
         const float dx = st.x, ay = st.y, az = st.z;
+        const float w = WGT ? st.w : 1.0f;
         const float dx2 = dx * dx;
-        int y = run_ylo[j] + (u - run_off[j]);
-        if (PER && y >= ny) y -= ny;
-        float dy = fmaf((float)y + 0.5f, hy, oy) - ay;
-        if (PER) dy = wrap(dy, Ly, iLy);
-        const float dy2 = dy * dy;
-        const float dxy2 = fmaf(dy, dy, dx2);
-        float w = rc;
-        if (CUT == PG_CUTOFF_SPHERE) {
-            const float rem = fmaf(rc, rc, -dxy2);
-            if (rem < 0.0f) continue;
-            w = sqrtf(rem);
-        } else if (fmaxf(dx2, dy2) > r2) {
-            continue;
-        }
-        int zlo, zhi;
-        disc_range<PER>(az, w, oz, inv_hz, nz, zlo, zhi);
-        int *row = acc_i + y * nz;
-        int z = PER ? wrap_index(zlo, nz) : zlo;
-        const float exy = ex2_approx(-q * dxy2);
-        // Fixed-point term of voxel zz of this run (0 when outside the cutoff): the product
-        // of the same row and z factors, under the same test, as the gather mode adds.
-        auto term = [&](int zz) -> int {
-            float dz = fmaf((float)zz + 0.5f, hz, oz) - az;
-            if (PER) dz = wrap(dz, Lz, iLz);
-            if (CUT == PG_CUTOFF_SPHERE && fmaf(dz, dz, dxy2) > r2) return 0;
-            return __float2int_rn(exy * z_factor<CUT, 0>(dz, q, r2, 0.0f, hz) * scale);
-        };
-        int k = zhi - zlo + 1;
-        // Four voxels at a time: independent terms first, then their atomics.
-        for (; k >= 4; k -= 4) {
-            int zz[4], tv[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                zz[i] = z + i;
-                if (PER && zz[i] >= nz) zz[i] -= nz;
-                tv[i] = term(zz[i]);
+        float rho = rc;
+        if (CUT == PG_CUTOFF_SPHERE) rho = sqrtf(fmaxf(fmaf(-dx, dx, rc * rc), 0.0f));
+        int ylo, yhi, zlo, zhi;
+        disc_range<PER>(ay, rho, oy, inv_hy, ny, ylo, yhi);
+        disc_range<PER>(az, rho, oz, inv_hz, nz, zlo, zhi);
+        const int H = yhi - ylo + 1, W = zhi - zlo + 1;
+        if (H <= 0 || W <= 0) continue;
+        const int wb = min(W, 32);
+        const int groups = 32 / wb;
+        const int g = lane / wb;
+        const int cl = lane - g * wb;
+        for (int r0 = 0; r0 < H; r0 += kDiscRows) {
+            const int nr = min(H - r0, kDiscRows);
+            // Orders this candidate's table (and accumulator updates) after every lane's use
+            // of the previous table and the previous candidate's updates.
+            __syncwarp();
+            for (int t = lane; t < nr; t += 32) {
+                int y = ylo + r0 + t;
+                if (PER) y = wrap_index(y, ny);
+                float dy = fmaf((float)y + 0.5f, hy, oy) - ay;
+                if (PER) dy = wrap(dy, Ly, iLy);
+                const float dxy2 = fmaf(dy, dy, dx2);
+                const float e = w * row_factor<CUT, 0>(0.0f, dy, dx2, dxy2, q, r2, 0.0f, hy);
+                rowtab[t] = make_float4(e, dxy2, __int_as_float(y * nz), 0.0f);
             }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-                if (tv[i]) atomicAdd(row + zz[i], tv[i]);
-            z += 4;
-            if (PER && z >= nz) z -= nz;
-        }
-        for (; k > 0; --k) {
-            const int tv = term(z);
-            if (tv) atomicAdd(row + z, tv);
-            ++z;
-            if (PER && z >= nz) z -= nz;
+            __syncwarp();
+            if (g >= groups) continue;
+            for (int c0 = 0; c0 < W; c0 += 32) {
+                const int col = c0 + cl;
+                if (col >= W) continue;
+                int z = zlo + col;
+                if (PER) z = wrap_index(z, nz);
+                float dz = fmaf((float)z + 0.5f, hz, oz) - az;
+                if (PER) dz = wrap(dz, Lz, iLz);
+                const float ez = z_factor<CUT, 0>(dz, q, r2, 0.0f, hz);
+                float *const accz = acc + z;
+                int r = g;
+                for (; r + groups < nr; r += 2 * groups) {
+                    const float4 ta = rowtab[r], tb = rowtab[r + groups];
+                    float *pa = accz + __float_as_int(ta.z);
+                    float *pb = accz + __float_as_int(tb.z);
+                    const float va = *pa, vb = *pb;
+                    if (CUT == PG_CUTOFF_SPHERE) {
+                        if (fmaf(dz, dz, ta.y) <= r2) *pa = fmaf(ta.x, ez, va);
+                        if (fmaf(dz, dz, tb.y) <= r2) *pb = fmaf(tb.x, ez, vb);
+                    } else {
+                        *pa = fmaf(ta.x, ez, va);
+                        *pb = fmaf(tb.x, ez, vb);
+                    }
+                }
+                if (r < nr) {
+                    const float4 ta = rowtab[r];
+                    float *pa = accz + __float_as_int(ta.z);
+                    if (CUT != PG_CUTOFF_SPHERE || fmaf(dz, dz, ta.y) <= r2)
+                        *pa = fmaf(ta.x, ez, *pa);
+                }
+            }
         }
     }
     __syncwarp();
 
-    // 3. Convert, store, and leave the accumulator zeroed for the next plane.
+    // Convert, store, and leave the accumulator zeroed for the next plane.
+    const int nvec = ny * nz / VEC;
     for (int v = lane; v < nvec; v += 32) {
         float a[VEC];
         if constexpr (VEC % 4 == 0) {
 #pragma unroll
             for (int k = 0; k < VEC; k += 4) {
-                int4 *p = reinterpret_cast<int4 *>(acc_i + v * VEC) + k / 4;
-                const int4 w = *p;
-                *p = make_int4(0, 0, 0, 0);
-                a[k] = (float)w.x * inv_scale;
-                a[k + 1] = (float)w.y * inv_scale;
-                a[k + 2] = (float)w.z * inv_scale;
-                a[k + 3] = (float)w.w * inv_scale;
+                float4 *p = reinterpret_cast<float4 *>(acc + v * VEC) + k / 4;
+                const float4 f = *p;
+                *p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                a[k] = f.x;
+                a[k + 1] = f.y;
+                a[k + 2] = f.z;
+                a[k + 3] = f.w;
             }
         } else {
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
-                a[k] = (float)acc_i[v * VEC + k] * inv_scale;
-                acc_i[v * VEC + k] = 0;
+                a[k] = acc[v * VEC + k];
+                acc[v * VEC + k] = 0.0f;
             }
         }
         store_lane<T, VEC, HINT>(out, v, a);
@@ -442,14 +491,18 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
     const int warp = threadIdx.x >> 5;
     const int warps_per_block = blockDim.x >> 5;
     // Per warp (layout in direct_warp_floats): the plane's staged candidates, the chunk's
-    // channel atoms, then in scatter mode the plane accumulator and the run bookkeeping.
-    float4 *stage = smem_all + (size_t)warp * (direct_warp_floats(A.plane_stride) / 4);
+    // channel atoms, then in dense-plane mode the plane accumulator and the row table.
+    float4 *stage = smem_all + (size_t)warp * (direct_warp_floats(A.plane_stride, A.erf_tab) / 4);
     float4 *chan = stage + kStageCap;
-    int *acc_i = reinterpret_cast<int *>(chan + kChanCap);
-    int *run_off = acc_i + A.plane_stride;
-    int *run_ylo = run_off + kStageCap + 4;
-    if (SCAT) {  // the scatter accumulator starts zeroed and each plane leaves it so
-        for (int i = lane; i < A.plane_stride; i += 32) acc_i[i] = 0;
+    float *acc = reinterpret_cast<float *>(chan + kChanCap);
+    float4 *rowtab = reinterpret_cast<float4 *>(acc + A.plane_stride);
+    // Voxel-integrated form with a separable cutoff: per-chunk factor tables (table_plane),
+    // held in the staging area, which molecules of at most 32 atoms do not use.
+    constexpr bool TAB = FORM == 1 && CUT != PG_CUTOFF_SPHERE;
+    float *tab = reinterpret_cast<float *>(stage);
+    long long tab_bc = -1;  // (molecule, channel) whose factors the table holds
+    if (SCAT) {  // the plane accumulator starts zeroed and each plane leaves it so
+        for (int i = lane; i < A.plane_stride; i += 32) acc[i] = 0.0f;
         __syncwarp();
     }
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -549,11 +602,66 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
             }
             if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(A.err, PG_DEVERR_ELEMENT);
         }
-        // Large molecule: this channel's atoms, in atom order, staged in shared memory once
-        // per chunk when they fit, so that each plane culls them from there.
+        // Small molecule, voxel-integrated form, separable cutoff: the factor table of this
+        // (molecule, channel), built unless the warp already holds it.  my_ti is the lane's atom's
+        // row in it (its rank among the channel's atoms).
+        bool use_tab = false;
+        int my_ti = -1;
+        if constexpr (TAB) {
+            if (small && blocked && A.erf_tab > 0) {
+                const unsigned chm = __ballot_sync(0xffffffffu, my_e == c);
+                const int nch = __popc(chm);
+                const int tw = erf_table_stride(G.ny, G.nz);
+                use_tab = nch > 0 && nch * tw <= A.erf_tab;
+                if (use_tab) {
+                    my_ti = (my_e == c) ? __popc(chm & lt_mask) : -1;
+                    if (tab_bc != (long long)bc) {
+                        const float kf = G.kerf[c], r2 = G.r2[c], q = G.q[c];
+                        const int tyw = (G.ny + 3) & ~3;
+                        const int total = nch * tw;
+                        __syncwarp();
+                        for (int base = 0; base < total; base += 32) {
+                            const int idx = base + lane;
+                            const int row = idx / tw;
+                            const int j = idx - row * tw;
+                            const int src = __fns(chm, 0, min(row, nch - 1) + 1);
+                            const float sy = __shfl_sync(0xffffffffu, my_y, src);
+                            const float sz = __shfl_sync(0xffffffffu, my_z, src);
+                            if (idx < total) {
+                                float v = 0.0f;
+                                if (j < tyw) {
+                                    if (j < G.ny) {
+                                        float dy = fmaf((float)j + 0.5f, hy, oy) - sy;
+                                        if (PER) dy = wrap(dy, Ly, iLy);
+                                        v = erf_axis(dy, hy, kf);
+                                        if (CUT == PG_CUTOFF_BOX && dy * dy > r2) v = 0.0f;
+                                    }
+                                } else if (j - tyw < G.nz) {
+                                    float dz = fmaf((float)(j - tyw) + 0.5f, hz, oz) - sz;
+                                    if (PER) dz = wrap(dz, Lz, iLz);
+                                    v = z_factor<CUT, 1>(dz, q, r2, kf, hz);
+                                }
+                                tab[idx] = v;
+                            }
+                        }
+                        __syncwarp();
+                        tab_bc = (long long)bc;
+                    }
+                }
+            }
+        }
+        // Large molecule: this channel's atoms that can reach a plane of the chunk, in atom
+        // order, staged in shared memory once per chunk when they fit, so that each plane culls
+        // them from there.  An atom can reach a plane only if its x distance (nearest image
+        // when periodic) to the chunk's centre is within the chunk's half width plus the
+        // widened cutoff, with a margin for rounding.
         int n_chan = -1;
         if (!small) {
+            tab_bc = -1;  // the staging below overwrites the factor table
             int cnt = 0;
+            const float xc = fmaf(0.5f * (float)(x_begin + x_end - 1) + 0.5f, hx, ox);
+            const float xreach = fmaf(0.5f * (float)(x_end - 1 - x_begin), hx, G.rcull[c]) +
+                                 1e-3f * hx + 1e-5f * (fabsf(xc) + (PER ? Lx : 0.0f));
             // 64 atoms per step, all loads issued before any is used.
             for (int base = a0; base < a1; base += 64) {
                 int e[2];
@@ -576,7 +684,11 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                 }
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
-                    const bool ok = e[h] == c;
+                    bool ok = e[h] == c;
+                    if (CUT != PG_CUTOFF_NONE) {
+                        const float ex = PER ? wrap(ax[h] - xc, Lx, iLx) : ax[h] - xc;
+                        ok = ok && fabsf(ex) <= xreach;
+                    }
                     const unsigned m = __ballot_sync(0xffffffffu, ok);
                     if (ok) {
                         const int pos = cnt + __popc(m & lt_mask);
@@ -606,6 +718,11 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                 const unsigned cmask = __ballot_sync(0xffffffffu, cand);
                 if (cmask == 0u) {
                     zero_plane<T, VEC, HINT>(out, nvec, lane);
+                } else if (TAB && use_tab) {
+                    const float fx = cand ? erf_axis(dx, hx, kf) : 0.0f;
+                    table_plane<T, VEC, CUT, PER, HINT, WGT>(
+                        out, tab, G.ny, G.nz, rpg, act, my_row, my_z0, lane, r2, rc, cand, dx, fx,
+                        my_ti, my_y, my_z, my_w, oy, oz, hy, hz, Ly, iLy, Lz, iLz);
                 } else if (blocked) {
                     blocked_plane<T, VEC, CUT, PER, HINT, FORM>(
                         out, G.ny, G.nz, rpg, act, my_row, my_z0, lane, q, r2, kf, hx, oy, oz, hy,
@@ -718,10 +835,10 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                 __syncwarp();
                 if (count == 0) {
                     zero_plane<T, VEC, HINT>(out, nvec, lane);
-                } else if (SCAT && count >= kScatterMin && count <= kStageCap) {
-                    scatter_plane<T, VEC, CUT, PER, HINT>(out, acc_i, run_off, run_ylo, stage,
-                                                         count, G.ny, G.nz, lane, q, r2, rc, oy,
-                                                         oz, hy, hz, Ly, iLy, Lz, iLz);
+                } else if (SCAT && count >= kDiscMin && count <= kStageCap) {
+                    disc_plane<T, VEC, CUT, PER, HINT, WGT>(out, acc, rowtab, stage, count, G.ny,
+                                                           G.nz, lane, q, r2, rc, oy, oz, hy, hz,
+                                                           Ly, iLy, Lz, iLz);
                 } else if (blocked && count <= kStageCap) {
                     blocked_plane<T, VEC, CUT, PER, HINT, FORM>(
                         out, G.ny, G.nz, rpg, act, my_row, my_z0, lane, q, r2, kf, hx, oy, oz, hy,
@@ -842,8 +959,8 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
     }
 }
 
-// Scatter-capable instantiations (SCAT) exist only for the point form and where a cutoff
-// bounds each atom's disc; the gather-only ones carry no scatter code and so keep their
+// Dense-plane instantiations (SCAT) exist only for the point form and where a cutoff
+// bounds each atom's disc; the gather-only ones carry no dense-plane code and so keep their
 // register allocation.
 template <typename T, int VEC, int CUT, bool PER, int HINT, int FORM>
 const void *pick_scat(bool scat)
@@ -875,7 +992,7 @@ const void *pick_shape(int cutoff, int periodic, int hint, bool scat)
     return pick_hint<T, VEC, PG_CUTOFF_NONE, false, FORM>(hint, scat);
 }
 
-// Weighted instantiations: gather mode (scatter mode assumes unit terms) and default stores.
+// Weighted instantiations: gather mode and default stores.
 template <typename T, int VEC, int FORM>
 const void *pick_weighted_shape(int cutoff, int periodic)
 {
@@ -907,7 +1024,7 @@ const void *pick_weighted(int dtype, bool vec_ok, int cut, int per)
 }
 
 // The instantiation for one launch: dtype, vector stores, cutoff, boundary, store hint,
-// scatter mode and voxel form.
+// dense-plane mode and voxel form.
 template <int FORM>
 const void *pick_direct(int dtype, bool vec_ok, int cut, int per, int hint, bool scat)
 {

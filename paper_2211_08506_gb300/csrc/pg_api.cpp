@@ -59,6 +59,9 @@ struct Device {
     unsigned long long *sched = nullptr;    // kSchedSlots work counters, 4 words apart
     std::atomic<unsigned> *next_slot = nullptr;
     std::string name;
+    // A separable launch reported PG_DEVERR_TMEM_HELD: a CTA kept tensor memory it could not
+    // safely free, so a later launch's allocation might never be granted.
+    std::atomic<bool> *tmem_held = nullptr;
 
     unsigned long long *take_slot()
     {
@@ -69,6 +72,16 @@ struct Device {
 
 std::mutex g_mu;
 std::map<int, Device> g_devices;
+
+// PG_DEBUG_LAUNCH=1 in the environment traces launches and per-device allocations to stderr.
+bool debug_trace_on()
+{
+    static const bool on = [] {
+        const char *v = std::getenv("PG_DEBUG_LAUNCH");
+        return v && v[0] == '1';
+    }();
+    return on;
+}
 
 pg_status get_device(Device **out)
 {
@@ -92,7 +105,10 @@ pg_status get_device(Device **out)
         PG_CUDA(cudaMalloc(&d.sched, sched_bytes), "cudaMalloc(work counters)");
         PG_CUDA(cudaMemset(d.sched, 0, sched_bytes), "cudaMemset(work counters)");
         d.next_slot = new std::atomic<unsigned>(0u);
+        d.tmem_held = new std::atomic<bool>(false);
         PG_CUDA(cudaDeviceSynchronize(), "cudaDeviceSynchronize(setup)");
+        if (debug_trace_on())
+            std::fprintf(stderr, "[pg] per-device state allocated on device %d\n", id);
         it = g_devices.emplace(id, d).first;
     }
     *out = &it->second;
@@ -205,7 +221,7 @@ pg_tuning default_tuning(int path)
     return t;
 }
 
-// Floats of per-warp shared memory for the direct kernel's scatter mode (dense planes), or 0
+// Floats of per-warp shared memory for the direct kernel's dense-plane mode, or 0
 // where it does not apply: no cutoff, planes above 16 KB of FP32 accumulators, or an axis
 // above 256 voxels (the per-atom tables hold one entry per row and per column).
 int direct_plane_stride(const pg_grid *g)
@@ -215,14 +231,23 @@ int direct_plane_stride(const pg_grid *g)
     return (int)((plane + 3) / 4 * 4);
 }
 
-// Whether the direct kernel runs with scatter mode (its scatter-capable instantiation).
+// Whether the direct kernel runs with dense-plane mode (its dense-plane instantiation).
 // Molecules of at most 32 atoms never reach it (they take the register path), so a batch
 // whose mean is that small keeps the gather-only instantiation and its higher occupancy.
 bool direct_scatter_on(const pg_batch *b, const pg_grid *g, const pg_tuning &t)
 {
-    // The fixed-point accumulator is scaled for unit terms: weighted grids gather in float.
+    // Weighted grids keep the gather-only instantiations.
     return !t.gather_only && g->voxel_form == PG_FORM_POINT && !b->weight && !b->cell &&
            direct_plane_stride(g) > 0 && b->n_atoms > 32LL * b->n_mol;
+}
+
+// Floats of per-warp factor table for the direct kernel's voxel-integrated form with a
+// separable cutoff: room for 32 atoms' per-axis factors, at most kErfTabCap; 0 elsewhere.
+int direct_erf_tab(const pg_batch *b, const pg_grid *g)
+{
+    if (g->voxel_form != PG_FORM_INTEGRAL || g->cutoff == PG_CUTOFF_SPHERE || b->cell) return 0;
+    const long long need = 32LL * erf_table_stride(g->ny, g->nz);
+    return (int)std::min<long long>(need, kErfTabCap);
 }
 
 bool vec_stores_ok(const void *out, const pg_grid *g, int dtype)
@@ -238,6 +263,10 @@ pg_status plan_forward(const pg_batch *b, const pg_grid *g, int dtype, void *out
     Geometry G;
     make_geometry(b, g, &G);
     if (t.path == PG_PATH_SEPARABLE) {
+        if (d.tmem_held->load())
+            return fail(PG_ERR_CUDA, "separable launches are refused on this device: an earlier "
+                                     "launch kept tensor memory after a timed-out wait "
+                                     "(PG_DEVERR_TMEM_HELD)");
         if (b->cell)
             return fail(PG_ERR_UNSUPPORTED, "the separable path needs an axis-aligned box; a "
                                             "cell matrix's metric does not factor per axis");
@@ -269,10 +298,12 @@ pg_status plan_forward(const pg_batch *b, const pg_grid *g, int dtype, void *out
     a.plane_stride = direct_scatter_on(b, g, t) ? direct_plane_stride(g) : 0;
     a.chunk_planes = (t.chunk_planes >= 1 && t.chunk_planes <= 64) ? t.chunk_planes : 8;
     a.chunk_order = t.chunk_order == 1 ? 1 : 0;
+    a.erf_tab = direct_erf_tab(b, g);
     a.geo = G;
     const int vec = vec_stores_ok(out, g, dtype) ? 1 : 0;
     if (b->cell) {
         a.plane_stride = 0;
+        a.erf_tab = 0;
         cudaError_t e = cell_plan(a, dtype, vec, t, d.sms, kl);
         if (e != cudaSuccess) return cuda_fail(e, "cell_plan");
         return PG_OK;
@@ -505,12 +536,13 @@ pg_status report_bits(unsigned bits)
 {
     if (!bits) return PG_OK;
     return fail((bits & PG_DEVERR_TIMEOUT) ? PG_ERR_TIMEOUT : PG_ERR_DEVICE_VALIDATION,
-                "device validation failed (bits 0x%x:%s%s%s%s%s)", bits,
+                "device validation failed (bits 0x%x:%s%s%s%s%s%s)", bits,
                 (bits & PG_DEVERR_ELEMENT) ? " element id outside [0, C)" : "",
                 (bits & PG_DEVERR_OFFSETS) ? " bad CSR offsets" : "",
                 (bits & PG_DEVERR_SPACING) ? " non-positive spacing" : "",
                 (bits & PG_DEVERR_PERIODIC) ? " periodic cutoff >= half a cell edge" : "",
-                (bits & PG_DEVERR_TIMEOUT) ? " tensor-core wait timed out" : "");
+                (bits & PG_DEVERR_TIMEOUT) ? " tensor-core wait timed out" : "",
+                (bits & PG_DEVERR_TMEM_HELD) ? " tensor memory kept" : "");
 }
 
 }  // namespace
@@ -519,11 +551,7 @@ namespace pgi {
 
 void debug_launch(const KernelLaunch &kl)
 {
-    static const bool on = [] {
-        const char *v = std::getenv("PG_DEBUG_LAUNCH");
-        return v && v[0] == '1';
-    }();
-    if (on)
+    if (debug_trace_on())
         std::fprintf(stderr, "[pg] launch func=%p grid=%u block=%u smem=%zu\n", kl.func,
                      kl.grid.x, kl.block.x, kl.smem);
 }
@@ -560,6 +588,7 @@ pg_status direct_launch_with_scratch(const pg_batch *b, const pg_grid *g, int dt
     const pg_tuning t = default_tuning(PG_PATH_DIRECT);
     a.plane_stride = direct_scatter_on(b, g, t) ? direct_plane_stride(g) : 0;
     a.chunk_planes = 8;
+    a.erf_tab = b->cell ? 0 : direct_erf_tab(b, g);
     make_geometry(b, g, &a.geo);
     const int vec = vec_stores_ok(out, g, dtype) ? 1 : 0;
     cudaError_t e = b->cell ? cell_plan(a, dtype, vec, t, sm_count, kl)
@@ -722,6 +751,7 @@ pg_status pg_sync_status(void *stream, uint32_t *bits_out)
     PG_CUDA(cudaMemsetAsync(d->err, 0, sizeof(unsigned), s), "clear error word");
     PG_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
     if (bits_out) *bits_out = bits;
+    if (bits & PG_DEVERR_TMEM_HELD) d->tmem_held->store(true);
     return report_bits(bits);
 }
 
@@ -756,9 +786,8 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
         return PG_OK;
     }
 
-    // Direct candidates with scatter mode on accumulate dense planes in fixed point; those
-    // without sum in float.  Within a class every candidate must match the reference's bits.
-    auto scatter_class = [&](const pg_tuning &t) { return direct_scatter_on(batch, grid, t); };
+    // Every direct candidate (any launch shape, chunk order or dense-plane setting) adds the
+    // same terms in the same order, so each must match the reference's bits.
     std::vector<pg_tuning> cands;
     if (path != PG_PATH_SEPARABLE) {
         // Full product of the direct kernel's launch knobs; the default comes first and is
@@ -778,7 +807,7 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
                         cands.push_back(t);
                     }
         for (int order : {0, 1})
-            for (int threads : {256, 512})
+            for (int threads : {128, 256, 512})
                 for (int bps : {0, 1, 2})
                     for (int hint : {0, 1})
                         for (int cp : {1, 2, 4, 8})
@@ -871,8 +900,7 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
                 return st;
             if ((st = cu(cudaStreamSynchronize(s), "sync"))) return st;
             ref_index = (int)i;
-        } else if (cands[i].path == PG_PATH_DIRECT && cands[ref_index].path == PG_PATH_DIRECT &&
-                   scatter_class(cands[i]) == scatter_class(cands[ref_index])) {
+        } else if (cands[i].path == PG_PATH_DIRECT && cands[ref_index].path == PG_PATH_DIRECT) {
             unsigned long long h = 0;
             if ((st = cu(buffer_hash(out, out_bytes, d_hash, s), "hash"))) return st;
             if ((st = cu(cudaMemcpyAsync(&h, d_hash, sizeof h, cudaMemcpyDeviceToHost, s),
@@ -889,15 +917,8 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
                          "copy compare")))
                 return st;
             if ((st = cu(cudaStreamSynchronize(s), "sync"))) return st;
-            // Separable candidates round through BF16 operands; direct candidates of the other
-            // accumulation class differ only in the rounding of each voxel's sum, which the
-            // output dtype may round once more.
-            const bool sep = cands[i].path == PG_PATH_SEPARABLE ||
-                             cands[ref_index].path == PG_PATH_SEPARABLE;
-            const float tol = sep ? 1e-2f
-                                  : (out_dtype == PG_F32 ? 1e-5f
-                                                         : (out_dtype == PG_F16 ? 1e-3f : 8e-3f));
-            pass = cmp[0] <= tol * cmp[1];
+            // Separable candidates round through BF16 operands.
+            pass = cmp[0] <= 1e-2f * cmp[1];
         }
         if (!pass) continue;
         // Time: median of 7 single launches, each after an unrelated fill of the spacer
@@ -1135,6 +1156,7 @@ pg_status pg_plan_run(pg_plan *p, const pg_batch *hb, void *out, void *stream)
     cudaStream_t s = (cudaStream_t)stream;
     PG_CUDA(cudaGraphLaunch(p->exec, s), "cudaGraphLaunch");
     PG_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
+    if (*p->h_err & PG_DEVERR_TMEM_HELD) d->tmem_held->store(true);
     return report_bits(*p->h_err);
 }
 
@@ -1157,6 +1179,7 @@ void pg_shutdown(void)
             cudaFree(kv.second.err);
             cudaFree(kv.second.sched);
             delete kv.second.next_slot;
+            delete kv.second.tmem_held;
         }
         g_devices.clear();
         if (cur >= 0) cudaSetDevice(cur);

@@ -18,7 +18,7 @@ cudaError_t direct_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tun
 
     int threads = t.block_threads;
     if (threads != 128 && threads != 256 && threads != 512) threads = 256;
-    const size_t per_warp = (size_t)direct_warp_floats(a.plane_stride) * sizeof(float);
+    const size_t per_warp = (size_t)direct_warp_floats(a.plane_stride, a.erf_tab) * sizeof(float);
     while (threads > 128 && (size_t)(threads / 32) * per_warp > 200 * 1024) threads /= 2;
     const size_t smem = (size_t)(threads / 32) * per_warp;
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

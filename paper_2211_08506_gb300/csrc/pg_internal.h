@@ -63,15 +63,29 @@ struct Inputs {
     const float *cell;    // per-molecule 3x3 box edges (rows), or null (axis-aligned box)
 };
 
-// 32-bit words of dynamic shared memory per warp of the direct kernel: kStageCap staged
-// candidates and kChanCap channel atoms (float4 each), then, when scatter mode is on
-// (plane_stride > 0), the plane's fixed-point accumulator (plane_stride words, a multiple of
-// 4), the run offsets (kStageCap + 4) and the first row of each candidate's disc (kStageCap).
-// A multiple of 4 words.
-__host__ __device__ inline int direct_warp_floats(int plane_stride)
+// Rows of a candidate's disc square whose table the dense-plane mode holds at a time.
+constexpr int kDiscRows = 32;
+// Largest per-warp factor table of the voxel-integrated form (floats).
+constexpr int kErfTabCap = 4096;
+
+// Row stride of the voxel-integrated form's per-atom factor table: the y factors, then the z
+// factors, each padded to a multiple of 4 floats so that a lane's z factors load as float4.
+__host__ __device__ inline int erf_table_stride(int ny, int nz)
 {
-    return 4 * (kStageCap + kChanCap) +
-           (plane_stride > 0 ? plane_stride + 2 * kStageCap + 4 : 0);
+    return ((ny + 3) & ~3) + ((nz + 3) & ~3);
+}
+
+// 32-bit words of dynamic shared memory per warp of the direct kernel: kStageCap staged
+// candidates and kChanCap channel atoms (float4 each), or, if larger, the voxel-integrated
+// form's factor table (erf_tab words; the two are never in use at once), then, when
+// dense-plane mode is on (plane_stride > 0, point form only), the plane's FP32 accumulator
+// (plane_stride words, a multiple of 4) and the row table (kDiscRows float4).  A multiple of
+// 4 words.
+__host__ __device__ inline int direct_warp_floats(int plane_stride, int erf_tab)
+{
+    const int staging = 4 * (kStageCap + kChanCap);
+    return (erf_tab > staging ? erf_tab : staging) +
+           (plane_stride > 0 ? plane_stride + 4 * kDiscRows : 0);
 }
 
 struct DirectArgs {
@@ -79,9 +93,10 @@ struct DirectArgs {
     void *out;
     unsigned *err;
     unsigned long long *sched;  // {next chunk, retired warps}; zero between launches
-    int plane_stride;           // floats of per-warp plane buffer for scatter mode (0: off)
+    int plane_stride;           // floats of per-warp plane accumulator, dense-plane mode (0: off)
     int chunk_planes;           // x-planes per dynamically scheduled chunk (>= 1)
     int chunk_order;            // 0: (molecule, channel) order; 1: channel-major
+    int erf_tab;                // floats of per-warp factor table, voxel-integrated form (0: off)
     Geometry geo;
 };
 
@@ -110,6 +125,8 @@ struct SeparableArgs {
     int n_tile;   // output columns per tensor-core tile
     int pack;     // pipelined: molecules per 128-row tile when C nx divides 128 (else 0)
     int kslots;   // pipelined: K chunks whose atom tables stay resident per tile (>= 1)
+    unsigned long long wait_ns;  // wall-time limit of each bounded mbarrier wait
+    int stall;    // test of the bounded waits: stop before the first handoff (0: off)
 };
 
 // A fully resolved kernel launch (function, shape, single by-value argument struct), so
@@ -173,7 +190,8 @@ pg_status direct_launch_with_scratch(const pg_batch *b, const pg_grid *g, int dt
 // Record a failure message for pg_last_error() and return `status`.
 pg_status set_last_error(pg_status status, const char *fmt, ...);
 
-// PG_DEBUG_LAUNCH=1 in the environment prints every launch shape to stderr.
+// PG_DEBUG_LAUNCH=1 in the environment prints every launch shape to stderr, and a line
+// whenever the library allocates its per-device state.
 void debug_launch(const KernelLaunch &kl);
 
 inline cudaError_t launch(KernelLaunch &kl, cudaStream_t s)

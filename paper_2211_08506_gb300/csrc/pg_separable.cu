@@ -28,8 +28,12 @@
 // 128 bytes apart along K (leading byte offset) and 512 bytes apart along M/N (stride byte
 // offset).
 //
-// Every mbarrier wait is bounded; on expiry the kernel sets PG_DEVERR_TIMEOUT, frees its
-// tensor memory and returns.
+// Every mbarrier wait is bounded; on expiry the kernel sets PG_DEVERR_TIMEOUT and returns.
+// Before a CTA frees its tensor memory, the thread that issued its MMAs commits once more to a
+// drain barrier and waits for it (bounded), so no MMA can still be writing the columns; if
+// that never arrives the columns stay allocated and PG_DEVERR_TMEM_HELD is set.
+#include <cstdlib>
+
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -47,11 +51,11 @@ constexpr int kKC = 32;         // atoms per K chunk (two K=16 MMA steps)
 constexpr int kTab = 36;        // floats per table row: 32 atoms + 4 pad (conflict-free reads)
 constexpr int kTabX = 33;       // g_x rows: A-tile threads read one atom across 32 rows
 constexpr int kRows = 128;      // M tile = CTA threads = TMEM lanes
-constexpr unsigned kWaitLimit = 1u << 24;         // polls of one mbarrier wait, at most
-constexpr unsigned long long kWaitNs = 2000000000ull;  // and at most 2 s of wall time
+constexpr unsigned kWaitLimit = 1u << 24;  // polls of one mbarrier wait, at most; and at most
+                                           // SeparableArgs::wait_ns of wall time
 
 struct SepLayout {
-    int bar, tmem, atoms, a, b, gy, gz, stage, stage_stride, total;
+    int bar, drain, tmem, atoms, a, b, gy, gz, stage, stage_stride, total;
 };
 
 __host__ __device__ inline int align_up(int x, int a) { return (x + a - 1) / a * a; }
@@ -61,6 +65,8 @@ __host__ __device__ inline SepLayout sep_layout(int ny, int nz, int n_tile, int 
     SepLayout L;
     int o = 0;
     L.bar = o;
+    o += 8;
+    L.drain = o;  // the final commit before tensor memory is freed
     o += 8;
     L.tmem = o;
     o += 8;
@@ -129,6 +135,21 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
         : "r"(bar), "r"(parity)
         : "memory");
     return ok != 0u;
+}
+
+// Bounded wait, at most kDrainNs, for phase 0 of the drain barrier: the final tcgen05.commit a
+// CTA issues before it frees its tensor memory, which arrives once every MMA the committing
+// thread issued has completed (at once when none is outstanding).
+constexpr unsigned long long kDrainNs = 2000000000ull;
+__device__ __forceinline__ bool drain_wait(uint32_t bar)
+{
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 0; it < kWaitLimit; ++it) {
+        if (mbar_try_wait(bar, 0u)) return true;
+        if ((it & 63u) == 63u && global_ns() - t0 > kDrainNs) return false;
+        __nanosleep(32);
+    }
+    return false;
 }
 
 __device__ __forceinline__ void fence_barrier_init()
@@ -410,10 +431,13 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
     float *tgz = reinterpret_cast<float *>(smem + L.gz);
     unsigned char *srow = smem + L.stage + tid * L.stage_stride;
     const uint32_t bar = smem_u32(smem + L.bar);
+    const uint32_t drain = smem_u32(smem + L.drain);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L.tmem);
+    volatile uint32_t *drained = tmem_slot + 1;  // the drain barrier arrived
 
     if (tid == 0) {
         mbar_init(bar, 1);
+        mbar_init(drain, 1);
         fence_barrier_init();
     }
     if (warp == 0) {
@@ -556,7 +580,7 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                 fence_proxy_async_smem();
                 tc_fence_before();
                 __syncthreads();
-                if (tid == 0) {
+                if (tid == 0 && !A.stall) {
                     tc_fence_after();
 #pragma unroll
                     for (int s = 0; s < kKC / 16; ++s) {
@@ -570,7 +594,7 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
                 const unsigned long long t0 = global_ns();
                 for (unsigned it = 0; it < kWaitLimit && !done; ++it) {
                     done = mbar_try_wait(bar, phase);
-                    if (!done && (it & 63u) == 63u && global_ns() - t0 > kWaitNs) break;
+                    if (!done && (it & 63u) == 63u && global_ns() - t0 > A.wait_ns) break;
                 }
                 phase ^= 1u;
                 timed_out = __syncthreads_or(!done) != 0;
@@ -593,9 +617,17 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
         }
     }
     if (timed_out && tid == 0) atomicOr(A.err, PG_DEVERR_TIMEOUT);
+    // The tensor memory is freed only once every MMA of the CTA has completed: thread 0, which
+    // issued them, commits to the drain barrier and waits for it.  If it never arrives, the
+    // columns stay allocated rather than be freed under an MMA that may still write them.
+    if (tid == 0) {
+        mma_commit(drain);
+        *drained = drain_wait(drain) ? 1u : 0u;
+        if (!*drained) atomicOr(A.err, PG_DEVERR_TIMEOUT | PG_DEVERR_TMEM_HELD);
+    }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 0 && *drained) {
         tc_fence_after();
         tmem_dealloc(tmem, (uint32_t)n_tile);
     }
@@ -631,11 +663,11 @@ __host__ __device__ inline PipeLayout pipe_layout(int nx, int ny, int nz, int n_
 {
     PipeLayout L;
     int o = 0;
-    L.bars = o;  // b_full[2], b_empty[2], acc_full[2], acc_empty[2]
-    o += 8 * 8;
+    L.bars = o;  // b_full[2], b_empty[2], acc_full[2], acc_empty[2], drain
+    o += 9 * 8;
     L.tmem = o;
     o += 8;
-    L.flag = o;
+    L.flag = o;  // {a role gave up, the drain arrived}
     o += 8;
     o = align_up(o, 16);
     // Packed tiles: the tile's CSR offsets (pack + 1) and each molecule's origin and spacing.
@@ -695,14 +727,15 @@ __device__ __forceinline__ bool producers_all(bool v)
 }
 
 // Bounded wait on `parity`; false if it gave up or another role already did.
-__device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatile int *flag)
+__device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatile int *flag,
+                                          unsigned long long wait_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned it = 0; it < kWaitLimit; ++it) {
         __nanosleep(32);  // back off so waiting warps leave issue slots to working ones
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 63u && (*flag || global_ns() - t0 > kWaitNs)) break;
+        if ((it & 63u) == 63u && (*flag || global_ns() - t0 > wait_ns)) break;
     }
     *flag = 1;
     return false;
@@ -710,10 +743,11 @@ __device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatil
 
 // One lane of the warp polls the barrier; __syncwarp then orders the other lanes after its
 // acquire.  Returns the same value on every lane.
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *flag)
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *flag,
+                                          unsigned long long wait_ns)
 {
     bool got = true;
-    if ((threadIdx.x & 31) == 0) got = pipe_wait(bar, parity, flag);
+    if ((threadIdx.x & 31) == 0) got = pipe_wait(bar, parity, flag, wait_ns);
     return __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
 }
 
@@ -800,8 +834,10 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
     auto b_empty = [&](int s) { return bars + 8u * (2 + s); };
     auto acc_full = [&](int s) { return bars + 8u * (4 + s); };
     auto acc_empty = [&](int s) { return bars + 8u * (6 + s); };
+    const uint32_t drain = bars + 8u * 8;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + L.tmem);
     volatile int *flag = reinterpret_cast<volatile int *>(smem + L.flag);
+    volatile int *drained = flag + 1;
 
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
@@ -810,7 +846,9 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
             mbar_init(acc_full(s), 1);   // tcgen05.commit
             mbar_init(acc_empty(s), 4);  // one elected lane per epilogue warp
         }
+        mbar_init(drain, 1);             // tcgen05.commit before the tensor memory is freed
         *flag = 0;
+        *drained = 0;
         fence_barrier_init();
     }
     if (warp == 0) {
@@ -878,8 +916,10 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                 for (int kc = 0; kc < it.n_kc && ok; ++kc, ++step) {
                     const int s = (int)(step % kPipeStages);
                     const uint32_t ph = (step / kPipeStages) & 1u;
-                    const bool got = warp_wait(b_empty(s), ph ^ 1u, flag);
-                    if (!producers_all(got)) {
+                    const bool got = warp_wait(b_empty(s), ph ^ 1u, flag, A.wait_ns);
+                    // A.stall (a test of the bounded waits) stops the producers before their
+                    // first arrive: no MMA is issued and no store starts, and every wait gives up.
+                    if (!producers_all(got) || A.stall) {
                         ok = false;
                         break;
                     }
@@ -893,7 +933,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                     if (resident && nc == 0 && kc == 0 && step > 0) {
                         const unsigned u = step - 1;
                         const bool done = warp_wait(b_empty((int)(u % kPipeStages)),
-                                                    (u / kPipeStages) & 1u, flag);
+                                                    (u / kPipeStages) & 1u, flag, A.wait_ns);
                         if (!producers_all(done)) {
                             ok = false;
                             break;
@@ -1137,11 +1177,11 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                     for (int kc = 0; kc < it.n_kc && ok; ++kc, ++step) {
                         const int s = (int)(step % kPipeStages);
                         const uint32_t ph = (step / kPipeStages) & 1u;
-                        if (!pipe_wait(b_full(s), ph, flag)) {
+                        if (!pipe_wait(b_full(s), ph, flag, A.wait_ns)) {
                             ok = false;
                             break;
                         }
-                        if (kc == 0 && !pipe_wait(acc_empty(buf), aph ^ 1u, flag)) {
+                        if (kc == 0 && !pipe_wait(acc_empty(buf), aph ^ 1u, flag, A.wait_ns)) {
                             ok = false;
                             break;
                         }
@@ -1161,6 +1201,9 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                     }
                 }
             }
+            // Every MMA issued here must complete before the tensor memory is freed.
+            mma_commit(drain);
+            *drained = drain_wait(drain) ? 1 : 0;
         }
     } else {
         // ------------------------------------------------------------------ epilogue
@@ -1177,7 +1220,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                 const uint32_t ph = (tile >> 1) & 1u;
                 // tcgen05.ld is warp-collective: the whole warp continues or stops together
                 // (warp_wait returns the same value on every lane).
-                if (!warp_wait(acc_full(buf), ph, flag)) {
+                if (!warp_wait(acc_full(buf), ph, flag, A.wait_ns)) {
                     ok = false;
                     break;
                 }
@@ -1227,10 +1270,13 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
         if (lane == 0) bulk_wait_all();
     }
 
-    if (tid == 0 && *flag) atomicOr(A.err, PG_DEVERR_TIMEOUT);
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    // If the drain never arrived, the columns stay allocated rather than be freed under an
+    // MMA that may still write them.
+    if (tid == 0 && (*flag || !*drained))
+        atomicOr(A.err, PG_DEVERR_TIMEOUT | (*drained ? 0u : PG_DEVERR_TMEM_HELD));
+    if (warp == 0 && *drained) {
         tc_fence_after();
         tmem_dealloc(tmem, (uint32_t)(2 * n_tile));
     }
@@ -1319,6 +1365,13 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
     if ((uintptr_t)a0.out % 16 != 0) return cudaErrorNotSupported;
     SeparableArgs a = a0;
     const bool pipe = t.separable_simple == 0;
+    // PG_DEBUG_STALL_PRODUCERS=1 (read at every call; for tests of the bounded waits) stops
+    // the operand producers (single-stage kernel: the MMA issue) before the first handoff and
+    // shortens every wait to 2 ms, so that the launch ends with PG_DEVERR_TIMEOUT having
+    // issued no MMA and started no store.
+    const char *stall = std::getenv("PG_DEBUG_STALL_PRODUCERS");
+    a.stall = (stall && stall[0] == '1') ? 1 : 0;
+    a.wait_ns = a.stall ? 2000000ull : 2000000000ull;
     int n_tile = t.n_tile;
     if (n_tile != 64 && n_tile != 128 && n_tile != 256) n_tile = 128;
     const int esz = dtype == PG_F32 ? 4 : 2;

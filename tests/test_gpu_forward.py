@@ -240,20 +240,19 @@ def test_register_and_staged_paths_agree_bitwise(pg):
         G1 = run(pg, wl, dtype=dtype)
         G2 = run(pg, wl, dtype=dtype, batch=padded, tuning={"path": 1, "gather_only": 1})
         assert np.array_equal(G1, G2)
-        # With scatter mode allowed, dense planes of the padded batch are summed in fixed point.
+        # With dense-plane mode allowed, dense planes of the padded batch walk each candidate's
+        # disc in shared memory: the same terms in the same order, identical bits.
         G3 = run(pg, wl, dtype=dtype, batch=padded, tuning={"path": 1})
-        if dtype == "f32":
-            assert_sum_rounding_only(G3, G1)
+        assert np.array_equal(G3, G1)
 
 
 @pytest.mark.parametrize("cutoff,periodic,shape", [
     ("sphere", False, (48, 48, 48)), ("box", False, (48, 48, 48)), ("box", True, (48, 48, 48)),
     ("sphere", True, (40, 44, 45)), ("box", False, (37, 52, 30))])
-def test_scatter_mode_every_cutoff_boundary_and_ragged_plane(pg, cutoff, periodic, shape):
-    # The run-based scatter mode against the gather mode on dense cells, for both cutoffs,
-    # open and periodic boundaries, and ragged planes that take the scalar store path.  The
-    # two modes add the same terms, one in float and one in exact fixed point: FP32 results
-    # agree to a few ulp of each grid's maximum, and both match the oracle.
+def test_dense_plane_mode_every_cutoff_boundary_and_ragged_plane(pg, cutoff, periodic, shape):
+    # Dense-plane mode against the gather mode on dense cells, for both cutoffs, open and
+    # periodic boundaries, and ragged planes that take the scalar store path.  The two modes
+    # add the same terms in the same order: identical bits, and both match the oracle.
     wl = synth.crystal_shaped(n_cells=10)
     wl.cutoff, wl.periodic = cutoff, periodic
     wl.nx, wl.ny, wl.nz = shape
@@ -262,32 +261,21 @@ def test_scatter_mode_every_cutoff_boundary_and_ragged_plane(pg, cutoff, periodi
         auto = run(pg, wl, dtype=dtype, tuning={"path": 1, "block_threads": 256})
         gather = run(pg, wl, dtype=dtype,
                      tuning={"path": 1, "block_threads": 256, "gather_only": 1})
-        if dtype == "f32":
-            assert_sum_rounding_only(auto, gather)
+        assert np.array_equal(auto.view(np.uint32), gather.view(np.uint32))
         for G in (auto, gather):
             grid_check(G[:4], prob, TOL[dtype], abs_tol=ABS_TOL[dtype])
 
 
-def assert_sum_rounding_only(a, b, rel=2e-6):
-    """a and b add the same terms in different arithmetic: per grid, max |a - b| is within
-    rel of the grid's maximum, and the zero pattern is identical."""
-    assert np.array_equal(a == 0, b == 0)
-    m = np.abs(b).reshape(b.shape[0], b.shape[1], -1).max(axis=2)
-    d = np.abs(a - b).reshape(b.shape[0], b.shape[1], -1).max(axis=2)
-    assert np.all(d <= rel * np.maximum(m, 1e-30)), float((d / np.maximum(m, 1e-30)).max())
-
-
-def test_scatter_and_gather_modes_on_dense_cells(pg):
-    # Dense periodic cells: planes with many candidates take the shared-memory scatter mode
-    # unless gather_only is set.  Each mode is bitwise stable across launch shapes; across
-    # modes only the rounding of the sums differs; both match the oracle.
+def test_dense_plane_and_gather_modes_on_dense_cells(pg):
+    # Dense periodic cells: planes with two or more candidates take dense-plane mode unless
+    # gather_only is set.  Both modes are bitwise equal to each other across launch shapes
+    # and match the oracle.
     wl = synth.crystal_shaped(n_cells=24)
     for dtype in ("f32", "f16"):
         auto = run(pg, wl, dtype=dtype, tuning={"path": 1, "block_threads": 256})
         gather = run(pg, wl, dtype=dtype,
                      tuning={"path": 1, "block_threads": 256, "gather_only": 1})
-        if dtype == "f32":
-            assert_sum_rounding_only(auto, gather)
+        assert np.array_equal(auto, gather)
         one = run(pg, wl, dtype=dtype,
                   tuning={"path": 1, "block_threads": 512, "chunk_planes": 1})
         assert np.array_equal(auto, one)
@@ -314,3 +302,31 @@ def test_chunk_orders_give_identical_bits(pg, kind):
                                       dtype="f16"))
     assert pg.sync_status() == 0
     assert torch.equal(outs[0], outs[1])
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_dense_plane_mode_wide_discs(pg, periodic):
+    # Discs wider and taller than a warp (r_c = 1.5 A on a 0.05 A grid: about 60 voxels
+    # across), so that the dense-plane walk takes its columns 32 at a time and its row table
+    # in several parts; atoms near the faces so that periodic discs wrap.  Bitwise equal to
+    # the gather, and equal to the oracle.
+    rng = np.random.default_rng(41)
+    n = 64
+    h = 0.05
+    mols = []
+    for _ in range(3):
+        pos = rng.uniform(0.0, n * h, (40, 3))
+        pos[:4] = [[0.02, 0.03, 3.1], [3.15, 0.1, 0.05], [1.6, 1.6, 1.6], [1.62, 1.58, 1.61]]
+        mols.append(pos)
+    el = [np.where(rng.uniform(size=40) < 0.7, 0, 1) for _ in range(3)]
+    nb = synth._pack(mols, el, np.zeros((3, 3)), np.full((3, 3), h))
+    wl = synth.plain_small(n_mol=1)
+    wl.nx = wl.ny = wl.nz = n
+    wl.periodic = periodic
+    wl.cutoff_k = 3.0 if not periodic else 2.0    # r_c = 1.0 A < L / 2 = 1.6 A when periodic
+    for dtype in ("f32", "f16"):
+        auto = run(pg, wl, dtype=dtype, batch=nb, tuning={"path": 1, "block_threads": 128})
+        gather = run(pg, wl, dtype=dtype, batch=nb, tuning={"path": 1, "gather_only": 1})
+        assert np.array_equal(auto, gather)
+        grid_check(auto, oracle.Problem.from_workload(wl, batch=nb), TOL[dtype],
+                   abs_tol=ABS_TOL[dtype])

@@ -123,3 +123,57 @@ def test_full_precision_form_batch_sampled(pg):
     sub = wl.batch.subset(pick)
     grid_check(G[pick].float().cpu().numpy(), oracle.Problem.from_workload(wl, batch=sub),
                SEPARABLE_TOL, abs_tol=ABS_TOL["f16"])
+
+
+def test_factor_tables_bitwise_across_launch_shapes(pg):
+    # With a separable cutoff, molecules of at most 32 atoms use per-chunk factor tables.  The
+    # table entries are the values the kernel would compute per voxel, so every chunk size,
+    # chunk order and block size gives identical bits, matching the oracle.
+    wl = synth.precision_form_integral(n_mol=12)
+    db = pg.DeviceBatch.from_numpy(wl.batch)
+    grid = pg.Grid.from_workload(wl)
+    ref = None
+    for threads in (128, 256, 512):
+        for cp in (1, 3, 8, 64):
+            for order in (0, 1):
+                G = pg.voxelize_tuned(db, grid, {"path": 1, "block_threads": threads,
+                                                 "chunk_planes": cp, "chunk_order": order},
+                                      dtype="f32")
+                assert pg.sync_status() == 0
+                if ref is None:
+                    ref = G.clone()
+                assert torch.equal(G, ref), (threads, cp, order)
+    pick = [0, 5, 11]
+    grid_check(ref[pick].cpu().numpy(),
+               oracle.Problem.from_workload(wl, batch=wl.batch.subset(pick)), TOL["f32"],
+               abs_tol=ABS_TOL["f32"])
+
+
+@pytest.mark.parametrize("cutoff,periodic", [("box", False), ("none", False), ("box", True)])
+def test_factor_tables_with_large_molecules_interleaved(pg, cutoff, periodic):
+    # Small molecules (factor tables) interleaved with 40-atom ones (staged path, which reuses
+    # the table's shared memory), one-plane chunks so that warps switch between the two often.
+    wl = integral(synth.plain_small(n_mol=6))
+    wl.cutoff, wl.periodic = cutoff, periodic
+    wl.cutoff_k = 2.5
+    b = wl.batch
+    coords, elems = [], []
+    rng = np.random.default_rng(5)
+    for i in range(b.n_mol):
+        s = b.atoms_of(i)
+        c, e = b.coords[s], b.elem[s]
+        if i % 2:
+            extra = c[rng.integers(0, len(c), 40 - len(c))] + rng.normal(0, 0.7, (40 - len(c), 3))
+            c = np.concatenate([c, extra]).astype(np.float32)
+            e = np.concatenate([e, rng.integers(0, 5, 40 - len(e))]).astype(np.int32)
+        coords.append(c)
+        elems.append(e)
+    nb = synth._pack(coords, elems, b.origin, b.spacing)
+    db = pg.DeviceBatch.from_numpy(nb)
+    grid = pg.Grid.from_workload(wl)
+    outs = [pg.voxelize_tuned(db, grid, {"path": 1, "chunk_planes": cp}, dtype="f32")
+            for cp in (1, 8)]
+    assert pg.sync_status() == 0
+    assert torch.equal(outs[0], outs[1])
+    grid_check(outs[0].cpu().numpy(), oracle.Problem.from_workload(wl, batch=nb), TOL["f32"],
+               abs_tol=ABS_TOL["f32"])

@@ -204,3 +204,36 @@ def test_packed_tiles_with_uneven_atom_counts(pg):
         grid_check(G, oracle.Problem.from_workload(wl, batch=nb), SEPARABLE_TOL,
                    abs_tol=ABS_TOL["f16"])
 
+
+
+@pytest.mark.parametrize("simple", [0, 1])
+@pytest.mark.parametrize("packed", [False, True])
+def test_bounded_waits_give_up_without_faulting_then_recover(pg, monkeypatch, simple, packed):
+    # Failure detection without a GPU fault: PG_DEBUG_STALL_PRODUCERS=1 stops the operand
+    # producers (the single-stage kernel: its MMA issue) before the first handoff and shortens
+    # every wait to 2 ms.  No MMA is issued and no store starts; each CTA's bounded waits give
+    # up, it confirms through the drain barrier that no MMA is outstanding, frees its tensor
+    # memory and returns.  The host reads PG_ERR_TIMEOUT with the timeout bit (and not the bit
+    # for kept tensor memory); the next normal call on the same device matches the oracle.
+    from paper_2211_08506_gb300 import binding as B
+
+    wl = small("box", n_mol=9, shape=(32, 32, 32) if not packed else (16, 16, 32))
+    if packed:
+        wl.n_channels, wl.sigma = 1, np.array([0.5], np.float32)
+        wl.batch.elem[:] = 0
+    db = pg.DeviceBatch.from_numpy(wl.batch)
+    grid = pg.Grid.from_workload(wl)
+    tuning = {"path": 2, "separable_simple": simple}
+    out = torch.full(grid.out_shape(wl.batch.n_mol), 7.0, dtype=torch.float16, device="cuda")
+    monkeypatch.setenv("PG_DEBUG_STALL_PRODUCERS", "1")
+    pg.voxelize_tuned(db, grid, tuning, dtype="f16", out=out)
+    st, bits = B.pg_sync_status(torch.cuda.current_stream().cuda_stream)
+    assert st == B.PG_ERR_TIMEOUT, B.last_error()
+    assert bits & B.PG_DEVERR_TIMEOUT and not bits & B.PG_DEVERR_TMEM_HELD
+    if not simple:
+        assert torch.all(out == 7.0)  # no store started
+    monkeypatch.delenv("PG_DEBUG_STALL_PRODUCERS")
+    pg.voxelize_tuned(db, grid, tuning, dtype="f16", out=out)
+    assert pg.sync_status() == 0
+    grid_check(out.float().cpu().numpy(), oracle.Problem.from_workload(wl), SEPARABLE_TOL,
+               abs_tol=ABS_TOL["f16"])
