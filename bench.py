@@ -573,6 +573,18 @@ def rank_workload(ses, name, n_mol=0):
     return wl, first, whole
 
 
+def _nvtx(torch, name):
+    """Open (name given) or close an NVTX range for profiler timelines; a no-op where torch
+    has no NVTX support."""
+    try:
+        if name is None:
+            torch.cuda.nvtx.range_pop()
+        else:
+            torch.cuda.nvtx.range_push(name)
+    except Exception:
+        pass
+
+
 def measure(ses, wl, dtype, path, tag, W=None, e2e=True):
     """Autotune, capture and time one workload: K graph replays of the forward launch (and
     of the adjoint when W, the upstream gradient, is given) after W warm-up replays, on the
@@ -621,6 +633,7 @@ def measure(ses, wl, dtype, path, tag, W=None, e2e=True):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ev_mid = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ses.sampler.mark("start", tag)
+    _nvtx(torch, f"timed graph replays: {tag}")
     with torch.cuda.stream(stream):
         ev[0].record(stream)
         for i in range(args.steps):
@@ -630,6 +643,7 @@ def measure(ses, wl, dtype, path, tag, W=None, e2e=True):
                 graph_bwd.replay()
             ev[i + 1].record(stream)
     torch.cuda.synchronize()
+    _nvtx(torch, None)
     ses.sampler.mark("stop", tag)
     ses.barrier()
     per_fwd = [ev[i].elapsed_time(ev_mid[i]) for i in range(args.steps)]
@@ -663,11 +677,15 @@ def measure(ses, wl, dtype, path, tag, W=None, e2e=True):
             d2h += grad_host.numel() * grad_host.element_size()
 
         def e2e_step():
-            plan.run(*host, out=out, **extra)
-            if Wd is not None:
-                api.voxelize_backward(db, grid, Wd, grad_coords=grad, stream=stream)
-                grad_host.copy_(grad, non_blocking=True)
-                stream.synchronize()
+            if Wd is None:
+                plan.run(*host, out=out, stream=stream, **extra)
+                return
+            # Forward from the host batch, the adjoint and the gradient's copy to the host,
+            # with one synchronization (pg_plan_wait) at the end of the step.
+            plan.launch(*host, out=out, stream=stream, **extra)
+            api.voxelize_backward(db, grid, Wd, grad_coords=grad, stream=stream)
+            grad_host.copy_(grad, non_blocking=True)
+            plan.wait(stream)
 
         with torch.cuda.stream(stream):
             for _ in range(max(3, args.warmup)):
@@ -682,10 +700,11 @@ def measure(ses, wl, dtype, path, tag, W=None, e2e=True):
         plan.close()
         e2e_res = {"value": units / e2e_s, "unit": "grids/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h,
-                   "api": "pg_plan_run (pinned host CSR batch -> graph: H2D + kernel -> "
-                          "error word D2H)"
-                          + (" + pg_voxelize_backward -> gradient D2H" if Wd is not None
-                             else "")}
+                   "api": ("pg_plan_run (pinned host CSR batch -> graph: H2D + kernel -> "
+                           "error word D2H)" if Wd is None else
+                           "pg_plan_launch (pinned host CSR batch -> graph: H2D + kernel -> "
+                           "error word D2H) + pg_voxelize_backward + gradient D2H + "
+                           "pg_plan_wait")}
 
     kernel = ("separable" if tuning.get("path") == 2
               else "cell" if wl.batch.cell is not None else "direct")

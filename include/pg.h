@@ -165,10 +165,12 @@ typedef struct {
  *                  path 2 also sizes its resident K chunks so that two CTAs fit an SM
  *   store_hint     0: default global stores; 1: streaming (evict-first) stores
  *   n_tile         separable path: output columns per tensor-core tile (64, 128 or 256)
- *   gather_only    direct path: 0 lets planes with many candidate atoms accumulate in
- *                  shared memory in exact fixed point (scatter mode; batches of molecules with
- *                  more than 32 atoms on average); 1 gathers every plane in float.  The two
- *                  differ only in the rounding of each voxel's sum.
+ *   gather_only    direct path: 0 lets per-axis factors come from tables in shared memory:
+ *                  in the point form with a cutoff (batches of molecules with more than 32
+ *                  atoms on average), planes with 2 to 32 staged candidates take each one's z
+ *                  factors from a per-plane table; in the voxel-integrated form with no or a box
+ *                  cutoff, every chunk's atoms get y and z factor tables.  1 computes every
+ *                  factor where it is used.  Both give identical bits.
  *   chunk_planes   direct path: x-planes per dynamically scheduled work chunk (1..64; 0 = 8)
  *   separable_simple  separable path: 0 = warp-specialized pipeline (default), 1 = one-stage
  *                  kernel.  Both accumulate the same BF16 products in the same order.
@@ -294,7 +296,10 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
 pg_status pg_get_tuning(const pg_batch *batch, const pg_grid *grid, int32_t out_dtype,
                         int32_t path, pg_tuning *tuning);
 
-/* Tuning cache as text lines "key value..."; load merges into the in-memory cache. */
+/* Tuning cache as text lines "key value..."; load merges into the in-memory cache.
+   If the environment variable PG_TUNING_CACHE names a file, the library merges it into the
+   cache on first use (when it exists) and pg_autotune rewrites it with the whole cache after
+   every successful tuning (PG_ERR_INVALID_ARG if it cannot be written). */
 pg_status pg_tuning_save(const char *file);
 pg_status pg_tuning_load(const char *file);
 
@@ -316,6 +321,21 @@ pg_status pg_plan_create(pg_plan **plan, const pg_grid *grid, int32_t out_dtype,
                          int32_t max_mol, int32_t max_atoms);
 pg_status pg_plan_run(pg_plan *plan, const pg_batch *host_batch, void *out, void *stream);
 pg_status pg_plan_destroy(pg_plan *plan);
+
+/*
+ * pg_plan_run in two halves, so that more work can follow the plan on the stream before the
+ * one host synchronization (in a differentiation step: the adjoint and the copy of the
+ * coordinate gradient to the host).
+ *   pg_plan_launch  everything pg_plan_run does up to and including the graph launch on
+ *                   `stream`; returns without synchronizing.  Host inputs must stay unchanged
+ *                   until the wait (pinned ones are copied by the graph).  One launch per
+ *                   plan may be outstanding: a second launch before the wait returns
+ *                   PG_ERR_INVALID_ARG.
+ *   pg_plan_wait    synchronizes `stream` and reports the device error word of the plan's
+ *                   outstanding launch as pg_plan_run would (PG_OK if none is outstanding).
+ */
+pg_status pg_plan_launch(pg_plan *plan, const pg_batch *host_batch, void *out, void *stream);
+pg_status pg_plan_wait(pg_plan *plan, void *stream);
 
 /* Free per-device state and the tuning cache.  Later calls re-create what they need. */
 void pg_shutdown(void);

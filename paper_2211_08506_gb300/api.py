@@ -238,11 +238,7 @@ class Plan:
         B.check(st)
         self._h = h
 
-    def run(self, coords, elem, mol_off, origin, spacing, out: torch.Tensor, stream=None,
-            weight=None, cell=None):
-        """Host arrays (numpy or CPU tensors, pinned or pageable) -> `out` on the device;
-        `spacing` may be None when `cell` is given.  Synchronous: returns after the device
-        error word has been read back."""
+    def _host_batch(self, coords, elem, mol_off, origin, spacing, weight, cell):
         keep = []
 
         def host(a, dt):
@@ -261,8 +257,31 @@ class Plan:
                         elem=host(elem, np.int32), mol_off=host(mol_off, np.int32),
                         origin=host(origin, np.float32), spacing=opt(spacing),
                         weight=opt(weight), cell=opt(cell))
+        return hb, keep
+
+    def run(self, coords, elem, mol_off, origin, spacing, out: torch.Tensor, stream=None,
+            weight=None, cell=None):
+        """Host arrays (numpy or CPU tensors, pinned or pageable) -> `out` on the device;
+        `spacing` may be None when `cell` is given.  Synchronous: returns after the device
+        error word has been read back."""
+        hb, keep = self._host_batch(coords, elem, mol_off, origin, spacing, weight, cell)
         B.check(B.pg_plan_run(self._h, hb, _ptr(out), _stream(stream)))
         return out
+
+    def launch(self, coords, elem, mol_off, origin, spacing, out: torch.Tensor, stream=None,
+               weight=None, cell=None):
+        """pg_plan_launch: as run(), but returns once the graph is enqueued; the host arrays
+        must stay unchanged until wait()."""
+        hb, keep = self._host_batch(coords, elem, mol_off, origin, spacing, weight, cell)
+        self._keep = (hb, keep)
+        B.check(B.pg_plan_launch(self._h, hb, _ptr(out), _stream(stream)))
+        return out
+
+    def wait(self, stream=None):
+        """pg_plan_wait: synchronize the stream and check the outstanding launch's error word."""
+        st = B.pg_plan_wait(self._h, _stream(stream))
+        self._keep = None
+        B.check(st)
 
     def close(self):
         if self._h:

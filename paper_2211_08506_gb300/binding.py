@@ -36,7 +36,7 @@ EXPORTED = (
     "pg_voxelize_backward", "pg_sync_status", "pg_autotune", "pg_get_tuning",
     "pg_tuning_save", "pg_tuning_load", "pg_plan_create", "pg_plan_run", "pg_plan_destroy",
     "pg_shutdown", "pg_voxelize_noalloc", "pg_refine", "pg_refine_work_floats",
-    "pg_voxelize_backward_ex",
+    "pg_voxelize_backward_ex", "pg_plan_launch", "pg_plan_wait",
 )
 
 
@@ -127,6 +127,8 @@ def load() -> ctypes.CDLL:
         lib.pg_tuning_load.argtypes = [ctypes.c_char_p]
         lib.pg_plan_create.argtypes = [P(vp), P(pg_grid), i32, i32, i32, i32]
         lib.pg_plan_run.argtypes = [vp, P(pg_batch), vp, vp]
+        lib.pg_plan_launch.argtypes = [vp, P(pg_batch), vp, vp]
+        lib.pg_plan_wait.argtypes = [vp, vp]
         lib.pg_plan_destroy.argtypes = [vp]
         lib.pg_shutdown.restype = None
         lib.pg_voxelize_noalloc.argtypes = [P(pg_batch), P(pg_grid), i32, vp, vp,
@@ -138,7 +140,7 @@ def load() -> ctypes.CDLL:
         for name in ("pg_voxelize", "pg_voxelize_tuned", "pg_voxelize_backward",
                      "pg_sync_status", "pg_autotune", "pg_get_tuning", "pg_tuning_save",
                      "pg_tuning_load", "pg_plan_create", "pg_plan_run", "pg_plan_destroy",
-                     "pg_voxelize_noalloc", "pg_refine"):
+                     "pg_voxelize_noalloc", "pg_refine", "pg_plan_launch", "pg_plan_wait"):
             getattr(lib, name).restype = i32
         _lib = lib
         return lib
@@ -236,6 +238,14 @@ def pg_plan_create(grid, out_dtype, path, max_mol, max_atoms):
 
 def pg_plan_run(plan, host_batch, out, stream):
     return load().pg_plan_run(plan, ctypes.byref(host_batch), out, stream)
+
+
+def pg_plan_launch(plan, host_batch, out, stream):
+    return load().pg_plan_launch(plan, ctypes.byref(host_batch), out, stream)
+
+
+def pg_plan_wait(plan, stream):
+    return load().pg_plan_wait(plan, stream)
 
 
 def pg_plan_destroy(plan):

@@ -25,10 +25,10 @@
 // across block sizes, occupancy, store hints and chunk sizes, and equal to the unstaged
 // fallback used when an item has more than kStageCap candidates.
 //
-// Dense planes (kDiscMin or more staged candidates) can instead be accumulated in dense-plane
-// mode (see disc_plane), in a kernel instantiation of its own: the warp visits each
-// candidate's disc in the plane rather than every voxel for every candidate.  It adds the same
-// terms in the same order, so its results are bitwise identical to the gather's.
+// Planes with several staged candidates (kZtabMin to kZtabCands) can instead take their z
+// factors from a per-plane table (z-table mode, see ztab_plane), in a kernel instantiation of
+// its own.  It adds the same terms in the same order, so its results are bitwise identical to
+// the gather's.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -40,8 +40,8 @@ namespace pgi {
 
 namespace {
 
-// Staged candidates from which a plane is accumulated in dense-plane mode instead of gathered.
-constexpr int kDiscMin = 2;
+// Staged candidates from which a plane takes its z factors from a table.
+constexpr int kZtabMin = 2;
 
 __device__ __forceinline__ float ex2_approx(float x)
 {
@@ -266,22 +266,21 @@ __device__ __forceinline__ void blocked_plane(T *out, int ny, int nz, int rpg, i
     }
 }
 
-// Voxel-integrated form with a separable cutoff (none or box), molecules of at most 32 atoms:
-// the per-axis factors do not depend on the plane, so the warp computes them once per chunk
-// into a table in shared memory (Sec. VI-A's per-axis tables): for the channel's i-th atom,
-// row i of the table (erf_table_stride floats) holds its y factor on each row y and then its
-// z factor on each column z, each exactly the value erf_axis gives for that row or column,
-// zeroed outside a box cutoff.  A plane is then walked in the passes of blocked_plane, and every term is the
-// atom's x factor times its table entries in the same order of operations as blocked_plane
-// uses, so the two give identical bits.  cand / dx / fx / ti are the lane's own atom's plane
-// candidacy, x displacement, x factor and table row.
-template <typename T, int VEC, int CUT, bool PER, int HINT, bool WGT>
+// Voxel-integrated form with a separable cutoff (none or box): the per-axis factors do not
+// depend on the plane, so the warp computes them once per chunk into a table in shared memory
+// (Sec. VI-A's per-axis tables): for the chunk's i-th atom of the channel, row i of the table
+// (erf_table_stride floats) holds its y factor on each row y and then its z factor on each
+// column z, each exactly the value erf_axis gives for that row or column, zeroed outside a box
+// cutoff.  A plane is then walked in the passes of blocked_plane, and every term is the atom's
+// x factor times its table entries in the same order of operations as blocked_plane uses, so
+// the two give identical bits.  for_each(cy, wy, cz, wz, f) calls f(dx, fx, w, ti) - the
+// candidate's x displacement, x factor, weight and table row - for the candidates that can
+// reach the pass's box of voxel centres, in atom order.
+template <typename T, int VEC, int CUT, bool PER, int HINT, typename ForEach>
 __device__ __forceinline__ void table_plane(T *out, const float *tab, int ny, int nz, int rpg,
                                             int act, int my_row, int z0, int lane, float r2,
-                                            float rc, bool cand, float dx, float fx, int ti,
-                                            float ay, float az, float aw, float oy, float oz,
-                                            float hy, float hz, float Ly, float iLy, float Lz,
-                                            float iLz)
+                                            float oy, float oz, float hy, float hz,
+                                            ForEach for_each)
 {
     const int tw = erf_table_stride(ny, nz);
     const int tyw = (ny + 3) & ~3;
@@ -297,21 +296,12 @@ __device__ __forceinline__ void table_plane(T *out, const float *tab, int ny, in
         float acc0[VEC], acc1[VEC];
 #pragma unroll
         for (int k = 0; k < VEC; ++k) acc0[k] = acc1[k] = 0.0f;
-        const bool hit = cand && reaches<CUT, PER>(dx, ay, az, cy, wy, cz, wz, rc, Ly, iLy, Lz,
-                                                   iLz);
-        unsigned m = __ballot_sync(0xffffffffu, hit);
-        while (m) {
-            const int src = __ffs(m) - 1;
-            m &= m - 1;
-            const float sdx = __shfl_sync(0xffffffffu, dx, src);
-            const float sfx = __shfl_sync(0xffffffffu, fx, src);
-            const float sw = WGT ? __shfl_sync(0xffffffffu, aw, src) : 1.0f;
-            const int sti = __shfl_sync(0xffffffffu, ti, src);
-            const float *ty = tab + sti * tw;
+        for_each(cy, wy, cz, wz, [&](float dx, float fx, float w, int ti) {
+            const float *ty = tab + ti * tw;
             const float *tz = ty + tyw;
-            const bool xout = CUT == PG_CUTOFF_BOX && sdx * sdx > r2;
-            const float ea = sw * (xout ? 0.0f : sfx * ty[ra]);
-            const float eb = sw * (xout ? 0.0f : sfx * ty[rb]);
+            const bool xout = CUT == PG_CUTOFF_BOX && dx * dx > r2;
+            const float ea = w * (xout ? 0.0f : fx * ty[ra]);
+            const float eb = w * (xout ? 0.0f : fx * ty[rb]);
             float ez[VEC];
             if constexpr (VEC % 4 == 0) {
 #pragma unroll
@@ -331,7 +321,7 @@ __device__ __forceinline__ void table_plane(T *out, const float *tab, int ny, in
                 acc0[k] = fmaf(ea, ez[k], acc0[k]);
                 acc1[k] = fmaf(eb, ez[k], acc1[k]);
             }
-        }
+        });
         if (lane < act) {
             if (ya < ny) store_lane<T, VEC, HINT>(out, (ya * nz + z0) / VEC, acc0);
             if (yb < ny) store_lane<T, VEC, HINT>(out, (yb * nz + z0) / VEC, acc1);
@@ -339,6 +329,42 @@ __device__ __forceinline__ void table_plane(T *out, const float *tab, int ny, in
     }
 }
 
+// Fills rows 0 .. n - 1 of a voxel-integrated factor table (see table_plane), 32 entries per
+// step across the warp; atom(i) gives row i's atom position {y, z} (a float2).
+template <int CUT, bool PER, typename AtomYZ>
+__device__ __forceinline__ void build_erf_table(float *tab, int n, int ny, int nz, int lane,
+                                                float q, float r2, float kf, float oy, float oz,
+                                                float hy, float hz, float Ly, float iLy, float Lz,
+                                                float iLz, AtomYZ atom)
+{
+    const int tw = erf_table_stride(ny, nz);
+    const int tyw = (ny + 3) & ~3;
+    const int total = n * tw;
+    for (int base = 0; base < total; base += 32) {
+        const int idx = base + lane;
+        const int row = idx / tw;
+        const int j = idx - row * tw;
+        const float2 a = atom(min(row, n - 1));
+        if (idx < total) {
+            float v = 0.0f;
+            if (j < tyw) {
+                if (j < ny) {
+                    float dy = fmaf((float)j + 0.5f, hy, oy) - a.x;
+                    if (PER) dy = wrap(dy, Ly, iLy);
+                    v = erf_axis(dy, hy, kf);
+                    if (CUT == PG_CUTOFF_BOX && dy * dy > r2) v = 0.0f;
+                }
+            } else if (j - tyw < nz) {
+                float dz = fmaf((float)(j - tyw) + 0.5f, hz, oz) - a.y;
+                if (PER) dz = wrap(dz, Lz, iLz);
+                v = z_factor<CUT, 1>(dz, q, r2, kf, hz);
+            }
+            tab[idx] = v;
+        }
+    }
+}
+
+// Index i wrapped into [0, n) (periodic axes).
 __device__ __forceinline__ int wrap_index(int i, int n)
 {
     if (i >= 0 && i < n) return i;
@@ -348,136 +374,111 @@ __device__ __forceinline__ int wrap_index(int i, int n)
     return r < 0 ? r + n : r;
 }
 
-// Index range [lo, hi] of voxel centres o + (i+1/2)h within rho of a (widened by one voxel
-// each side): clamped to the grid, or for periodic cells at most n consecutive (unwrapped)
-// indices so that no voxel is visited twice.
-template <bool PER>
-__device__ __forceinline__ void disc_range(float a, float rho, float o, float inv_h, int n,
-                                           int &lo, int &hi)
-{
-    lo = (int)fmaxf(floorf((a - rho - o) * inv_h - 0.5f), -1e8f) - 1;
-    hi = (int)fminf(ceilf((a + rho - o) * inv_h - 0.5f), 1e8f) + 1;
-    if (PER) {
-        if (hi - lo + 1 > n) hi = lo + n - 1;
-    } else {
-        lo = max(lo, 0);
-        hi = min(hi, n - 1);
-    }
-}
-
-// Dense-plane mode (Sec. VI-A/VI-B visit only each atom's non-zero box; here the box is cut
-// down to the candidate's disc in the plane).  The warp takes the staged candidates one at a
-// time, in atom order, and for each visits only the voxels of its disc's bounding square,
-// adding the candidate's terms to a per-warp FP32 plane accumulator in shared memory; then it
-// converts and stores the whole plane and leaves the accumulator zeroed.  Every term is the
-// same row factor times the same z factor, under the same exact cutoff test, as in the
-// gather, and every voxel receives its terms in atom order: the plane is bitwise identical to
-// the gathered one, whatever the launch shape.
-//
-// Per candidate the lanes first build a table of the square's rows (row factor, dx^2 + dy^2,
-// row offset in the plane), kDiscRows rows at a time.  Each lane then owns one column of the
-// square and keeps its z factor and dz in registers; a square of W <= 32 columns splits the
-// warp into 32 / W groups of W lanes, and the groups step through the rows together, two rows
-// per step so that both accumulator loads are in flight at once.  Wider squares take their
-// columns 32 at a time.
+// Z-table mode (Sec. VI-A's per-axis tables) for planes with several staged candidates, at
+// most kZtabCands: a candidate's z factors and z displacements do not depend on the row, so the
+// warp computes them once per plane into a table in shared memory, ztab[j][z] and
+// ztab[kZtabCands + j][z] (rows of nz rounded up to 4 floats), instead of in every pass.  The
+// plane is then walked in the passes of blocked_plane, and every term is formed from the same
+// values in the same order as there: identical bits.
 template <typename T, int VEC, int CUT, bool PER, int HINT, bool WGT>
-__device__ __forceinline__ void disc_plane(T *out, float *acc, float4 *rowtab, const float4 *stage,
-                                           int count, int ny, int nz, int lane, float q, float r2,
-                                           float rc, float oy, float oz, float hy, float hz,
-                                           float Ly, float iLy, float Lz, float iLz)
+__device__ __forceinline__ void ztab_plane(T *out, float *ztab, const float4 *stage, int count,
+                                           int ny, int nz, int rpg, int act, int my_row, int z0,
+                                           int lane, float q, float r2, float rc, float oy,
+                                           float oz, float hy, float hz, float Ly, float iLy,
+                                           float Lz, float iLz)
 {
-    const float inv_hy = 1.0f / hy, inv_hz = 1.0f / hz;
-    for (int j = 0; j < count; ++j) {
-        const float4 st = stage[j];
-        const float dx = st.x, ay = st.y, az = st.z;
-        const float w = WGT ? st.w : 1.0f;
-        const float dx2 = dx * dx;
-        float rho = rc;
-        if (CUT == PG_CUTOFF_SPHERE) rho = sqrtf(fmaxf(fmaf(-dx, dx, rc * rc), 0.0f));
-        int ylo, yhi, zlo, zhi;
-        disc_range<PER>(ay, rho, oy, inv_hy, ny, ylo, yhi);
-        disc_range<PER>(az, rho, oz, inv_hz, nz, zlo, zhi);
-        const int H = yhi - ylo + 1, W = zhi - zlo + 1;
-        if (H <= 0 || W <= 0) continue;
-        const int wb = min(W, 32);
-        const int groups = 32 / wb;
-        const int g = lane / wb;
-        const int cl = lane - g * wb;
-        for (int r0 = 0; r0 < H; r0 += kDiscRows) {
-            const int nr = min(H - r0, kDiscRows);
-            // Orders this candidate's table (and accumulator updates) after every lane's use
-            // of the previous table and the previous candidate's updates.
-            __syncwarp();
-            for (int t = lane; t < nr; t += 32) {
-                int y = ylo + r0 + t;
-                if (PER) y = wrap_index(y, ny);
-                float dy = fmaf((float)y + 0.5f, hy, oy) - ay;
-                if (PER) dy = wrap(dy, Ly, iLy);
-                const float dxy2 = fmaf(dy, dy, dx2);
-                const float e = w * row_factor<CUT, 0>(0.0f, dy, dx2, dxy2, q, r2, 0.0f, hy);
-                rowtab[t] = make_float4(e, dxy2, __int_as_float(y * nz), 0.0f);
-            }
-            __syncwarp();
-            if (g >= groups) continue;
-            for (int c0 = 0; c0 < W; c0 += 32) {
-                const int col = c0 + cl;
-                if (col >= W) continue;
-                int z = zlo + col;
-                if (PER) z = wrap_index(z, nz);
+    const int nz4 = (nz + 3) & ~3;
+    float *const tez = ztab;
+    float *const tdz = ztab + kZtabCands * nz4;
+    // Table: entry (j, z) for j < count, z < nz, 32 entries per step; (j, z) advances by 32.
+    {
+        int j = lane / nz4, z = lane - (lane / nz4) * nz4;
+        const int dj = 32 / nz4, dzs = 32 - (32 / nz4) * nz4;
+        for (int base = 0; base < count * nz4; base += 32) {
+            if (j < count && z < nz) {
+                const float az = stage[j].z;
                 float dz = fmaf((float)z + 0.5f, hz, oz) - az;
                 if (PER) dz = wrap(dz, Lz, iLz);
-                const float ez = z_factor<CUT, 0>(dz, q, r2, 0.0f, hz);
-                float *const accz = acc + z;
-                int r = g;
-                for (; r + groups < nr; r += 2 * groups) {
-                    const float4 ta = rowtab[r], tb = rowtab[r + groups];
-                    float *pa = accz + __float_as_int(ta.z);
-                    float *pb = accz + __float_as_int(tb.z);
-                    const float va = *pa, vb = *pb;
-                    if (CUT == PG_CUTOFF_SPHERE) {
-                        if (fmaf(dz, dz, ta.y) <= r2) *pa = fmaf(ta.x, ez, va);
-                        if (fmaf(dz, dz, tb.y) <= r2) *pb = fmaf(tb.x, ez, vb);
-                    } else {
-                        *pa = fmaf(ta.x, ez, va);
-                        *pb = fmaf(tb.x, ez, vb);
-                    }
-                }
-                if (r < nr) {
-                    const float4 ta = rowtab[r];
-                    float *pa = accz + __float_as_int(ta.z);
-                    if (CUT != PG_CUTOFF_SPHERE || fmaf(dz, dz, ta.y) <= r2)
-                        *pa = fmaf(ta.x, ez, *pa);
-                }
+                tez[j * nz4 + z] = z_factor<CUT, 0>(dz, q, r2, 0.0f, hz);
+                tdz[j * nz4 + z] = dz;
+            }
+            j += dj;
+            z += dzs;
+            if (z >= nz4) {
+                z -= nz4;
+                ++j;
             }
         }
     }
     __syncwarp();
-
-    // Convert, store, and leave the accumulator zeroed for the next plane.
-    const int nvec = ny * nz / VEC;
-    for (int v = lane; v < nvec; v += 32) {
-        float a[VEC];
-        if constexpr (VEC % 4 == 0) {
+    const float cz = fmaf(0.5f * (float)(nz - 1) + 0.5f, hz, oz);
+    const float wz = 0.5f * (float)(nz - 1) * hz;
+    for (int y0 = 0; y0 < ny; y0 += 2 * rpg) {
+        const int y_end = min(y0 + 2 * rpg, ny) - 1;
+        const float cy = fmaf(0.5f * (float)(y0 + y_end) + 0.5f, hy, oy);
+        const float wy = 0.5f * (float)(y_end - y0) * hy;
+        const int ya = y0 + my_row, yb = ya + rpg;
+        const float vya = fmaf((float)ya + 0.5f, hy, oy);
+        const float vyb = fmaf((float)yb + 0.5f, hy, oy);
+        float acc0[VEC], acc1[VEC];
 #pragma unroll
-            for (int k = 0; k < VEC; k += 4) {
-                float4 *p = reinterpret_cast<float4 *>(acc + v * VEC) + k / 4;
-                const float4 f = *p;
-                *p = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                a[k] = f.x;
-                a[k + 1] = f.y;
-                a[k + 2] = f.z;
-                a[k + 3] = f.w;
+        for (int k = 0; k < VEC; ++k) acc0[k] = acc1[k] = 0.0f;
+        bool ok = false;
+        if (lane < count) {
+            const float4 st = stage[lane];
+            ok = reaches<CUT, PER>(st.x, st.y, st.z, cy, wy, cz, wz, rc, Ly, iLy, Lz, iLz);
+        }
+        unsigned m = __ballot_sync(0xffffffffu, ok);
+        while (m) {
+            const int j = __ffs(m) - 1;
+            m &= m - 1;
+            const float4 st = stage[j];
+            const float dx = st.x, ay = st.y;
+            const float w = WGT ? st.w : 1.0f;
+            const float dx2 = dx * dx;
+            float dya = vya - ay, dyb = vyb - ay;
+            if (PER) {
+                dya = wrap(dya, Ly, iLy);
+                dyb = wrap(dyb, Ly, iLy);
             }
-        } else {
+            const float dxya = fmaf(dya, dya, dx2), dxyb = fmaf(dyb, dyb, dx2);
+            const float ea = w * row_factor<CUT, 0>(0.0f, dya, dx2, dxya, q, r2, 0.0f, hy);
+            const float eb = w * row_factor<CUT, 0>(0.0f, dyb, dx2, dxyb, q, r2, 0.0f, hy);
+            float ez[VEC], dz[VEC];
+            const float *pez = tez + j * nz4 + z0;
+            const float *pdz = tdz + j * nz4 + z0;
+            if constexpr (VEC % 4 == 0) {
+#pragma unroll
+                for (int k = 0; k < VEC; k += 4) {
+                    const float4 e4 = *reinterpret_cast<const float4 *>(pez + k);
+                    const float4 d4 = *reinterpret_cast<const float4 *>(pdz + k);
+                    ez[k] = e4.x, ez[k + 1] = e4.y, ez[k + 2] = e4.z, ez[k + 3] = e4.w;
+                    dz[k] = d4.x, dz[k + 1] = d4.y, dz[k + 2] = d4.z, dz[k + 3] = d4.w;
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) {
+                    ez[k] = pez[k];
+                    dz[k] = pdz[k];
+                }
+            }
 #pragma unroll
             for (int k = 0; k < VEC; ++k) {
-                a[k] = acc[v * VEC + k];
-                acc[v * VEC + k] = 0.0f;
+                if (CUT == PG_CUTOFF_SPHERE) {
+                    acc0[k] = (fmaf(dz[k], dz[k], dxya) <= r2) ? fmaf(ea, ez[k], acc0[k]) : acc0[k];
+                    acc1[k] = (fmaf(dz[k], dz[k], dxyb) <= r2) ? fmaf(eb, ez[k], acc1[k]) : acc1[k];
+                } else {
+                    acc0[k] = fmaf(ea, ez[k], acc0[k]);
+                    acc1[k] = fmaf(eb, ez[k], acc1[k]);
+                }
             }
         }
-        store_lane<T, VEC, HINT>(out, v, a);
+        if (lane < act) {
+            if (ya < ny) store_lane<T, VEC, HINT>(out, (ya * nz + z0) / VEC, acc0);
+            if (yb < ny) store_lane<T, VEC, HINT>(out, (yb * nz + z0) / VEC, acc1);
+        }
     }
-    __syncwarp();
+    __syncwarp();  // the next plane rebuilds the table
 }
 
 // WGT: per-atom weights (weighted grids).  Unweighted batches run the instantiation without
@@ -491,20 +492,20 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
     const int warp = threadIdx.x >> 5;
     const int warps_per_block = blockDim.x >> 5;
     // Per warp (layout in direct_warp_floats): the plane's staged candidates, the chunk's
-    // channel atoms, then in dense-plane mode the plane accumulator and the row table.
-    float4 *stage = smem_all + (size_t)warp * (direct_warp_floats(A.plane_stride, A.erf_tab) / 4);
+    // channel atoms, then in z-table mode the plane's z-factor table.
+    float4 *stage = smem_all + (size_t)warp * (direct_warp_floats(A.ztab, A.erf_tab) / 4);
     float4 *chan = stage + kStageCap;
-    float *acc = reinterpret_cast<float *>(chan + kChanCap);
-    float4 *rowtab = reinterpret_cast<float4 *>(acc + A.plane_stride);
-    // Voxel-integrated form with a separable cutoff: per-chunk factor tables (table_plane),
-    // held in the staging area, which molecules of at most 32 atoms do not use.
+    float *ztab = reinterpret_cast<float *>(chan + kChanCap);
+    // Voxel-integrated form with a separable cutoff: per-chunk factor tables (table_plane).
+    // Molecules of at most 32 atoms keep theirs in the staging area, which they do not use;
+    // larger molecules keep theirs after their staged candidates and channel atoms, with each
+    // staged candidate's x factor in sfx.
     constexpr bool TAB = FORM == 1 && CUT != PG_CUTOFF_SPHERE;
+    constexpr int kStaging = 4 * (kStageCap + kChanCap);
     float *tab = reinterpret_cast<float *>(stage);
+    float *stab = reinterpret_cast<float *>(stage) + kStaging;
+    float *sfx = reinterpret_cast<float *>(stage) + max(kStaging, A.erf_tab);
     long long tab_bc = -1;  // (molecule, channel) whose factors the table holds
-    if (SCAT) {  // the plane accumulator starts zeroed and each plane leaves it so
-        for (int i = lane; i < A.plane_stride; i += 32) acc[i] = 0.0f;
-        __syncwarp();
-    }
     const unsigned lt_mask = (1u << lane) - 1u;
 
     // Work is handed out dynamically in chunks of up to chunk_planes consecutive x-planes of
@@ -616,34 +617,14 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                 if (use_tab) {
                     my_ti = (my_e == c) ? __popc(chm & lt_mask) : -1;
                     if (tab_bc != (long long)bc) {
-                        const float kf = G.kerf[c], r2 = G.r2[c], q = G.q[c];
-                        const int tyw = (G.ny + 3) & ~3;
-                        const int total = nch * tw;
                         __syncwarp();
-                        for (int base = 0; base < total; base += 32) {
-                            const int idx = base + lane;
-                            const int row = idx / tw;
-                            const int j = idx - row * tw;
-                            const int src = __fns(chm, 0, min(row, nch - 1) + 1);
-                            const float sy = __shfl_sync(0xffffffffu, my_y, src);
-                            const float sz = __shfl_sync(0xffffffffu, my_z, src);
-                            if (idx < total) {
-                                float v = 0.0f;
-                                if (j < tyw) {
-                                    if (j < G.ny) {
-                                        float dy = fmaf((float)j + 0.5f, hy, oy) - sy;
-                                        if (PER) dy = wrap(dy, Ly, iLy);
-                                        v = erf_axis(dy, hy, kf);
-                                        if (CUT == PG_CUTOFF_BOX && dy * dy > r2) v = 0.0f;
-                                    }
-                                } else if (j - tyw < G.nz) {
-                                    float dz = fmaf((float)(j - tyw) + 0.5f, hz, oz) - sz;
-                                    if (PER) dz = wrap(dz, Lz, iLz);
-                                    v = z_factor<CUT, 1>(dz, q, r2, kf, hz);
-                                }
-                                tab[idx] = v;
-                            }
-                        }
+                        build_erf_table<CUT, PER>(
+                            tab, nch, G.ny, G.nz, lane, G.q[c], G.r2[c], G.kerf[c], oy, oz, hy, hz,
+                            Ly, iLy, Lz, iLz, [&](int i) {
+                                const int src = __fns(chm, 0, i + 1);
+                                return make_float2(__shfl_sync(0xffffffffu, my_y, src),
+                                                   __shfl_sync(0xffffffffu, my_z, src));
+                            });
                         __syncwarp();
                         tab_bc = (long long)bc;
                     }
@@ -700,6 +681,22 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
             __syncwarp();
             n_chan = cnt <= kChanCap ? cnt : -1;
         }
+        // Larger molecule, voxel-integrated form, separable cutoff: the factor table of the
+        // chunk's channel atoms, when it fits after the staging area.
+        bool use_stab = false;
+        if constexpr (TAB) {
+            if (!small && blocked && n_chan > 0 &&
+                n_chan * erf_table_stride(G.ny, G.nz) <= A.erf_tab - kStaging) {
+                use_stab = true;
+                build_erf_table<CUT, PER>(stab, n_chan, G.ny, G.nz, lane, G.q[c], G.r2[c],
+                                          G.kerf[c], oy, oz, hy, hz, Ly, iLy, Lz, iLz,
+                                          [&](int i) {
+                                              const float4 a = chan[i];
+                                              return make_float2(a.y, a.z);
+                                          });
+                __syncwarp();
+            }
+        }
         for (int x = x_begin; x < x_end; ++x) {
             const long long item = (long long)bc * G.nx + x;
             T *out = reinterpret_cast<T *>(A.out) + item * (long long)plane;
@@ -720,9 +717,21 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                     zero_plane<T, VEC, HINT>(out, nvec, lane);
                 } else if (TAB && use_tab) {
                     const float fx = cand ? erf_axis(dx, hx, kf) : 0.0f;
-                    table_plane<T, VEC, CUT, PER, HINT, WGT>(
-                        out, tab, G.ny, G.nz, rpg, act, my_row, my_z0, lane, r2, rc, cand, dx, fx,
-                        my_ti, my_y, my_z, my_w, oy, oz, hy, hz, Ly, iLy, Lz, iLz);
+                    table_plane<T, VEC, CUT, PER, HINT>(
+                        out, tab, G.ny, G.nz, rpg, act, my_row, my_z0, lane, r2, oy, oz, hy, hz,
+                        [&](float cy, float wy, float cz, float wz, auto &&f) {
+                            const bool hit = cand && reaches<CUT, PER>(dx, my_y, my_z, cy, wy, cz,
+                                                                       wz, rc, Ly, iLy, Lz, iLz);
+                            unsigned m = __ballot_sync(0xffffffffu, hit);
+                            while (m) {
+                                const int src = __ffs(m) - 1;
+                                m &= m - 1;
+                                f(__shfl_sync(0xffffffffu, dx, src),
+                                  __shfl_sync(0xffffffffu, fx, src),
+                                  WGT ? __shfl_sync(0xffffffffu, my_w, src) : 1.0f,
+                                  __shfl_sync(0xffffffffu, my_ti, src));
+                            }
+                        });
                 } else if (blocked) {
                     blocked_plane<T, VEC, CUT, PER, HINT, FORM>(
                         out, G.ny, G.nz, rpg, act, my_row, my_z0, lane, q, r2, kf, hx, oy, oz, hy,
@@ -803,7 +812,17 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                         ok = (CUT == PG_CUTOFF_NONE) || (fabsf(dx) <= rc);
                     }
                     const unsigned m = __ballot_sync(0xffffffffu, ok);
-                    if (ok) stage[count + __popc(m & lt_mask)] = make_float4(dx, ay, az, aw);
+                    if (ok) {
+                        const int pos = count + __popc(m & lt_mask);
+                        if (TAB && use_stab) {
+                            // With a factor table: the atom's table row instead of its weight,
+                            // and its x factor beside.
+                            stage[pos] = make_float4(dx, ay, az, __int_as_float(j));
+                            sfx[pos] = erf_axis(dx, hx, kf);
+                        } else {
+                            stage[pos] = make_float4(dx, ay, az, aw);
+                        }
+                    }
                     count += __popc(m);
                 }
                 for (int base = n_chan >= 0 ? a1 : a0; base < a1; base += 32) {
@@ -835,10 +854,32 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                 __syncwarp();
                 if (count == 0) {
                     zero_plane<T, VEC, HINT>(out, nvec, lane);
-                } else if (SCAT && count >= kDiscMin && count <= kStageCap) {
-                    disc_plane<T, VEC, CUT, PER, HINT, WGT>(out, acc, rowtab, stage, count, G.ny,
-                                                           G.nz, lane, q, r2, rc, oy, oz, hy, hz,
-                                                           Ly, iLy, Lz, iLz);
+                } else if (TAB && use_stab) {
+                    table_plane<T, VEC, CUT, PER, HINT>(
+                        out, stab, G.ny, G.nz, rpg, act, my_row, my_z0, lane, r2, oy, oz, hy, hz,
+                        [&](float cy, float wy, float cz, float wz, auto &&f) {
+                            for (int cb = 0; cb < count; cb += 32) {
+                                const int j = cb + lane;
+                                bool ok = false;
+                                if (j < count) {
+                                    const float4 st = stage[j];
+                                    ok = reaches<CUT, PER>(st.x, st.y, st.z, cy, wy, cz, wz, rc, Ly,
+                                                           iLy, Lz, iLz);
+                                }
+                                unsigned m = __ballot_sync(0xffffffffu, ok);
+                                while (m) {
+                                    const int src = __ffs(m) - 1;
+                                    m &= m - 1;
+                                    const float4 st = stage[cb + src];
+                                    const int ti = __float_as_int(st.w);
+                                    f(st.x, sfx[cb + src], WGT ? chan[ti].w : 1.0f, ti);
+                                }
+                            }
+                        });
+                } else if (SCAT && blocked && count >= kZtabMin && count <= kZtabCands) {
+                    ztab_plane<T, VEC, CUT, PER, HINT, WGT>(out, ztab, stage, count, G.ny, G.nz,
+                                                           rpg, act, my_row, my_z0, lane, q, r2,
+                                                           rc, oy, oz, hy, hz, Ly, iLy, Lz, iLz);
                 } else if (blocked && count <= kStageCap) {
                     blocked_plane<T, VEC, CUT, PER, HINT, FORM>(
                         out, G.ny, G.nz, rpg, act, my_row, my_z0, lane, q, r2, kf, hx, oy, oz, hy,
@@ -959,8 +1000,8 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
     }
 }
 
-// Dense-plane instantiations (SCAT) exist only for the point form and where a cutoff
-// bounds each atom's disc; the gather-only ones carry no dense-plane code and so keep their
+// Z-table instantiations (SCAT) exist only for the point form and where a cutoff
+// bounds each atom's disc; the gather-only ones carry no z-table code and so keep their
 // register allocation.
 template <typename T, int VEC, int CUT, bool PER, int HINT, int FORM>
 const void *pick_scat(bool scat)
@@ -1024,7 +1065,7 @@ const void *pick_weighted(int dtype, bool vec_ok, int cut, int per)
 }
 
 // The instantiation for one launch: dtype, vector stores, cutoff, boundary, store hint,
-// dense-plane mode and voxel form.
+// z-table mode and voxel form.
 template <int FORM>
 const void *pick_direct(int dtype, bool vec_ok, int cut, int per, int hint, bool scat)
 {

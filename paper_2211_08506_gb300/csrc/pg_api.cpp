@@ -16,7 +16,10 @@
 #include <mutex>
 #include <sstream>
 #include <string>
+#include <tuple>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>  // header-only NVTX v3: inert unless a profiler injects itself
 
 #include "pg.h"
 #include "pg_internal.h"
@@ -26,6 +29,15 @@ using namespace pgi;
 namespace {
 
 thread_local std::string t_last_error;
+
+// An NVTX range over one API call, so that profiler timelines show where each call's host
+// work (and, for plan runs, the graph replay it waits for) begins and ends.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 pg_status fail(pg_status s, const char *fmt, ...)
 {
@@ -221,32 +233,25 @@ pg_tuning default_tuning(int path)
     return t;
 }
 
-// Floats of per-warp shared memory for the direct kernel's dense-plane mode, or 0
-// where it does not apply: no cutoff, planes above 16 KB of FP32 accumulators, or an axis
-// above 256 voxels (the per-atom tables hold one entry per row and per column).
-int direct_plane_stride(const pg_grid *g)
-{
-    const long long plane = (long long)g->ny * g->nz;
-    if (g->cutoff == PG_CUTOFF_NONE || plane * 4 > 16384 || g->ny > 256 || g->nz > 256) return 0;
-    return (int)((plane + 3) / 4 * 4);
-}
-
-// Whether the direct kernel runs with dense-plane mode (its dense-plane instantiation).
-// Molecules of at most 32 atoms never reach it (they take the register path), so a batch
-// whose mean is that small keeps the gather-only instantiation and its higher occupancy.
+// Whether the direct kernel runs with z-table mode (its z-table instantiation): the point form
+// with a cutoff, axes of at most 256 voxels, unweighted axis-aligned boxes.  Molecules of at
+// most 32 atoms never reach it (they take the register path), so a batch whose mean is that
+// small keeps the gather-only instantiation and its higher occupancy.
 bool direct_scatter_on(const pg_batch *b, const pg_grid *g, const pg_tuning &t)
 {
-    // Weighted grids keep the gather-only instantiations.
     return !t.gather_only && g->voxel_form == PG_FORM_POINT && !b->weight && !b->cell &&
-           direct_plane_stride(g) > 0 && b->n_atoms > 32LL * b->n_mol;
+           g->cutoff != PG_CUTOFF_NONE && g->ny <= 256 && g->nz <= 256 &&
+           b->n_atoms > 32LL * b->n_mol;
 }
 
 // Floats of per-warp factor table for the direct kernel's voxel-integrated form with a
-// separable cutoff: room for 32 atoms' per-axis factors, at most kErfTabCap; 0 elsewhere.
-int direct_erf_tab(const pg_batch *b, const pg_grid *g)
+// separable cutoff: room for 64 atoms' per-axis factors, at most kErfTabCap; 0 elsewhere.
+int direct_erf_tab(const pg_batch *b, const pg_grid *g, const pg_tuning &t)
 {
-    if (g->voxel_form != PG_FORM_INTEGRAL || g->cutoff == PG_CUTOFF_SPHERE || b->cell) return 0;
-    const long long need = 32LL * erf_table_stride(g->ny, g->nz);
+    if (t.gather_only || g->voxel_form != PG_FORM_INTEGRAL || g->cutoff == PG_CUTOFF_SPHERE ||
+        b->cell)
+        return 0;
+    const long long need = 64LL * erf_table_stride(g->ny, g->nz);
     return (int)std::min<long long>(need, kErfTabCap);
 }
 
@@ -295,14 +300,14 @@ pg_status plan_forward(const pg_batch *b, const pg_grid *g, int dtype, void *out
     a.out = out;
     a.err = err;
     a.sched = sched;
-    a.plane_stride = direct_scatter_on(b, g, t) ? direct_plane_stride(g) : 0;
+    a.ztab = direct_scatter_on(b, g, t) ? direct_ztab_floats(g->nz) : 0;
     a.chunk_planes = (t.chunk_planes >= 1 && t.chunk_planes <= 64) ? t.chunk_planes : 8;
     a.chunk_order = t.chunk_order == 1 ? 1 : 0;
-    a.erf_tab = direct_erf_tab(b, g);
+    a.erf_tab = direct_erf_tab(b, g, t);
     a.geo = G;
     const int vec = vec_stores_ok(out, g, dtype) ? 1 : 0;
     if (b->cell) {
-        a.plane_stride = 0;
+        a.ztab = 0;
         a.erf_tab = 0;
         cudaError_t e = cell_plan(a, dtype, vec, t, d.sms, kl);
         if (e != cudaSuccess) return cuda_fail(e, "cell_plan");
@@ -351,8 +356,31 @@ std::string bucket_key(const pg_batch *b, const pg_grid *g, int dtype, int path,
     return buf;
 }
 
+// PG_TUNING_CACHE names a tuning-cache file: it is merged into the in-memory cache on first
+// use, and every pg_autotune rewrites it with the whole cache.
+const char *tuning_cache_path()
+{
+    const char *p = std::getenv("PG_TUNING_CACHE");
+    return (p && *p) ? p : nullptr;
+}
+
+void tuning_cache_init()
+{
+    static std::once_flag once;
+    std::call_once(once, [] {
+        const char *p = tuning_cache_path();
+        if (!p) return;
+        std::ifstream probe(p);
+        if (!probe) return;  // not written yet
+        const std::string saved = t_last_error;
+        pg_tuning_load(p);
+        t_last_error = saved;
+    });
+}
+
 pg_tuning resolve(const pg_batch *b, const pg_grid *g, int dtype, int path, const Device &d)
 {
+    tuning_cache_init();
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(bucket_key(b, g, dtype, path, d));
     if (it != g_tune.end()) return it->second;
@@ -405,6 +433,7 @@ struct pg_plan {
     size_t cur_cnt[kPlanCopies] = {};
     KernelLaunch cur_kl;
     bool cur_valid = false;
+    bool in_flight = false;  // launched, not yet waited for
 };
 
 namespace {
@@ -556,6 +585,33 @@ void debug_launch(const KernelLaunch &kl)
                      kl.grid.x, kl.block.x, kl.smem);
 }
 
+cudaError_t occupancy(const void *func, int threads, size_t smem, int *per_sm)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const auto key = std::make_tuple(dev, func, threads, smem);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            *per_sm = it->second;
+            return cudaSuccess;
+        }
+    }
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, func, threads, smem);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    cache[key] = n;
+    *per_sm = n;
+    return cudaSuccess;
+}
+
 pg_status set_last_error(pg_status status, const char *fmt, ...)
 {
     char buf[768];
@@ -586,9 +642,9 @@ pg_status direct_launch_with_scratch(const pg_batch *b, const pg_grid *g, int dt
     a.err = err;
     a.sched = sched;
     const pg_tuning t = default_tuning(PG_PATH_DIRECT);
-    a.plane_stride = direct_scatter_on(b, g, t) ? direct_plane_stride(g) : 0;
+    a.ztab = direct_scatter_on(b, g, t) ? direct_ztab_floats(g->nz) : 0;
     a.chunk_planes = 8;
-    a.erf_tab = b->cell ? 0 : direct_erf_tab(b, g);
+    a.erf_tab = b->cell ? 0 : direct_erf_tab(b, g, t);
     make_geometry(b, g, &a.geo);
     const int vec = vec_stores_ok(out, g, dtype) ? 1 : 0;
     cudaError_t e = b->cell ? cell_plan(a, dtype, vec, t, sm_count, kl)
@@ -629,6 +685,7 @@ pg_status pg_voxelize_tuned(const pg_batch *batch, const pg_grid *grid, int32_t 
 pg_status pg_voxelize(const pg_batch *batch, const pg_grid *grid, int32_t out_dtype, void *out,
                       int32_t path, void *stream)
 {
+    NvtxRange range("pg_voxelize");
     t_last_error.clear();
     if (path != PG_PATH_AUTO && path != PG_PATH_DIRECT && path != PG_PATH_SEPARABLE)
         return fail(PG_ERR_INVALID_ARG, "unknown path %d", path);
@@ -657,6 +714,7 @@ pg_status pg_voxelize_backward_ex(const pg_batch *batch, const pg_grid *grid,
                                   int32_t grad_dtype, const void *grad_out, float *grad_coords,
                                   float *grad_weight, void *stream)
 {
+    NvtxRange range("pg_voxelize_backward");
     t_last_error.clear();
     pg_status st = validate(batch, grid);
     if (st) return st;
@@ -702,6 +760,7 @@ pg_status pg_refine(const pg_batch *batch, const pg_grid *grid, const float *tar
                     float *coords, float *work, float *loss, int32_t *steps, int32_t iters,
                     float lr, float eps, void *stream)
 {
+    NvtxRange range("pg_refine");
     t_last_error.clear();
     if (!batch) return fail(PG_ERR_INVALID_ARG, "batch must not be NULL");
     if (iters < 0) return fail(PG_ERR_INVALID_ARG, "iters must be >= 0");
@@ -771,6 +830,8 @@ pg_status pg_get_tuning(const pg_batch *batch, const pg_grid *grid, int32_t out_
 pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dtype, void *out,
                       int32_t path, void *stream, pg_tuning *chosen)
 {
+    NvtxRange range("pg_autotune");
+    tuning_cache_init();
     t_last_error.clear();
     pg_status st = validate(batch, grid);
     if (st) return st;
@@ -793,7 +854,9 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
         // Full product of the direct kernel's launch knobs; the default comes first and is
         // the reference every other candidate must match bit for bit.
         cands.push_back(default_tuning(PG_PATH_DIRECT));
-        const int go_max = direct_scatter_on(batch, grid, default_tuning(PG_PATH_DIRECT)) ? 1 : 0;
+        const pg_tuning def = default_tuning(PG_PATH_DIRECT);
+        const int go_max =
+            (direct_scatter_on(batch, grid, def) || direct_erf_tab(batch, grid, def) > 0) ? 1 : 0;
         // The general-cell kernel has a fixed block and no store hint or scatter mode: only
         // the residency and the chunk size vary.
         if (batch->cell)
@@ -810,7 +873,7 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
             for (int threads : {128, 256, 512})
                 for (int bps : {0, 1, 2})
                     for (int hint : {0, 1})
-                        for (int cp : {1, 2, 4, 8})
+                        for (int cp : {1, 2, 4, 8, 16, 32})
                             for (int go = 0; go <= go_max && !batch->cell; ++go) {
                                 pg_tuning t = default_tuning(PG_PATH_DIRECT);
                                 t.block_threads = threads;
@@ -972,6 +1035,11 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
             g_tune[bucket_key(batch, grid, out_dtype, PG_PATH_SEPARABLE, *d)] = cands[best_sep];
     }
     if (chosen) *chosen = cands[best];
+    if (const char *path_file = tuning_cache_path()) {
+        if (pg_tuning_save(path_file) != PG_OK)
+            return fail(PG_ERR_INVALID_ARG, "tuned, but the tuning cache %s could not be "
+                                            "written", path_file);
+    }
     return PG_OK;
 }
 
@@ -1089,8 +1157,35 @@ pg_status pg_plan_create(pg_plan **plan, const pg_grid *grid, int32_t out_dtype,
 
 pg_status pg_plan_run(pg_plan *p, const pg_batch *hb, void *out, void *stream)
 {
+    NvtxRange range("pg_plan_run (copies + kernel graph replay)");
+    pg_status st = pg_plan_launch(p, hb, out, stream);
+    if (st) return st;
+    return pg_plan_wait(p, stream);
+}
+
+pg_status pg_plan_wait(pg_plan *p, void *stream)
+{
     t_last_error.clear();
     if (!p) return fail(PG_ERR_INVALID_ARG, "plan must not be NULL");
+    if (!p->in_flight) return PG_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const cudaError_t e = cudaStreamSynchronize(s);
+    p->in_flight = false;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (*p->h_err & PG_DEVERR_TMEM_HELD) {
+        Device *d = nullptr;
+        if (get_device(&d) == PG_OK) d->tmem_held->store(true);
+    }
+    return report_bits(*p->h_err);
+}
+
+pg_status pg_plan_launch(pg_plan *p, const pg_batch *hb, void *out, void *stream)
+{
+    t_last_error.clear();
+    if (!p) return fail(PG_ERR_INVALID_ARG, "plan must not be NULL");
+    if (p->in_flight)
+        return fail(PG_ERR_INVALID_ARG, "the plan's previous launch has not been waited for "
+                                        "(pg_plan_wait)");
     pg_status st = validate(hb, &p->grid);
     if (st) return st;
     if (hb->n_mol > p->max_mol || hb->n_atoms > p->max_atoms)
@@ -1155,9 +1250,8 @@ pg_status pg_plan_run(pg_plan *p, const pg_batch *hb, void *out, void *stream)
     if ((st = plan_update_graph(p, src, cnt, dst, kl))) return st;
     cudaStream_t s = (cudaStream_t)stream;
     PG_CUDA(cudaGraphLaunch(p->exec, s), "cudaGraphLaunch");
-    PG_CUDA(cudaStreamSynchronize(s), "cudaStreamSynchronize");
-    if (*p->h_err & PG_DEVERR_TMEM_HELD) d->tmem_held->store(true);
-    return report_bits(*p->h_err);
+    p->in_flight = true;
+    return PG_OK;
 }
 
 pg_status pg_plan_destroy(pg_plan *p)

@@ -323,7 +323,7 @@ cudaError_t backward_plan(const BackwardArgs &a, int grad_dtype, int sm_count, K
                                            : pick<__nv_bfloat16>(cut, per, form);
     const int threads = 256;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, 0);
+    cudaError_t e = occupancy(f, threads, 0, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     // Persistent grid: atoms come from the work counter; never more warps than atoms.

@@ -559,10 +559,8 @@ cudaError_t cell_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tunin
                    : pick_cell_shape<__nv_bfloat16, 1>(cut, per);
     const int threads = kCellThreads;
     const size_t smem = (size_t)(threads / 32) * kCellWarpBytes;
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem);
+    cudaError_t e = occupancy(f, threads, smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (t.blocks_per_sm > 0 && t.blocks_per_sm < per_sm) per_sm = t.blocks_per_sm;
@@ -589,7 +587,7 @@ cudaError_t cell_backward_plan(const BackwardArgs &a, int grad_dtype, int sm_cou
                                            : pick_cell_backward<__nv_bfloat16>(cut, per);
     const int threads = 256;
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, 0);
+    cudaError_t e = occupancy(f, threads, 0, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) per_sm = 1;
     long long blocks = (long long)sm_count * per_sm;

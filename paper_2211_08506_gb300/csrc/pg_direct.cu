@@ -9,7 +9,7 @@ cudaError_t direct_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tun
                         int sm_count, KernelLaunch *kl)
 {
     const int hint = t.store_hint == 1 ? 1 : 0;
-    const bool scat = a.plane_stride > 0 && a.geo.cutoff != PG_CUTOFF_NONE;
+    const bool scat = a.ztab > 0 && a.geo.cutoff != PG_CUTOFF_NONE;
     const int cut = a.geo.cutoff, per = a.geo.periodic;
     const void *f = a.in.weight ? pick_direct_weighted(dtype, vec_ok != 0, cut, per, a.geo.form)
                     : a.geo.form == PG_FORM_INTEGRAL
@@ -18,13 +18,11 @@ cudaError_t direct_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tun
 
     int threads = t.block_threads;
     if (threads != 128 && threads != 256 && threads != 512) threads = 256;
-    const size_t per_warp = (size_t)direct_warp_floats(a.plane_stride, a.erf_tab) * sizeof(float);
+    const size_t per_warp = (size_t)direct_warp_floats(a.ztab, a.erf_tab) * sizeof(float);
     while (threads > 128 && (size_t)(threads / 32) * per_warp > 200 * 1024) threads /= 2;
     const size_t smem = (size_t)(threads / 32) * per_warp;
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem);
+    cudaError_t e = occupancy(f, threads, smem, &per_sm);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     if (t.blocks_per_sm > 0 && t.blocks_per_sm < per_sm) per_sm = t.blocks_per_sm;

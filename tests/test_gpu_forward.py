@@ -240,8 +240,8 @@ def test_register_and_staged_paths_agree_bitwise(pg):
         G1 = run(pg, wl, dtype=dtype)
         G2 = run(pg, wl, dtype=dtype, batch=padded, tuning={"path": 1, "gather_only": 1})
         assert np.array_equal(G1, G2)
-        # With dense-plane mode allowed, dense planes of the padded batch walk each candidate's
-        # disc in shared memory: the same terms in the same order, identical bits.
+        # With z-table mode allowed, planes of the padded batch with several candidates read
+        # their z factors from a table: the same terms in the same order, identical bits.
         G3 = run(pg, wl, dtype=dtype, batch=padded, tuning={"path": 1})
         assert np.array_equal(G3, G1)
 
@@ -249,8 +249,8 @@ def test_register_and_staged_paths_agree_bitwise(pg):
 @pytest.mark.parametrize("cutoff,periodic,shape", [
     ("sphere", False, (48, 48, 48)), ("box", False, (48, 48, 48)), ("box", True, (48, 48, 48)),
     ("sphere", True, (40, 44, 45)), ("box", False, (37, 52, 30))])
-def test_dense_plane_mode_every_cutoff_boundary_and_ragged_plane(pg, cutoff, periodic, shape):
-    # Dense-plane mode against the gather mode on dense cells, for both cutoffs, open and
+def test_ztab_mode_every_cutoff_boundary_and_ragged_plane(pg, cutoff, periodic, shape):
+    # Z-table mode against the gather mode on dense cells, for both cutoffs, open and
     # periodic boundaries, and ragged planes that take the scalar store path.  The two modes
     # add the same terms in the same order: identical bits, and both match the oracle.
     wl = synth.crystal_shaped(n_cells=10)
@@ -266,8 +266,8 @@ def test_dense_plane_mode_every_cutoff_boundary_and_ragged_plane(pg, cutoff, per
             grid_check(G[:4], prob, TOL[dtype], abs_tol=ABS_TOL[dtype])
 
 
-def test_dense_plane_and_gather_modes_on_dense_cells(pg):
-    # Dense periodic cells: planes with two or more candidates take dense-plane mode unless
+def test_ztab_and_gather_modes_on_dense_cells(pg):
+    # Dense periodic cells: planes with two or more candidates take z-table mode unless
     # gather_only is set.  Both modes are bitwise equal to each other across launch shapes
     # and match the oracle.
     wl = synth.crystal_shaped(n_cells=24)
@@ -305,11 +305,11 @@ def test_chunk_orders_give_identical_bits(pg, kind):
 
 
 @pytest.mark.parametrize("periodic", [False, True])
-def test_dense_plane_mode_wide_discs(pg, periodic):
-    # Discs wider and taller than a warp (r_c = 1.5 A on a 0.05 A grid: about 60 voxels
-    # across), so that the dense-plane walk takes its columns 32 at a time and its row table
-    # in several parts; atoms near the faces so that periodic discs wrap.  Bitwise equal to
-    # the gather, and equal to the oracle.
+def test_ztab_mode_wide_discs(pg, periodic):
+    # Wide discs on a fine grid (r_c = 1.5 A on 0.05 A voxels: about 60 voxels across; 64-voxel
+    # table rows) and dense planes of up to about 30 candidates, some above the table's limit
+    # of 32; atoms near the faces so that periodic images wrap.  Bitwise equal to the gather,
+    # and equal to the oracle.
     rng = np.random.default_rng(41)
     n = 64
     h = 0.05

@@ -143,6 +143,10 @@ def test_factor_tables_bitwise_across_launch_shapes(pg):
                 if ref is None:
                     ref = G.clone()
                 assert torch.equal(G, ref), (threads, cp, order)
+    # Without the tables (every factor computed where it is used): the same bits.
+    G = pg.voxelize_tuned(db, grid, {"path": 1, "gather_only": 1}, dtype="f32")
+    assert pg.sync_status() == 0
+    assert torch.equal(G, ref)
     pick = [0, 5, 11]
     grid_check(ref[pick].cpu().numpy(),
                oracle.Problem.from_workload(wl, batch=wl.batch.subset(pick)), TOL["f32"],
@@ -151,8 +155,8 @@ def test_factor_tables_bitwise_across_launch_shapes(pg):
 
 @pytest.mark.parametrize("cutoff,periodic", [("box", False), ("none", False), ("box", True)])
 def test_factor_tables_with_large_molecules_interleaved(pg, cutoff, periodic):
-    # Small molecules (factor tables) interleaved with 40-atom ones (staged path, which reuses
-    # the table's shared memory), one-plane chunks so that warps switch between the two often.
+    # Small molecules interleaved with 40-atom ones (staged path, which overwrites the small
+    # molecules' cached table), one-plane chunks so that warps switch between the two often.
     wl = integral(synth.plain_small(n_mol=6))
     wl.cutoff, wl.periodic = cutoff, periodic
     wl.cutoff_k = 2.5
@@ -171,9 +175,15 @@ def test_factor_tables_with_large_molecules_interleaved(pg, cutoff, periodic):
     nb = synth._pack(coords, elems, b.origin, b.spacing)
     db = pg.DeviceBatch.from_numpy(nb)
     grid = pg.Grid.from_workload(wl)
-    outs = [pg.voxelize_tuned(db, grid, {"path": 1, "chunk_planes": cp}, dtype="f32")
-            for cp in (1, 8)]
+    # Tables for the small molecules (register path) and for the 40-atom ones (staged path),
+    # against every factor computed where it is used: identical bits.
+    outs = [pg.voxelize_tuned(db, grid, {"path": 1, "chunk_planes": cp, "gather_only": go},
+                              dtype=dt)
+            for dt in ("f32", "bf16") for cp in (1, 8) for go in (0, 1)]
     assert pg.sync_status() == 0
-    assert torch.equal(outs[0], outs[1])
+    for k in (1, 2, 3):
+        assert torch.equal(outs[0], outs[k]), k
+    for k in (5, 6, 7):
+        assert torch.equal(outs[4], outs[k]), k
     grid_check(outs[0].cpu().numpy(), oracle.Problem.from_workload(wl, batch=nb), TOL["f32"],
                abs_tol=ABS_TOL["f32"])

@@ -94,3 +94,85 @@ def test_plan_reports_device_detected_errors(pg):
         assert torch.equal(out, direct(pg, wl, wl.batch, "f32"))
     finally:
         plan.close()
+
+
+
+def test_plan_launch_then_adjoint_then_wait(pg):
+    # pg_plan_launch enqueues the copies and the forward pass without synchronizing; the
+    # adjoint and the gradient's copy to the host follow on the same stream; pg_plan_wait
+    # synchronizes once and reports the error word.  Results equal the synchronous calls.
+    wl = synth.differentiation(n_mol=24)
+    grid = pg.Grid.from_workload(wl)
+    db = pg.DeviceBatch.from_numpy(wl.batch)
+    W = torch.as_tensor(synth.loss_weights(wl), device="cuda")
+    stream = torch.cuda.Stream()
+    plan = pg.Plan(grid, "f32", max_mol=24, max_atoms=int(wl.batch.n_atoms), path="direct")
+    try:
+        out = torch.empty(grid.out_shape(24), dtype=torch.float32, device="cuda")
+        grad = torch.empty((wl.batch.n_atoms, 3), dtype=torch.float32, device="cuda")
+        grad_host = torch.empty_like(grad, device="cpu").pin_memory()
+        host = host_arrays(wl.batch, True)
+        plan.wait(stream)  # nothing outstanding: a no-op
+        for _ in range(2):
+            plan.launch(*host, out=out, stream=stream)
+            with pytest.raises(Exception, match="waited"):
+                plan.launch(*host, out=out, stream=stream)
+            pg.voxelize_backward(db, grid, W, grad_coords=grad, stream=stream)
+            grad_host.copy_(grad, non_blocking=True)
+            plan.wait(stream)
+            assert torch.equal(out, direct(pg, wl, wl.batch, "f32"))
+            ref = pg.voxelize_backward(db, grid, W)
+            assert pg.sync_status() == 0
+            assert torch.equal(grad_host, ref.cpu())
+        # A device-detected error is reported by the wait.
+        bad = host_arrays(wl.batch, False)
+        bad[1] = bad[1].copy()
+        bad[1][0] = 9
+        plan.launch(*bad, out=out, stream=stream)
+        with pytest.raises(Exception):
+            plan.wait(stream)
+    finally:
+        plan.close()
+
+_CACHE_CHILD = r"""
+import json, sys
+sys.path.insert(0, sys.argv[2])
+import synth
+from paper_2211_08506_gb300 import api
+wl = synth.qm9_shaped(n_mol=64)
+db = api.DeviceBatch.from_numpy(wl.batch)
+grid = api.Grid.from_workload(wl)
+if sys.argv[1] == "tune":
+    print(json.dumps(api.autotune(db, grid, dtype="f32", path="direct")))
+else:
+    print(json.dumps(api.get_tuning(db, grid, dtype="f32", path="direct")))
+"""
+
+
+def test_tuning_cache_file_named_by_the_environment(pg, tmp_path):
+    # PG_TUNING_CACHE: a tuning run writes the cache file; a fresh process merges it on first
+    # use, so PG_PATH_DIRECT resolves to the stored launch without tuning again.
+    import json
+    import os
+    import subprocess
+    import sys
+
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    path = tmp_path / "tuning.txt"
+    env = dict(os.environ, PG_TUNING_CACHE=str(path))
+
+    def child(mode):
+        r = subprocess.run([sys.executable, "-c", _CACHE_CHILD, mode, root], env=env,
+                           capture_output=True, text=True, timeout=600)
+        assert r.returncode == 0, r.stderr[-3000:]
+        return json.loads(r.stdout.strip().splitlines()[-1])
+
+    child("tune")
+    lines = path.read_text().splitlines()
+    key = next(l.split()[0] for l in lines if "|path1" in l.split()[0] and "|dt0|" in l)
+    # A distinctive stored launch for that bucket, which the tuner itself would not pick.
+    rest = [l for l in lines if l.split()[0] != key]
+    path.write_text("\n".join(rest + [f"{key} 1 512 1 0 128 1 3 0 1"]) + "\n")
+    got = child("get")
+    assert (got["block_threads"], got["blocks_per_sm"], got["chunk_planes"],
+            got["chunk_order"]) == (512, 1, 3, 1), got

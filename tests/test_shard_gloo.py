@@ -83,3 +83,52 @@ def test_two_gloo_ranks_reproduce_single_process_grids():
         for i, s in zip(range(start, stop), sums):
             assert s == float(G[i].sum())
     assert covered == list(range(24))
+
+
+def _union_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        # As the benchmark's ranks do: every rank builds the same global batch (world times the
+        # per-rank size, one seed) and keeps its contiguous range.
+        whole = synth.qm9_shaped(n_mol=40 * world)
+        sub, (start, stop) = shard.shard(whole.batch, rank, world, whole.voxels_per_grid * 4)
+        parts = [None] * world
+        dist.all_gather_object(parts, (start, stop, sub.coords, sub.elem, sub.mol_off,
+                                       sub.origin, sub.spacing))
+        if rank == 0:
+            q.put(parts)
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_rank_shares_reassemble_the_global_batch(world):
+    import multiprocessing as mp
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_union_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    parts = q.get(timeout=240)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    whole = synth.qm9_shaped(n_mol=40 * world).batch
+    assert parts[0][0] == 0 and parts[-1][1] == whole.n_mol
+    assert all(a[1] == b[0] for a, b in zip(parts, parts[1:]))
+    # Concatenated per-molecule inputs equal the global batch's, molecule by molecule.
+    coords = np.concatenate([p[2] for p in parts])
+    elem = np.concatenate([p[3] for p in parts])
+    assert np.array_equal(coords, whole.coords) and np.array_equal(elem, whole.elem)
+    assert np.array_equal(np.concatenate([p[5] for p in parts]), whole.origin)
+    assert np.array_equal(np.concatenate([p[6] for p in parts]), whole.spacing)
+    counts = np.concatenate([np.diff(p[4]) for p in parts])
+    assert np.array_equal(counts, np.diff(whole.mol_off))
+    # Every share is within one molecule's cost of an equal split.
+    cost = shard.molecule_costs(whole.mol_off, synth.qm9_shaped(n_mol=1).voxels_per_grid * 4)
+    loads = [cost[a:b].sum() for a, b, *_ in parts]
+    assert max(loads) - min(loads) <= 2 * cost.max()
