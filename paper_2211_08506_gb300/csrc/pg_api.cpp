@@ -589,24 +589,28 @@ cudaError_t occupancy(const void *func, int threads, size_t smem, int *per_sm)
 {
     static std::mutex mu;
     static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
+    // The kernel's dynamic shared-memory limit is only ever raised: a launch planned from the
+    // cache must never find it lowered by a later, smaller plan.
+    static std::map<std::pair<int, const void *>, size_t> limit;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     const auto key = std::make_tuple(dev, func, threads, smem);
-    {
-        std::lock_guard<std::mutex> lk(mu);
-        auto it = cache.find(key);
-        if (it != cache.end()) {
-            *per_sm = it->second;
-            return cudaSuccess;
-        }
+    std::lock_guard<std::mutex> lk(mu);
+    size_t &lim = limit[std::make_pair(dev, func)];
+    if (smem > lim) {
+        e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        lim = smem;
     }
-    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+        *per_sm = it->second;
+        return cudaSuccess;
+    }
     int n = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, func, threads, smem);
     if (e != cudaSuccess) return e;
-    std::lock_guard<std::mutex> lk(mu);
     cache[key] = n;
     *per_sm = n;
     return cudaSuccess;
