@@ -669,42 +669,59 @@ def measure(ses, wl, dtype, path, tag, W=None, e2e=True):
         extra = {"weight": pin(b.weight), "cell": pin(b.cell)}
         h2d = sum(t.numel() * t.element_size() for t in host + list(extra.values())
                   if t is not None)
-        plan = api.Plan(grid, dtype, max_mol=B, max_atoms=b.n_atoms, path=path)
-        grad_host = None
+        # Two plans alternate (double buffering, as a data loader runs them): step i's batch
+        # is copied in and launched before step i - 1's results are waited for and read.
+        plans = [api.Plan(grid, dtype, max_mol=B, max_atoms=b.n_atoms, path=path)
+                 for _ in range(2)]
+        outs = [out, torch.empty_like(out)]
         d2h = 4
+        grads = grad_hosts = None
         if Wd is not None:
-            grad_host = torch.empty((b.n_atoms, 3), dtype=torch.float32).pin_memory()
-            d2h += grad_host.numel() * grad_host.element_size()
+            grads = [grad, torch.empty_like(grad)]
+            grad_hosts = [torch.empty((b.n_atoms, 3), dtype=torch.float32).pin_memory()
+                          for _ in range(2)]
+            d2h += grad_hosts[0].numel() * grad_hosts[0].element_size()
+        done = [torch.cuda.Event(), torch.cuda.Event()]
 
-        def e2e_step():
-            if Wd is None:
-                plan.run(*host, out=out, stream=stream, **extra)
-                return
-            # Forward from the host batch, the adjoint and the gradient's copy to the host,
-            # with one synchronization (pg_plan_wait) at the end of the step.
-            plan.launch(*host, out=out, stream=stream, **extra)
-            api.voxelize_backward(db, grid, Wd, grad_coords=grad, stream=stream)
-            grad_host.copy_(grad, non_blocking=True)
-            plan.wait(stream)
+        def launch(i):
+            k = i % 2
+            plans[k].launch(*host, out=outs[k], stream=stream, **extra)
+            if Wd is not None:
+                # The adjoint of the step's forward pass and its gradient back to the host.
+                api.voxelize_backward(db, grid, Wd, grad_coords=grads[k], stream=stream)
+                grad_hosts[k].copy_(grads[k], non_blocking=True)
+            done[k].record(stream)
+
+        def finish(i):
+            k = i % 2
+            plans[k].wait(stream)   # the error word of step i's forward pass
+            done[k].synchronize()   # and, with the adjoint, its gradient on the host
+
+        def run(n):
+            launch(0)
+            for i in range(1, n):
+                launch(i)
+                finish(i - 1)
+            finish(n - 1)
 
         with torch.cuda.stream(stream):
-            for _ in range(max(3, args.warmup)):
-                e2e_step()
+            run(max(3, args.warmup))
         e2e_steps = max(3, min(args.steps, 200))
         ses.barrier()
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
-            for _ in range(e2e_steps):
-                e2e_step()
+            run(e2e_steps)
         e2e_s = ses.max_over_ranks((time.perf_counter() - t0) / e2e_steps)
-        plan.close()
+        for pl in plans:
+            pl.close()
+        del outs
         e2e_res = {"value": units / e2e_s, "unit": "grids/s", "h2d_bytes_per_step": h2d,
                    "d2h_bytes_per_step": d2h,
-                   "api": ("pg_plan_run (pinned host CSR batch -> graph: H2D + kernel -> "
-                           "error word D2H)" if Wd is None else
-                           "pg_plan_launch (pinned host CSR batch -> graph: H2D + kernel -> "
-                           "error word D2H) + pg_voxelize_backward + gradient D2H + "
-                           "pg_plan_wait")}
+                   "api": "two pg_plan_* plans alternating: pg_plan_launch (pinned host CSR "
+                          "batch -> graph: H2D + kernel -> error word D2H)"
+                          + (" + pg_voxelize_backward + gradient D2H" if Wd is not None
+                             else "")
+                          + ", then pg_plan_wait for the previous step"}
 
     kernel = ("separable" if tuning.get("path") == 2
               else "cell" if wl.batch.cell is not None else "direct")

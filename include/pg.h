@@ -312,8 +312,9 @@ pg_status pg_tuning_load(const char *file);
  *                   pageable memory is first packed into the plan's pinned staging),
  *                   weight and cell included when given;
  *                   replays the graph on `stream`, writes `out` (DEVICE), then copies the
- *                   4-byte device error word back and synchronizes the stream.  Returns
- *                   PG_ERR_DEVICE_VALIDATION if it was set.  Not thread-safe per plan.
+ *                   4-byte device error word back and waits for the graph to finish.
+ *                   Returns PG_ERR_DEVICE_VALIDATION if it was set.  Not thread-safe per
+ *                   plan.
  *   pg_plan_destroy frees the plan (synchronize users of it first).
  */
 typedef struct pg_plan pg_plan;
@@ -331,8 +332,13 @@ pg_status pg_plan_destroy(pg_plan *plan);
  *                   until the wait (pinned ones are copied by the graph).  One launch per
  *                   plan may be outstanding: a second launch before the wait returns
  *                   PG_ERR_INVALID_ARG.
- *   pg_plan_wait    synchronizes `stream` and reports the device error word of the plan's
- *                   outstanding launch as pg_plan_run would (PG_OK if none is outstanding).
+ *   pg_plan_wait    waits for the plan's outstanding launch (its copies, kernel and error
+ *                   word; not for later work on the stream) and reports the device error
+ *                   word as pg_plan_run would (PG_OK if none is outstanding).  `stream` is
+ *                   the launch's stream (kept for symmetry; the wait uses an event recorded
+ *                   after the launch).
+ * Two plans of the same shape can alternate (double buffering): launch one batch, then wait
+ * for the previous batch's plan while the new one runs.
  */
 pg_status pg_plan_launch(pg_plan *plan, const pg_batch *host_batch, void *out, void *stream);
 pg_status pg_plan_wait(pg_plan *plan, void *stream);

@@ -434,6 +434,7 @@ struct pg_plan {
     KernelLaunch cur_kl;
     bool cur_valid = false;
     bool in_flight = false;  // launched, not yet waited for
+    cudaEvent_t done = nullptr;  // recorded after each launch's graph
 };
 
 namespace {
@@ -453,6 +454,7 @@ void plan_free(pg_plan *p)
     cudaFree(p->d_sched);
     if (p->h_stage) cudaFreeHost(p->h_stage);
     if (p->h_err) cudaFreeHost(p->h_err);
+    if (p->done) cudaEventDestroy(p->done);
     delete p;
 }
 
@@ -1153,6 +1155,8 @@ pg_status pg_plan_create(pg_plan **plan, const pg_grid *grid, int32_t out_dtype,
     if ((e = cudaHostAlloc((void **)&p->h_err, sizeof(unsigned), cudaHostAllocDefault)) !=
         cudaSuccess)
         return bad(e, "cudaHostAlloc");
+    if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess)
+        return bad(e, "cudaEventCreateWithFlags");
     std::memset(p->h_stage, 0, total);
     *p->h_err = 0;
     *plan = p;
@@ -1171,11 +1175,11 @@ pg_status pg_plan_wait(pg_plan *p, void *stream)
 {
     t_last_error.clear();
     if (!p) return fail(PG_ERR_INVALID_ARG, "plan must not be NULL");
+    (void)stream;
     if (!p->in_flight) return PG_OK;
-    cudaStream_t s = (cudaStream_t)stream;
-    const cudaError_t e = cudaStreamSynchronize(s);
+    const cudaError_t e = cudaEventSynchronize(p->done);
     p->in_flight = false;
-    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
     if (*p->h_err & PG_DEVERR_TMEM_HELD) {
         Device *d = nullptr;
         if (get_device(&d) == PG_OK) d->tmem_held->store(true);
@@ -1254,6 +1258,7 @@ pg_status pg_plan_launch(pg_plan *p, const pg_batch *hb, void *out, void *stream
     if ((st = plan_update_graph(p, src, cnt, dst, kl))) return st;
     cudaStream_t s = (cudaStream_t)stream;
     PG_CUDA(cudaGraphLaunch(p->exec, s), "cudaGraphLaunch");
+    PG_CUDA(cudaEventRecord(p->done, s), "cudaEventRecord");
     p->in_flight = true;
     return PG_OK;
 }

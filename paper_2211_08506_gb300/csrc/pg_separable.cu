@@ -638,12 +638,12 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
 //   warps 0-3  epilogue: thread t owns accumulator row t; drains one of two TMEM accumulators
 //              (tcgen05.ld -> output type -> staging row -> coalesced stores) while the other
 //              fills;
-//   warps 4-7  producer: per item builds atoms and per-axis tables, then for every step
+//   warps 4-11 producer: per item builds atoms and per-axis tables, then for every step
 //              (N tile, K chunk) writes the B operand into one of two shared-memory stages.
 //              The A operand does not depend on the N tile: when the item's K chunks fit the
 //              resident slots it is written once per K chunk into a slot of its own, else
 //              into the stage with B at every step;
-//   warp 8     MMA: one thread issues the tcgen05.mma pair of each step and commits to the
+//   warp 12    MMA: one thread issues the tcgen05.mma pair of each step and commits to the
 //              stage's "empty" barrier and, after a tile's last K chunk, to the accumulator's
 //              "full" barrier.
 // All three walk the same (item, N tile, K chunk) sequence, so every handoff is a
@@ -651,7 +651,14 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
 // bounded: a role that gives up raises a shared flag the others poll, then all drain and
 // the CTA frees its tensor memory.
 constexpr int kPipeStages = 2;
-constexpr int kPipeThreads = 288;  // 9 warps
+// Producer warps: 8 for packed tiles (molecules of a few dozen atoms, where building the
+// operands is the critical path), else 4 so that two CTAs fit an SM.
+__host__ __device__ constexpr int pipe_prod_warps(bool pack) { return pack ? 8 : 4; }
+// Threads of the pipelined kernel: epilogue, producers, MMA issuer.
+__host__ __device__ constexpr int pipe_threads(bool pack)
+{
+    return 128 + 32 * pipe_prod_warps(pack) + 32;
+}
 
 struct PipeLayout {
     int bars, tmem, flag, tile, atoms, stage0, stage_bytes, a_bytes, aslots, gx, gy, gz, out,
@@ -705,23 +712,25 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
                  : "memory");
 }
 
+template <int NPROD>
 __device__ __forceinline__ void producer_sync()
 {
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, %0;" ::"n"(NPROD) : "memory");
 }
 
-// True for every producer thread iff it is true for all of them (named barrier 1, 128
-// threads), so the producers always take the same branch after a bounded wait.
+// True for every producer thread iff it is true for all of them (named barrier 1, all
+// producer threads), so the producers always take the same branch after a bounded wait.
+template <int NPROD>
 __device__ __forceinline__ bool producers_all(bool v)
 {
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred p, q;\n\t"
         "setp.ne.u32 p, %1, 0;\n\t"
-        "bar.red.and.pred q, 1, 128, p;\n\t"
+        "bar.red.and.pred q, 1, %2, p;\n\t"
         "selp.u32 %0, 1, 0, q;\n\t}"
         : "=r"(r)
-        : "r"((uint32_t)v)
+        : "r"((uint32_t)v), "n"(NPROD)
         : "memory");
     return r != 0u;
 }
@@ -818,9 +827,11 @@ __device__ __forceinline__ PipeItem pipe_item(const SeparableArgs &A, long long 
 }
 
 template <typename T, int CUT, bool PER, int FORM, bool PACK>
-__global__ void __launch_bounds__(kPipeThreads, 2)
+__global__ void __launch_bounds__(pipe_threads(PACK), PACK ? 1 : 2)
     separable_pipe_kernel(const __grid_constant__ SeparableArgs A)
 {
+    constexpr int kProdWarps = pipe_prod_warps(PACK);
+    constexpr int kProducers = 32 * kProdWarps;
     extern __shared__ __align__(1024) unsigned char smem[];
     const Geometry &G = A.geo;
     const int tid = threadIdx.x;
@@ -841,7 +852,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
 
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
-            mbar_init(b_full(s), 4);     // one elected lane per producer warp
+            mbar_init(b_full(s), kProdWarps);  // one elected lane per producer warp
             mbar_init(b_empty(s), 1);    // tcgen05.commit
             mbar_init(acc_full(s), 1);   // tcgen05.commit
             mbar_init(acc_empty(s), 4);  // one elected lane per epilogue warp
@@ -866,9 +877,13 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
     const long long n_items = PACK ? ((long long)G.n_mol + A.pack - 1) / A.pack
                                          : (long long)G.n_mol * A.m_tiles;
 
-    if (warp >= 4 && warp < 8) {
+    if (warp >= 4 && warp < 4 + kProdWarps) {
         // ------------------------------------------------------------------ producer
-        const int p = tid - 128;
+        const int p = tid - 128;  // 0 .. kProducers - 1
+        // A-tile work: producer p builds row p % 128 of the tile, atom groups (p / 128) * 2 and
+        // (p / 128) * 2 + 1 of it.
+        const int arow = p & (kRows - 1);
+        const int ahalf = p / kRows;
         // Per atom of the K chunk: {x, y, z, q}, {r2, elem, k_erf, molecule within the tile},
         // and its molecule's grid geometry {ox, oy, oz, hx} with {hy, hz, weight, -}.  The
         // weight scales the atom's A entries (its g_x), exactly 1 for unweighted grids.
@@ -880,14 +895,15 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
         float *const tgx0 = reinterpret_cast<float *>(smem + L.gx);
         float *const tgy0 = reinterpret_cast<float *>(smem + L.gy);
         float *const tgz0 = reinterpret_cast<float *>(smem + L.gz);
-        const int dy32 = 32 / G.nz, dz32 = 32 - (32 / G.nz) * G.nz;
+        constexpr int kColStep = kProducers / 4;  // B columns between a producer's chunks
+        const int dyc = kColStep / G.nz, dzc = kColStep - (kColStep / G.nz) * G.nz;
         unsigned step = 0;
         bool ok = true;
         for (long long item = blockIdx.x; item < n_items && ok; item += gridDim.x) {
             const PipeItem it = pipe_item<PACK>(A, item);
             if (it.bad && p == 0 && it.m0 == 0) atomicOr(A.err, it.bad);
             // This producer's A row: molecule lm of the tile (0 unless packed), channel, x.
-            const int R = it.m0 + p;
+            const int R = it.m0 + arow;
             const int lm = PACK ? R / M : 0;
             const int r = R - lm * M;
             const bool row_ok = PACK ? lm < it.nb : R < M;
@@ -903,9 +919,10 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
             int *const t_off = reinterpret_cast<int *>(smem + L.tile);
             float *const t_geo = reinterpret_cast<float *>(t_off + (PACK ? A.pack + 1 : 0));
             if (PACK) {
-                producer_sync();
-                for (int k = p; k <= it.nb; k += 128) t_off[k] = __ldg(A.in.mol_off + it.b + k);
-                for (int k = p; k < 6 * it.nb; k += 128) {
+                producer_sync<kProducers>();
+                for (int k = p; k <= it.nb; k += kProducers)
+                    t_off[k] = __ldg(A.in.mol_off + it.b + k);
+                for (int k = p; k < 6 * it.nb; k += kProducers) {
                     const int m = it.b + k / 6, f = k % 6;
                     t_geo[k] = f < 3 ? __ldg(A.in.origin + 3 * m + f)
                                      : __ldg(A.in.spacing + 3 * m + f - 3);
@@ -919,7 +936,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                     const bool got = warp_wait(b_empty(s), ph ^ 1u, flag, A.wait_ns);
                     // A.stall (a test of the bounded waits) stops the producers before their
                     // first arrive: no MMA is issued and no store starts, and every wait gives up.
-                    if (!producers_all(got) || A.stall) {
+                    if (!producers_all<kProducers>(got) || A.stall) {
                         ok = false;
                         break;
                     }
@@ -934,7 +951,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                         const unsigned u = step - 1;
                         const bool done = warp_wait(b_empty((int)(u % kPipeStages)),
                                                     (u / kPipeStages) & 1u, flag, A.wait_ns);
-                        if (!producers_all(done)) {
+                        if (!producers_all<kProducers>(done)) {
                             ok = false;
                             break;
                         }
@@ -950,7 +967,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                     const bool new_atoms =
                         resident ? nc == 0 : ((nc == 0 && kc == 0) || it.n_kc > 1);
                     if (new_atoms) {
-                        producer_sync();  // every producer is done reading the old tables
+                        producer_sync<kProducers>();  // every producer is done reading the old tables
                         if (p < kKC) {
                             const int ai = it.a0 + kc * kKC + p;
                             float4 pos = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1003,7 +1020,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             atom_g0[p] = g0;
                             atom_g1[p] = g1;
                         }
-                        producer_sync();
+                        producer_sync<kProducers>();
                         // Per-axis tables of this K chunk: g_y, g_z, and for the erf form also
                         // g_x (an erf per A entry would cost more than the table).
                         if (FORM == 1 && !PER) {
@@ -1015,7 +1032,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             auto erf_table = [&](float *tab, int n, int stride, int axis) {
                                 const int blocks = (n + 31) >> 5;
 #pragma unroll 2
-                                for (int task = pw; task < kKC * blocks; task += 4) {
+                                for (int task = pw; task < kKC * blocks; task += kProdWarps) {
                                     const int j = task % kKC, i = (task / kKC) * 32 + lane;
                                     const float4 q4 = atom_pos[j];
                                     const float4 aux = atom_aux[j];
@@ -1039,7 +1056,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             erf_table(tgy, G.ny, kTab, 1);
                             erf_table(tgz, G.nz, kTab, 2);
                         }
-                        for (int i = p; FORM == 1 && PER && i < G.nx * kKC; i += 128) {
+                        for (int i = p; FORM == 1 && PER && i < G.nx * kKC; i += kProducers) {
                             const int x = i / kKC, j = i - (i / kKC) * kKC;
                             const float4 q4 = atom_pos[j];
                             const float4 g0 = PACK ? atom_g0[j]
@@ -1056,7 +1073,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             }
                             tgx[x * kTabX + j] = v;
                         }
-                        for (int i = p; (FORM == 0 || PER) && i < G.ny * kKC; i += 128) {
+                        for (int i = p; (FORM == 0 || PER) && i < G.ny * kKC; i += kProducers) {
                             const int y = i / kKC, j = i - (i / kKC) * kKC;
                             const float4 q4 = atom_pos[j];
                             const float oy = PACK ? atom_g0[j].y : it.oy;
@@ -1073,7 +1090,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             }
                             tgy[y * kTab + j] = v;
                         }
-                        for (int i = p; (FORM == 0 || PER) && i < G.nz * kKC; i += 128) {
+                        for (int i = p; (FORM == 0 || PER) && i < G.nz * kKC; i += kProducers) {
                             const int z = i / kKC, j = i - (i / kKC) * kKC;
                             const float4 q4 = atom_pos[j];
                             const float oz = PACK ? atom_g0[j].z : it.oz;
@@ -1090,12 +1107,13 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                             }
                             tgz[z * kTab + j] = v;
                         }
-                        producer_sync();
+                        producer_sync<kProducers>();
                     }
                     // A tile: once per K chunk of a resident tile, else every step.
                     if (!resident || nc == 0) {
 #pragma unroll
-                        for (int jg = 0; jg < kKC / 8; ++jg) {
+                        for (int jh = 0; jh < kKC / 16; ++jh) {
+                            const int jg = ahalf * (kKC / 16) + jh;
                             float v[8];
 #pragma unroll
                             for (int t = 0; t < 8; ++t) {
@@ -1122,8 +1140,8 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                                     }
                                 }
                             }
-                            *reinterpret_cast<uint4 *>(a_dst + (p >> 3) * 512 + jg * 128 +
-                                                       (p & 7) * 16) =
+                            *reinterpret_cast<uint4 *>(a_dst + (arow >> 3) * 512 + jg * 128 +
+                                                       (arow & 7) * 16) =
                                 make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
                                            pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
                         }
@@ -1135,7 +1153,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                         const int kg = (p >> 3) & 3;
                         int n = n0 + (p >> 5) * 8 + (p & 7);
                         int y = n / G.nz, z = n - (n / G.nz) * G.nz;
-                        for (int qi = p; qi < n_tile * (kKC / 8); qi += 128) {
+                        for (int qi = p; qi < n_tile * (kKC / 8); qi += kProducers) {
                             uint4 w = make_uint4(0u, 0u, 0u, 0u);
                             if (n < N) {
                                 const float4 *gy4 =
@@ -1149,9 +1167,9 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                                                pack_bf16x2(y1.z * z1.z, y1.w * z1.w));
                             }
                             *reinterpret_cast<uint4 *>(sb + qi * 16) = w;
-                            n += 32;
-                            z += dz32;
-                            y += dy32;
+                            n += kColStep;
+                            z += dzc;
+                            y += dyc;
                             if (z >= G.nz) {
                                 z -= G.nz;
                                 ++y;
@@ -1163,7 +1181,7 @@ __global__ void __launch_bounds__(kPipeThreads, 2)
                 }
             }
         }
-    } else if (warp == 8) {
+    } else if (warp == 4 + kProdWarps) {
         // ------------------------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = instr_desc(n_tile);
@@ -1407,7 +1425,7 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
     const void *f = dtype == PG_F32   ? pick_cut<float>(cut, per, pipe, form, pack)
                     : dtype == PG_F16 ? pick_cut<__half>(cut, per, pipe, form, pack)
                                       : pick_cut<__nv_bfloat16>(cut, per, pipe, form, pack);
-    const int threads = pipe ? kPipeThreads : kRows;
+    const int threads = pipe ? pipe_threads(a.pack > 0) : kRows;
     const int tmem_cols = pipe ? 2 * n_tile : n_tile;
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

@@ -100,7 +100,8 @@ def test_plan_reports_device_detected_errors(pg):
 def test_plan_launch_then_adjoint_then_wait(pg):
     # pg_plan_launch enqueues the copies and the forward pass without synchronizing; the
     # adjoint and the gradient's copy to the host follow on the same stream; pg_plan_wait
-    # synchronizes once and reports the error word.  Results equal the synchronous calls.
+    # waits for the plan's own work and reports its error word.  Results equal the
+    # synchronous calls.
     wl = synth.differentiation(n_mol=24)
     grid = pg.Grid.from_workload(wl)
     db = pg.DeviceBatch.from_numpy(wl.batch)
@@ -119,7 +120,8 @@ def test_plan_launch_then_adjoint_then_wait(pg):
                 plan.launch(*host, out=out, stream=stream)
             pg.voxelize_backward(db, grid, W, grad_coords=grad, stream=stream)
             grad_host.copy_(grad, non_blocking=True)
-            plan.wait(stream)
+            plan.wait(stream)      # the plan's own copies, kernel and error word
+            stream.synchronize()   # the adjoint and the gradient copy that follow it
             assert torch.equal(out, direct(pg, wl, wl.batch, "f32"))
             ref = pg.voxelize_backward(db, grid, W)
             assert pg.sync_status() == 0
@@ -147,6 +149,31 @@ if sys.argv[1] == "tune":
 else:
     print(json.dumps(api.get_tuning(db, grid, dtype="f32", path="direct")))
 """
+
+
+def test_two_plans_alternate(pg):
+    # Double buffering: batch i is launched on one plan before batch i - 1's plan is waited
+    # for; every output equals the stream-ordered call on its own batch.
+    wl = synth.qm9_shaped(n_mol=40)
+    grid = pg.Grid.from_workload(wl)
+    plans = [pg.Plan(grid, "f16", max_mol=20, max_atoms=int(wl.batch.n_atoms), path="direct")
+             for _ in range(2)]
+    stream = torch.cuda.Stream()
+    try:
+        subs = [wl.batch.subset(range(k * 10, k * 10 + 10 + k % 3)) for k in range(6)]
+        outs = [torch.empty(grid.out_shape(s.n_mol), dtype=torch.float16, device="cuda")
+                for s in subs]
+        hosts = [host_arrays(s, True) for s in subs]
+        plans[0].launch(*hosts[0], out=outs[0], stream=stream)
+        for i in range(1, len(subs)):
+            plans[i % 2].launch(*hosts[i], out=outs[i], stream=stream)
+            plans[(i - 1) % 2].wait(stream)
+        plans[(len(subs) - 1) % 2].wait(stream)
+        for s, o in zip(subs, outs):
+            assert torch.equal(o, direct(pg, wl, s, "f16"))
+    finally:
+        for p in plans:
+            p.close()
 
 
 def test_tuning_cache_file_named_by_the_environment(pg, tmp_path):
