@@ -283,7 +283,8 @@ pg_status pg_sync_status(void *stream, uint32_t *bits_out);
  * output (bitwise for the direct kernel's launch shapes, 1e-2 of the grid maximum for
  * the separable path), and record the fastest passing one for PG_PATH_AUTO.
  * Each candidate is timed as the median of single launches that each follow an unrelated
- * 32 MB device fill, as a launch runs inside a larger step.
+ * 32 MB device fill, as a launch runs inside a larger step; the fastest few of each path
+ * are then timed again, 15 launches each, interleaved, and their medians decide.
  * `out` is used as scratch and holds an arbitrary candidate's result afterwards; the call
  * also allocates and frees a 32 MB spacer buffer.
  * `path` restricts the search (AUTO = all eligible paths).  Synchronizes `stream`.

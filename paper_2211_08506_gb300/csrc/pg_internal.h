@@ -193,6 +193,10 @@ pg_status direct_launch_with_scratch(const pg_batch *b, const pg_grid *g, int dt
                                      unsigned *err, unsigned long long *sched, int sm_count,
                                      KernelLaunch *kl);
 
+// Raise kernel `func`'s dynamic shared-memory limit on the current device to at least `smem`
+// bytes.  Never lowered: a launch planned earlier with a larger size must still be valid.
+cudaError_t raise_smem_limit(const void *func, size_t smem);
+
 // Resident CTAs per SM of kernel `func` at `threads` threads and `smem` bytes of dynamic shared
 // memory on the current device, after raising the kernel's dynamic shared-memory limit to
 // `smem`.  Cached per (device, kernel, threads, smem): the driver calls cost microseconds,

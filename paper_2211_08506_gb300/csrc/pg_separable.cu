@@ -880,10 +880,11 @@ __global__ void __launch_bounds__(pipe_threads(PACK), PACK ? 1 : 2)
     if (warp >= 4 && warp < 4 + kProdWarps) {
         // ------------------------------------------------------------------ producer
         const int p = tid - 128;  // 0 .. kProducers - 1
-        // A-tile work: producer p builds row p % 128 of the tile, atom groups (p / 128) * 2 and
-        // (p / 128) * 2 + 1 of it.
+        // A-tile work: producer p builds row p % 128 of the tile, its kAGroups atom groups of 8
+        // starting at group (p / 128) * kAGroups.
+        constexpr int kAGroups = (kKC / 8) / (kProducers / kRows);
         const int arow = p & (kRows - 1);
-        const int ahalf = p / kRows;
+        const int ag0 = (p / kRows) * kAGroups;
         // Per atom of the K chunk: {x, y, z, q}, {r2, elem, k_erf, molecule within the tile},
         // and its molecule's grid geometry {ox, oy, oz, hx} with {hy, hz, weight, -}.  The
         // weight scales the atom's A entries (its g_x), exactly 1 for unweighted grids.
@@ -1112,8 +1113,8 @@ __global__ void __launch_bounds__(pipe_threads(PACK), PACK ? 1 : 2)
                     // A tile: once per K chunk of a resident tile, else every step.
                     if (!resident || nc == 0) {
 #pragma unroll
-                        for (int jh = 0; jh < kKC / 16; ++jh) {
-                            const int jg = ahalf * (kKC / 16) + jh;
+                        for (int jh = 0; jh < kAGroups; ++jh) {
+                            const int jg = ag0 + jh;
                             float v[8];
 #pragma unroll
                             for (int t = 0; t < 8; ++t) {
@@ -1427,7 +1428,7 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
                                       : pick_cut<__nv_bfloat16>(cut, per, pipe, form, pack);
     const int threads = pipe ? pipe_threads(a.pack > 0) : kRows;
     const int tmem_cols = pipe ? 2 * n_tile : n_tile;
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = raise_smem_limit(f, (size_t)smem);
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);

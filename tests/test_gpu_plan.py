@@ -154,7 +154,7 @@ else:
 def test_two_plans_alternate(pg):
     # Double buffering: batch i is launched on one plan before batch i - 1's plan is waited
     # for; every output equals the stream-ordered call on its own batch.
-    wl = synth.qm9_shaped(n_mol=40)
+    wl = synth.qm9_shaped(n_mol=72)
     grid = pg.Grid.from_workload(wl)
     plans = [pg.Plan(grid, "f16", max_mol=20, max_atoms=int(wl.batch.n_atoms), path="direct")
              for _ in range(2)]
