@@ -633,7 +633,7 @@ def measure(ses, wl, dtype, path, tag, W=None, e2e=True):
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     ev_mid = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ses.sampler.mark("start", tag)
-    _nvtx(torch, f"timed graph replays: {tag}")
+    _nvtx(torch, "timed_" + tag.replace(":", "_"))
     with torch.cuda.stream(stream):
         ev[0].record(stream)
         for i in range(args.steps):

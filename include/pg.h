@@ -308,7 +308,9 @@ pg_status pg_tuning_load(const char *file);
  * Plans: fixed-capacity input buffers plus a CUDA graph holding the host-to-device copy
  * of a batch and the voxelization launch, for on-the-fly grid generation from host data
  * (the data-loader use of Sec. V / Sec. VI-D).
- *   pg_plan_create  capacity max_mol molecules / max_atoms atoms; grid and dtype fixed.
+ *   pg_plan_create  capacity max_mol molecules / max_atoms atoms; grid, dtype and path fixed.
+ *                   Each run launches the choice pg_voxelize would make for its batch's
+ *                   bucket (atoms per molecule, weights, cell matrices).
  *   pg_plan_run     batch holds HOST pointers (pinned memory is copied directly;
  *                   pageable memory is first packed into the plan's pinned staging),
  *                   weight and cell included when given;

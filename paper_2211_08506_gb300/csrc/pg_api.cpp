@@ -409,8 +409,8 @@ struct pg_plan {
     pg_grid grid;
     std::vector<float> sigma;
     int dtype = 0;
-    pg_tuning tuning;
     int max_mol = 0, max_atoms = 0;
+    int path = PG_PATH_AUTO;  // as requested at creation
     float *d_coords = nullptr;
     int *d_elem = nullptr;
     int *d_moloff = nullptr;
@@ -1171,14 +1171,7 @@ pg_status pg_plan_create(pg_plan **plan, const pg_grid *grid, int32_t out_dtype,
     p->dtype = out_dtype;
     p->max_mol = max_mol;
     p->max_atoms = max_atoms;
-    // The launch choice is fixed at creation: the tuned entry for a batch of this
-    // capacity's shape if one exists, else the default for the path.
-    pg_batch shape = probe;
-    shape.n_mol = max_mol;
-    shape.n_atoms = max_atoms;
-    p->tuning = resolve(&shape, grid, out_dtype, path, *d);
-    if (p->tuning.path == PG_PATH_SEPARABLE && grid->cutoff == PG_CUTOFF_SPHERE)
-        p->tuning = default_tuning(PG_PATH_DIRECT);
+    p->path = path;
     const size_t A = (size_t)std::max(max_atoms, 1), M = (size_t)max_mol;
     const size_t sizes[kPlanCopies] = {A * 3 * 4, A * 4,      (M + 1) * 4, M * 3 * 4,
                                        M * 3 * 4, A * 4, M * 9 * 4};
@@ -1305,9 +1298,11 @@ pg_status pg_plan_launch(pg_plan *p, const pg_batch *hb, void *out, void *stream
     db.cell = hb->cell ? p->d_cell : nullptr;
     KernelLaunch kl;
     // A batch with cell matrices always takes the general-cell kernel.
-    const pg_tuning t = (hb->cell && p->tuning.path == PG_PATH_SEPARABLE)
-                            ? default_tuning(PG_PATH_DIRECT)
-                            : p->tuning;
+    // The launch choice of this batch's bucket (its atoms per molecule, and whether it
+    // carries weights or cell matrices), as pg_voxelize would make it.
+    pg_tuning t = resolve(hb, &p->grid, p->dtype, p->path, *d);
+    if (t.path == PG_PATH_SEPARABLE && (p->grid.cutoff == PG_CUTOFF_SPHERE || hb->cell))
+        t = default_tuning(PG_PATH_DIRECT);
     if ((st = plan_forward(&db, &p->grid, p->dtype, out, t, *d, p->d_err, p->d_sched, &kl)))
         return st;
     if ((st = plan_update_graph(p, src, cnt, dst, kl))) return st;
