@@ -638,12 +638,13 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
 //   warps 0-3  epilogue: thread t owns accumulator row t; drains one of two TMEM accumulators
 //              (tcgen05.ld -> output type -> staging row -> coalesced stores) while the other
 //              fills;
-//   warps 4-11 producer: per item builds atoms and per-axis tables, then for every step
+//   warps 4-7 (4-19 for packed tiles) producer: per item builds atoms and per-axis tables,
+//              then for every step
 //              (N tile, K chunk) writes the B operand into one of two shared-memory stages.
 //              The A operand does not depend on the N tile: when the item's K chunks fit the
 //              resident slots it is written once per K chunk into a slot of its own, else
 //              into the stage with B at every step;
-//   warp 12    MMA: one thread issues the tcgen05.mma pair of each step and commits to the
+//   warp 8 (20) MMA: one thread issues the tcgen05.mma pair of each step and commits to the
 //              stage's "empty" barrier and, after a tile's last K chunk, to the accumulator's
 //              "full" barrier.
 // All three walk the same (item, N tile, K chunk) sequence, so every handoff is a
@@ -651,9 +652,10 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
 // bounded: a role that gives up raises a shared flag the others poll, then all drain and
 // the CTA frees its tensor memory.
 constexpr int kPipeStages = 2;
-// Producer warps: 8 for packed tiles (molecules of a few dozen atoms, where building the
-// operands is the critical path), else 4 so that two CTAs fit an SM.
-__host__ __device__ constexpr int pipe_prod_warps(bool pack) { return pack ? 8 : 4; }
+// Producer warps: 16 for packed tiles (molecules of a few dozen atoms, where building the
+// operands is the critical path and each producer warp waits on long dependent chains), else 4
+// so that two CTAs fit an SM.
+__host__ __device__ constexpr int pipe_prod_warps(bool pack) { return pack ? 16 : 4; }
 // Threads of the pipelined kernel: epilogue, producers, MMA issuer.
 __host__ __device__ constexpr int pipe_threads(bool pack)
 {
