@@ -1097,7 +1097,7 @@ def main():
     ap.add_argument("--chunk-planes", type=int, default=8, help="--profile: planes per chunk")
     ap.add_argument("--chunk-order", type=int, default=0,
                     help="--profile: 0 = molecule-major chunks, 1 = channel-major")
-    ap.add_argument("--gather-only", type=int, default=0, help="--profile: 1 = no scatter mode")
+    ap.add_argument("--gather-only", type=int, default=0, help="--profile: 1 = gather only (no lane lists or factor tables)")
     ap.add_argument("--n-tile", type=int, default=128, help="--profile: separable tile width")
     args = ap.parse_args()
     if args.warmup < 3:

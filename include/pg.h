@@ -165,12 +165,13 @@ typedef struct {
  *                  path 2 also sizes its resident K chunks so that two CTAs fit an SM
  *   store_hint     0: default global stores; 1: streaming (evict-first) stores
  *   n_tile         separable path: output columns per tensor-core tile (64, 128 or 256)
- *   gather_only    direct path: 0 lets per-axis factors come from tables in shared memory:
- *                  in the point form with a cutoff (batches of molecules with more than 32
- *                  atoms on average), planes with 2 to 32 staged candidates take each one's z
- *                  factors from a per-plane table; in the voxel-integrated form with no or a box
- *                  cutoff, every chunk's atoms get y and z factor tables.  1 computes every
- *                  factor where it is used.  Both give identical bits.
+ *   gather_only    direct path, 0 allows the dense-plane modes: in the point form with a
+ *                  cutoff (batches of molecules with more than 32 atoms on average), each
+ *                  lane of a plane pass adds only the candidates that reach its own voxels
+ *                  (lane lists); in the voxel-integrated form with no or a box cutoff,
+ *                  every chunk's atoms get y and z factor tables in shared memory.  1: every
+ *                  lane adds every candidate of the pass, and every factor is computed where
+ *                  it is used.  Both give identical bits.
  *   chunk_planes   direct path: x-planes per dynamically scheduled work chunk (1..64; 0 = 8)
  *   separable_simple  separable path: 0 = warp-specialized pipeline (default), 1 = one-stage
  *                  kernel.  Both accumulate the same BF16 products in the same order.

@@ -25,10 +25,10 @@
 // across block sizes, occupancy, store hints and chunk sizes, and equal to the unstaged
 // fallback used when an item has more than kStageCap candidates.
 //
-// Planes with several staged candidates (kZtabMin to kZtabCands) can instead take their z
-// factors from a per-plane table (z-table mode, see ztab_plane), in a kernel instantiation of
-// its own.  It adds the same terms in the same order, so its results are bitwise identical to
-// the gather's.
+// Planes of large molecules can instead give each lane its own list of the candidates that
+// reach its voxels (lane-list mode, see lane_plane), in a kernel instantiation of its own.  It
+// adds the same terms in the same order, so its results are bitwise identical to the
+// gather's.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -39,9 +39,6 @@
 namespace pgi {
 
 namespace {
-
-// Staged candidates from which a plane takes its z factors from a table.
-constexpr int kZtabMin = 2;
 
 __device__ __forceinline__ float ex2_approx(float x)
 {
@@ -204,14 +201,50 @@ __device__ __forceinline__ void store_lane(T *out, int v, const float (&acc)[VEC
         out[v] = from_float<T>(acc[0]);
 }
 
+// One atom's terms on a lane's VEC columns of two rows (voxel centres vz[], rows vya and vyb):
+// the row factors once per row, each z factor once for both rows, the exact per-voxel test for
+// a sphere.  Every voxel adds the same terms in the same order of operations as
+// LaneVoxels::add.
+template <int VEC, int CUT, bool PER, int FORM>
+__device__ __forceinline__ void add_pair(float (&acc0)[VEC], float (&acc1)[VEC],
+                                         const float (&vz)[VEC], float vya, float vyb, float dx,
+                                         float ay, float az, float w, float q, float r2, float kf,
+                                         float hx, float hy, float hz, float Ly, float iLy,
+                                         float Lz, float iLz)
+{
+    const float dx2 = dx * dx;
+    float dya = vya - ay, dyb = vyb - ay;
+    if (PER) {
+        dya = wrap(dya, Ly, iLy);
+        dyb = wrap(dyb, Ly, iLy);
+    }
+    const float dxya = fmaf(dya, dya, dx2), dxyb = fmaf(dyb, dyb, dx2);
+    const float fx = FORM ? erf_axis(dx, hx, kf) : 0.0f;
+    const float ea = w * row_factor<CUT, FORM>(fx, dya, dx2, dxya, q, r2, kf, hy);
+    const float eb = w * row_factor<CUT, FORM>(fx, dyb, dx2, dxyb, q, r2, kf, hy);
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) {
+        float dz = vz[k] - az;
+        if (PER) dz = wrap(dz, Lz, iLz);
+        const float ez = z_factor<CUT, FORM>(dz, q, r2, kf, hz);
+        if (CUT == PG_CUTOFF_SPHERE) {
+            acc0[k] = (fmaf(dz, dz, dxya) <= r2) ? fmaf(ea, ez, acc0[k]) : acc0[k];
+            acc1[k] = (fmaf(dz, dz, dxyb) <= r2) ? fmaf(eb, ez, acc1[k]) : acc1[k];
+        } else {
+            acc0[k] = fmaf(ea, ez, acc0[k]);
+            acc1[k] = fmaf(eb, ez, acc1[k]);
+        }
+    }
+}
+
 // Gather of one plane in passes of two lane groups, for planes whose lane columns repeat
 // from group to group: with lpr = nz / VEC lanes per row, lane l < act = rpg * lpr owns the
 // columns z0 .. z0 + VEC - 1 of rows y0 + l / lpr and y0 + l / lpr + rpg of each pass of
 // 2 * rpg rows.  Each surviving atom's z factors are computed once per pass and shared by both
 // rows.  for_each(cy, wy, cz, wz, f) calls f(dx, ay, az, w), w the atom's weight, for the
 // candidates that can reach the pass's box of voxel centres, in atom order.  Every voxel adds
-// the same terms in the same order as LaneVoxels::add does (atoms culled for one of the two rows add exact zeros or are
-// skipped by the same test), so both give identical bits.
+// the same terms in the same order as LaneVoxels::add does (atoms culled for one of the two
+// rows add exact zeros or are skipped by the same test), so both give identical bits.
 template <typename T, int VEC, int CUT, bool PER, int HINT, int FORM, typename ForEach>
 __device__ __forceinline__ void blocked_plane(T *out, int ny, int nz, int rpg, int act,
                                               int my_row, int z0, int lane, float q, float r2,
@@ -235,29 +268,8 @@ __device__ __forceinline__ void blocked_plane(T *out, int ny, int nz, int rpg, i
 #pragma unroll
         for (int k = 0; k < VEC; ++k) acc0[k] = acc1[k] = 0.0f;
         for_each(cy, wy, cz, wz, [&](float dx, float ay, float az, float w) {
-            const float dx2 = dx * dx;
-            float dya = vya - ay, dyb = vyb - ay;
-            if (PER) {
-                dya = wrap(dya, Ly, iLy);
-                dyb = wrap(dyb, Ly, iLy);
-            }
-            const float dxya = fmaf(dya, dya, dx2), dxyb = fmaf(dyb, dyb, dx2);
-            const float fx = FORM ? erf_axis(dx, hx, kf) : 0.0f;
-            const float ea = w * row_factor<CUT, FORM>(fx, dya, dx2, dxya, q, r2, kf, hy);
-            const float eb = w * row_factor<CUT, FORM>(fx, dyb, dx2, dxyb, q, r2, kf, hy);
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) {
-                float dz = vz[k] - az;
-                if (PER) dz = wrap(dz, Lz, iLz);
-                const float ez = z_factor<CUT, FORM>(dz, q, r2, kf, hz);
-                if (CUT == PG_CUTOFF_SPHERE) {
-                    acc0[k] = (fmaf(dz, dz, dxya) <= r2) ? fmaf(ea, ez, acc0[k]) : acc0[k];
-                    acc1[k] = (fmaf(dz, dz, dxyb) <= r2) ? fmaf(eb, ez, acc1[k]) : acc1[k];
-                } else {
-                    acc0[k] = fmaf(ea, ez, acc0[k]);
-                    acc1[k] = fmaf(eb, ez, acc1[k]);
-                }
-            }
+            add_pair<VEC, CUT, PER, FORM>(acc0, acc1, vz, vya, vyb, dx, ay, az, w, q, r2, kf, hx,
+                                          hy, hz, Ly, iLy, Lz, iLz);
         });
         if (lane < act) {
             if (ya < ny) store_lane<T, VEC, HINT>(out, (ya * nz + z0) / VEC, acc0);
@@ -374,103 +386,68 @@ __device__ __forceinline__ int wrap_index(int i, int n)
     return r < 0 ? r + n : r;
 }
 
-// Z-table mode (Sec. VI-A's per-axis tables) for planes with several staged candidates, at
-// most kZtabCands: a candidate's z factors and z displacements do not depend on the row, so the
-// warp computes them once per plane into a table in shared memory, ztab[j][z] and
-// ztab[kZtabCands + j][z] (rows of nz rounded up to 4 floats), instead of in every pass.  The
-// plane is then walked in the passes of blocked_plane, and every term is formed from the same
-// values in the same order as there: identical bits.
-template <typename T, int VEC, int CUT, bool PER, int HINT, bool WGT>
-__device__ __forceinline__ void ztab_plane(T *out, float *ztab, const float4 *stage, int count,
-                                           int ny, int nz, int rpg, int act, int my_row, int z0,
-                                           int lane, float q, float r2, float rc, float oy,
-                                           float oz, float hy, float hz, float Ly, float iLy,
-                                           float Lz, float iLz)
+// Lane-list mode, for planes of large molecules (staged candidates) with a cutoff: the passes
+// of blocked_plane, but each lane adds only the candidates that can reach its own voxels.  A
+// lane owns VEC columns of two adjacent rows, a box of 2 x VEC voxel centres; for every
+// candidate that reaches the pass's box the warp tests, per lane, whether the candidate also
+// reaches the lane's box, and each lane then walks its own list in atom order.  On dense
+// planes a disc covers a small part of the 2 * rpg rows x nz columns of a pass, so the lane
+// lists are much shorter than the pass list: the warp runs as many terms as the longest lane
+// list rather than one per candidate of the pass.  The lists are conservative and in atom
+// order, and each term is add_pair's, as in blocked_plane: identical bits.
+template <typename T, int VEC, int CUT, bool PER, int HINT, int FORM, bool WGT>
+__device__ __forceinline__ void lane_plane(T *out, const float4 *stage, int count, int ny,
+                                           int nz, int rpg, int act, int my_row, int z0, int lane,
+                                           float q, float r2, float rc, float kf, float hx,
+                                           float oy, float oz, float hy, float hz, float Ly,
+                                           float iLy, float Lz, float iLz)
 {
-    const int nz4 = (nz + 3) & ~3;
-    float *const tez = ztab;
-    float *const tdz = ztab + kZtabCands * nz4;
-    // Table: entry (j, z) for j < count, z < nz, 32 entries per step; (j, z) advances by 32.
-    {
-        int j = lane / nz4, z = lane - (lane / nz4) * nz4;
-        const int dj = 32 / nz4, dzs = 32 - (32 / nz4) * nz4;
-        for (int base = 0; base < count * nz4; base += 32) {
-            if (j < count && z < nz) {
-                const float az = stage[j].z;
-                float dz = fmaf((float)z + 0.5f, hz, oz) - az;
-                if (PER) dz = wrap(dz, Lz, iLz);
-                tez[j * nz4 + z] = z_factor<CUT, 0>(dz, q, r2, 0.0f, hz);
-                tdz[j * nz4 + z] = dz;
-            }
-            j += dj;
-            z += dzs;
-            if (z >= nz4) {
-                z -= nz4;
-                ++j;
-            }
-        }
-    }
-    __syncwarp();
+    float vz[VEC];
+#pragma unroll
+    for (int k = 0; k < VEC; ++k) vz[k] = fmaf((float)(z0 + k) + 0.5f, hz, oz);
+    // Pass box: whole rows.  Lane box: the lane's VEC columns of its two rows.
     const float cz = fmaf(0.5f * (float)(nz - 1) + 0.5f, hz, oz);
     const float wz = 0.5f * (float)(nz - 1) * hz;
+    const float lcz = fmaf((float)z0 + 0.5f * (float)(VEC - 1) + 0.5f, hz, oz);
+    const float lwz = 0.5f * (float)(VEC - 1) * hz;
+    const float lwy = 0.5f * hy;
     for (int y0 = 0; y0 < ny; y0 += 2 * rpg) {
         const int y_end = min(y0 + 2 * rpg, ny) - 1;
         const float cy = fmaf(0.5f * (float)(y0 + y_end) + 0.5f, hy, oy);
         const float wy = 0.5f * (float)(y_end - y0) * hy;
-        const int ya = y0 + my_row, yb = ya + rpg;
+        const int ya = y0 + 2 * my_row, yb = ya + 1;
         const float vya = fmaf((float)ya + 0.5f, hy, oy);
         const float vyb = fmaf((float)yb + 0.5f, hy, oy);
+        const float lcy = fmaf((float)ya + 1.0f, hy, oy);
         float acc0[VEC], acc1[VEC];
 #pragma unroll
         for (int k = 0; k < VEC; ++k) acc0[k] = acc1[k] = 0.0f;
-        bool ok = false;
-        if (lane < count) {
-            const float4 st = stage[lane];
-            ok = reaches<CUT, PER>(st.x, st.y, st.z, cy, wy, cz, wz, rc, Ly, iLy, Lz, iLz);
-        }
-        unsigned m = __ballot_sync(0xffffffffu, ok);
-        while (m) {
-            const int j = __ffs(m) - 1;
-            m &= m - 1;
-            const float4 st = stage[j];
-            const float dx = st.x, ay = st.y;
-            const float w = WGT ? st.w : 1.0f;
-            const float dx2 = dx * dx;
-            float dya = vya - ay, dyb = vyb - ay;
-            if (PER) {
-                dya = wrap(dya, Ly, iLy);
-                dyb = wrap(dyb, Ly, iLy);
+        for (int cb = 0; cb < count; cb += 32) {
+            const int j = cb + lane;
+            bool ok = false;
+            if (j < count) {
+                const float4 st = stage[j];
+                ok = reaches<CUT, PER>(st.x, st.y, st.z, cy, wy, cz, wz, rc, Ly, iLy, Lz, iLz);
             }
-            const float dxya = fmaf(dya, dya, dx2), dxyb = fmaf(dyb, dyb, dx2);
-            const float ea = w * row_factor<CUT, 0>(0.0f, dya, dx2, dxya, q, r2, 0.0f, hy);
-            const float eb = w * row_factor<CUT, 0>(0.0f, dyb, dx2, dxyb, q, r2, 0.0f, hy);
-            float ez[VEC], dz[VEC];
-            const float *pez = tez + j * nz4 + z0;
-            const float *pdz = tdz + j * nz4 + z0;
-            if constexpr (VEC % 4 == 0) {
-#pragma unroll
-                for (int k = 0; k < VEC; k += 4) {
-                    const float4 e4 = *reinterpret_cast<const float4 *>(pez + k);
-                    const float4 d4 = *reinterpret_cast<const float4 *>(pdz + k);
-                    ez[k] = e4.x, ez[k + 1] = e4.y, ez[k + 2] = e4.z, ez[k + 3] = e4.w;
-                    dz[k] = d4.x, dz[k + 1] = d4.y, dz[k + 2] = d4.z, dz[k + 3] = d4.w;
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < VEC; ++k) {
-                    ez[k] = pez[k];
-                    dz[k] = pdz[k];
-                }
+            unsigned m = __ballot_sync(0xffffffffu, ok);
+            // The lane's list: bit i for candidate cb + i.
+            unsigned lm = 0u;
+            while (m) {
+                const int i = __ffs(m) - 1;
+                m &= m - 1;
+                const float4 st = stage[cb + i];
+                if (reaches<CUT, PER>(st.x, st.y, st.z, lcy, lwy, lcz, lwz, rc, Ly, iLy, Lz,
+                                      iLz))
+                    lm |= 1u << i;
             }
-#pragma unroll
-            for (int k = 0; k < VEC; ++k) {
-                if (CUT == PG_CUTOFF_SPHERE) {
-                    acc0[k] = (fmaf(dz[k], dz[k], dxya) <= r2) ? fmaf(ea, ez[k], acc0[k]) : acc0[k];
-                    acc1[k] = (fmaf(dz[k], dz[k], dxyb) <= r2) ? fmaf(eb, ez[k], acc1[k]) : acc1[k];
-                } else {
-                    acc0[k] = fmaf(ea, ez[k], acc0[k]);
-                    acc1[k] = fmaf(eb, ez[k], acc1[k]);
-                }
+            if (lane >= act) lm = 0u;
+            while (lm) {
+                const int i = __ffs(lm) - 1;
+                lm &= lm - 1;
+                const float4 st = stage[cb + i];
+                add_pair<VEC, CUT, PER, FORM>(acc0, acc1, vz, vya, vyb, st.x, st.y, st.z,
+                                              WGT ? st.w : 1.0f, q, r2, kf, hx, hy, hz, Ly, iLy,
+                                              Lz, iLz);
             }
         }
         if (lane < act) {
@@ -478,24 +455,22 @@ __device__ __forceinline__ void ztab_plane(T *out, float *ztab, const float4 *st
             if (yb < ny) store_lane<T, VEC, HINT>(out, (yb * nz + z0) / VEC, acc1);
         }
     }
-    __syncwarp();  // the next plane rebuilds the table
 }
 
 // WGT: per-atom weights (weighted grids).  Unweighted batches run the instantiation without
 // them, which carries no weight loads, shuffles or multiplies.
-template <typename T, int VEC, int CUT, bool PER, int HINT, bool SCAT, int FORM, bool WGT>
-__global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel(const DirectArgs A)
+template <typename T, int VEC, int CUT, bool PER, int HINT, bool LANE, int FORM, bool WGT>
+__global__ void __launch_bounds__(512, (LANE || VEC == 8) ? 1 : 2) direct_kernel(const DirectArgs A)
 {
     extern __shared__ float4 smem_all[];
     const Geometry &G = A.geo;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int warps_per_block = blockDim.x >> 5;
-    // Per warp (layout in direct_warp_floats): the plane's staged candidates, the chunk's
-    // channel atoms, then in z-table mode the plane's z-factor table.
-    float4 *stage = smem_all + (size_t)warp * (direct_warp_floats(A.ztab, A.erf_tab) / 4);
+    // Per warp (layout in direct_warp_floats): the plane's staged candidates, then the
+    // chunk's channel atoms.
+    float4 *stage = smem_all + (size_t)warp * (direct_warp_floats(A.erf_tab) / 4);
     float4 *chan = stage + kStageCap;
-    float *ztab = reinterpret_cast<float *>(chan + kChanCap);
     // Voxel-integrated form with a separable cutoff: per-chunk factor tables (table_plane).
     // Molecules of at most 32 atoms keep theirs in the staging area, which they do not use;
     // larger molecules keep theirs after their staged candidates and channel atoms, with each
@@ -734,8 +709,9 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                         });
                 } else if (blocked) {
                     blocked_plane<T, VEC, CUT, PER, HINT, FORM>(
-                        out, G.ny, G.nz, rpg, act, my_row, my_z0, lane, q, r2, kf, hx, oy, oz, hy,
-                        hz, Ly, iLy, Lz, iLz, [&](float cy, float wy, float cz, float wz, auto &&f) {
+                        out, G.ny, G.nz, rpg, act, my_row, my_z0, lane, q, r2, kf, hx, oy, oz,
+                        hy, hz, Ly, iLy, Lz, iLz,
+                        [&](float cy, float wy, float cz, float wz, auto &&f) {
                             const bool hit = cand && reaches<CUT, PER>(dx, my_y, my_z, cy, wy, cz,
                                                                        wz, rc, Ly, iLy, Lz, iLz);
                             unsigned m = __ballot_sync(0xffffffffu, hit);
@@ -876,14 +852,15 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
                                 }
                             }
                         });
-                } else if (SCAT && blocked && count >= kZtabMin && count <= kZtabCands) {
-                    ztab_plane<T, VEC, CUT, PER, HINT, WGT>(out, ztab, stage, count, G.ny, G.nz,
-                                                           rpg, act, my_row, my_z0, lane, q, r2,
-                                                           rc, oy, oz, hy, hz, Ly, iLy, Lz, iLz);
+                } else if (LANE && blocked && count <= kStageCap) {
+                    lane_plane<T, VEC, CUT, PER, HINT, FORM, WGT>(
+                        out, stage, count, G.ny, G.nz, rpg, act, my_row, my_z0, lane, q, r2,
+                        rc, kf, hx, oy, oz, hy, hz, Ly, iLy, Lz, iLz);
                 } else if (blocked && count <= kStageCap) {
                     blocked_plane<T, VEC, CUT, PER, HINT, FORM>(
-                        out, G.ny, G.nz, rpg, act, my_row, my_z0, lane, q, r2, kf, hx, oy, oz, hy,
-                        hz, Ly, iLy, Lz, iLz, [&](float cy, float wy, float cz, float wz, auto &&f) {
+                        out, G.ny, G.nz, rpg, act, my_row, my_z0, lane, q, r2, kf, hx, oy, oz,
+                        hy, hz, Ly, iLy, Lz, iLz,
+                        [&](float cy, float wy, float cz, float wz, auto &&f) {
                             for (int cb = 0; cb < count; cb += 32) {
                                 const int j = cb + lane;
                                 bool ok = false;
@@ -1000,37 +977,37 @@ __global__ void __launch_bounds__(512, (SCAT || VEC == 8) ? 1 : 2) direct_kernel
     }
 }
 
-// Z-table instantiations (SCAT) exist only for the point form and where a cutoff
-// bounds each atom's disc; the gather-only ones carry no z-table code and so keep their
-// register allocation.
+// Lane-list instantiations exist only for the point form and where a cutoff bounds each
+// atom's disc; the gather-only ones carry no lane-list code and so keep their register
+// allocation.
 template <typename T, int VEC, int CUT, bool PER, int HINT, int FORM>
-const void *pick_scat(bool scat)
+const void *pick_lane(bool lanes)
 {
     if constexpr (CUT != PG_CUTOFF_NONE && FORM == 0)
-        if (scat) return (const void *)direct_kernel<T, VEC, CUT, PER, HINT, true, FORM, false>;
+        if (lanes) return (const void *)direct_kernel<T, VEC, CUT, PER, HINT, true, FORM, false>;
     return (const void *)direct_kernel<T, VEC, CUT, PER, HINT, false, FORM, false>;
 }
 
 template <typename T, int VEC, int CUT, bool PER, int FORM>
-const void *pick_hint(int hint, bool scat)
+const void *pick_hint(int hint, bool lanes)
 {
-    return hint == 1 ? pick_scat<T, VEC, CUT, PER, 1, FORM>(scat)
-                     : pick_scat<T, VEC, CUT, PER, 0, FORM>(scat);
+    return hint == 1 ? pick_lane<T, VEC, CUT, PER, 1, FORM>(lanes)
+                     : pick_lane<T, VEC, CUT, PER, 0, FORM>(lanes);
 }
 
 template <typename T, int VEC, int FORM>
-const void *pick_shape(int cutoff, int periodic, int hint, bool scat)
+const void *pick_shape(int cutoff, int periodic, int hint, bool lanes)
 {
     if (periodic) {
         if (cutoff == PG_CUTOFF_SPHERE)
-            return pick_hint<T, VEC, PG_CUTOFF_SPHERE, true, FORM>(hint, scat);
-        if (cutoff == PG_CUTOFF_BOX) return pick_hint<T, VEC, PG_CUTOFF_BOX, true, FORM>(hint, scat);
-        return pick_hint<T, VEC, PG_CUTOFF_NONE, true, FORM>(hint, scat);
+            return pick_hint<T, VEC, PG_CUTOFF_SPHERE, true, FORM>(hint, lanes);
+        if (cutoff == PG_CUTOFF_BOX) return pick_hint<T, VEC, PG_CUTOFF_BOX, true, FORM>(hint, lanes);
+        return pick_hint<T, VEC, PG_CUTOFF_NONE, true, FORM>(hint, lanes);
     }
     if (cutoff == PG_CUTOFF_SPHERE)
-        return pick_hint<T, VEC, PG_CUTOFF_SPHERE, false, FORM>(hint, scat);
-    if (cutoff == PG_CUTOFF_BOX) return pick_hint<T, VEC, PG_CUTOFF_BOX, false, FORM>(hint, scat);
-    return pick_hint<T, VEC, PG_CUTOFF_NONE, false, FORM>(hint, scat);
+        return pick_hint<T, VEC, PG_CUTOFF_SPHERE, false, FORM>(hint, lanes);
+    if (cutoff == PG_CUTOFF_BOX) return pick_hint<T, VEC, PG_CUTOFF_BOX, false, FORM>(hint, lanes);
+    return pick_hint<T, VEC, PG_CUTOFF_NONE, false, FORM>(hint, lanes);
 }
 
 // Weighted instantiations: gather mode and default stores.
@@ -1065,18 +1042,18 @@ const void *pick_weighted(int dtype, bool vec_ok, int cut, int per)
 }
 
 // The instantiation for one launch: dtype, vector stores, cutoff, boundary, store hint,
-// z-table mode and voxel form.
+// lane-list mode and voxel form.
 template <int FORM>
-const void *pick_direct(int dtype, bool vec_ok, int cut, int per, int hint, bool scat)
+const void *pick_direct(int dtype, bool vec_ok, int cut, int per, int hint, bool lanes)
 {
     if (dtype == PG_F32)
-        return vec_ok ? pick_shape<float, 4, FORM>(cut, per, hint, scat)
-                      : pick_shape<float, 1, FORM>(cut, per, hint, scat);
+        return vec_ok ? pick_shape<float, 4, FORM>(cut, per, hint, lanes)
+                      : pick_shape<float, 1, FORM>(cut, per, hint, lanes);
     if (dtype == PG_F16)
-        return vec_ok ? pick_shape<__half, 8, FORM>(cut, per, hint, scat)
-                      : pick_shape<__half, 1, FORM>(cut, per, hint, scat);
-    return vec_ok ? pick_shape<__nv_bfloat16, 8, FORM>(cut, per, hint, scat)
-                  : pick_shape<__nv_bfloat16, 1, FORM>(cut, per, hint, scat);
+        return vec_ok ? pick_shape<__half, 8, FORM>(cut, per, hint, lanes)
+                      : pick_shape<__half, 1, FORM>(cut, per, hint, lanes);
+    return vec_ok ? pick_shape<__nv_bfloat16, 8, FORM>(cut, per, hint, lanes)
+                  : pick_shape<__nv_bfloat16, 1, FORM>(cut, per, hint, lanes);
 }
 
 }  // namespace

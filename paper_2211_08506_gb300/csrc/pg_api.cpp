@@ -233,15 +233,14 @@ pg_tuning default_tuning(int path)
     return t;
 }
 
-// Whether the direct kernel runs with z-table mode (its z-table instantiation): the point form
-// with a cutoff, axes of at most 256 voxels, unweighted axis-aligned boxes.  Molecules of at
-// most 32 atoms never reach it (they take the register path), so a batch whose mean is that
-// small keeps the gather-only instantiation and its higher occupancy.
-bool direct_scatter_on(const pg_batch *b, const pg_grid *g, const pg_tuning &t)
+// Whether the direct kernel runs in lane-list mode (its lane-list instantiation): the point
+// form with a cutoff, unweighted axis-aligned boxes.  Molecules of at most 32 atoms never
+// reach it (they take the register path), so a batch whose mean is that small keeps the
+// gather-only instantiation and its higher occupancy.
+bool direct_lanes_on(const pg_batch *b, const pg_grid *g, const pg_tuning &t)
 {
     return !t.gather_only && g->voxel_form == PG_FORM_POINT && !b->weight && !b->cell &&
-           g->cutoff != PG_CUTOFF_NONE && g->ny <= 256 && g->nz <= 256 &&
-           b->n_atoms > 32LL * b->n_mol;
+           g->cutoff != PG_CUTOFF_NONE && b->n_atoms > 32LL * b->n_mol;
 }
 
 // Floats of per-warp factor table for the direct kernel's voxel-integrated form with a
@@ -300,14 +299,14 @@ pg_status plan_forward(const pg_batch *b, const pg_grid *g, int dtype, void *out
     a.out = out;
     a.err = err;
     a.sched = sched;
-    a.ztab = direct_scatter_on(b, g, t) ? direct_ztab_floats(g->nz) : 0;
+    a.lane_lists = direct_lanes_on(b, g, t) ? 1 : 0;
     a.chunk_planes = (t.chunk_planes >= 1 && t.chunk_planes <= 64) ? t.chunk_planes : 8;
     a.chunk_order = t.chunk_order == 1 ? 1 : 0;
     a.erf_tab = direct_erf_tab(b, g, t);
     a.geo = G;
     const int vec = vec_stores_ok(out, g, dtype) ? 1 : 0;
     if (b->cell) {
-        a.ztab = 0;
+        a.lane_lists = 0;
         a.erf_tab = 0;
         cudaError_t e = cell_plan(a, dtype, vec, t, d.sms, kl);
         if (e != cudaSuccess) return cuda_fail(e, "cell_plan");
@@ -657,7 +656,7 @@ pg_status direct_launch_with_scratch(const pg_batch *b, const pg_grid *g, int dt
     a.err = err;
     a.sched = sched;
     const pg_tuning t = default_tuning(PG_PATH_DIRECT);
-    a.ztab = direct_scatter_on(b, g, t) ? direct_ztab_floats(g->nz) : 0;
+    a.lane_lists = direct_lanes_on(b, g, t) ? 1 : 0;
     a.chunk_planes = 8;
     a.erf_tab = b->cell ? 0 : direct_erf_tab(b, g, t);
     make_geometry(b, g, &a.geo);
@@ -871,8 +870,8 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
         cands.push_back(default_tuning(PG_PATH_DIRECT));
         const pg_tuning def = default_tuning(PG_PATH_DIRECT);
         const int go_max =
-            (direct_scatter_on(batch, grid, def) || direct_erf_tab(batch, grid, def) > 0) ? 1 : 0;
-        // The general-cell kernel has a fixed block and no store hint or scatter mode: only
+            (direct_lanes_on(batch, grid, def) || direct_erf_tab(batch, grid, def) > 0) ? 1 : 0;
+        // The general-cell kernel has a fixed block and no store hint or lane-list mode: only
         // the residency and the chunk size vary.
         if (batch->cell)
             for (int order : {0, 1})

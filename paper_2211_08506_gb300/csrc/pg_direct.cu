@@ -9,16 +9,16 @@ cudaError_t direct_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tun
                         int sm_count, KernelLaunch *kl)
 {
     const int hint = t.store_hint == 1 ? 1 : 0;
-    const bool scat = a.ztab > 0 && a.geo.cutoff != PG_CUTOFF_NONE;
+    const bool lanes = a.lane_lists != 0 && a.geo.cutoff != PG_CUTOFF_NONE;
     const int cut = a.geo.cutoff, per = a.geo.periodic;
     const void *f = a.in.weight ? pick_direct_weighted(dtype, vec_ok != 0, cut, per, a.geo.form)
                     : a.geo.form == PG_FORM_INTEGRAL
                         ? pick_direct_integral(dtype, vec_ok != 0, cut, per, hint)
-                        : pick_direct<0>(dtype, vec_ok != 0, cut, per, hint, scat);
+                        : pick_direct<0>(dtype, vec_ok != 0, cut, per, hint, lanes);
 
     int threads = t.block_threads;
     if (threads != 128 && threads != 256 && threads != 512) threads = 256;
-    const size_t per_warp = (size_t)direct_warp_floats(a.ztab, a.erf_tab) * sizeof(float);
+    const size_t per_warp = (size_t)direct_warp_floats(a.erf_tab) * sizeof(float);
     while (threads > 128 && (size_t)(threads / 32) * per_warp > 200 * 1024) threads /= 2;
     const size_t smem = (size_t)(threads / 32) * per_warp;
     int per_sm = 0;

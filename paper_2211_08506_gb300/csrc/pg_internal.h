@@ -63,8 +63,6 @@ struct Inputs {
     const float *cell;    // per-molecule 3x3 box edges (rows), or null (axis-aligned box)
 };
 
-// Staged candidates of a plane whose z factors the direct kernel's z-table mode tabulates.
-constexpr int kZtabCands = 32;
 // Largest per-warp factor table of the voxel-integrated form (floats).
 constexpr int kErfTabCap = 4096;
 
@@ -75,23 +73,15 @@ __host__ __device__ inline int erf_table_stride(int ny, int nz)
     return ((ny + 3) & ~3) + ((nz + 3) & ~3);
 }
 
-// Floats of the direct kernel's per-warp z-factor table in z-table mode: z factors and z
-// displacements of kZtabCands candidates, rows of nz rounded up to 4.
-__host__ __device__ inline int direct_ztab_floats(int nz)
-{
-    return 2 * kZtabCands * ((nz + 3) & ~3);
-}
-
 // 32-bit words of dynamic shared memory per warp of the direct kernel: kStageCap staged
 // candidates and kChanCap channel atoms (float4 each), or, if larger, the voxel-integrated
 // form's factor table (erf_tab words: molecules of at most 32 atoms use it from the start,
-// larger ones past the staging area), then, in z-table mode (point form only), the plane's
-// z-factor table (ztab words), and with a factor table the staged candidates' x factors
-// (kStageCap words).  A multiple of 4 words.
-__host__ __device__ inline int direct_warp_floats(int ztab, int erf_tab)
+// larger ones past the staging area), then, with a factor table, the staged candidates' x
+// factors (kStageCap words).  A multiple of 4 words.
+__host__ __device__ inline int direct_warp_floats(int erf_tab)
 {
     const int staging = 4 * (kStageCap + kChanCap);
-    return (erf_tab > staging ? erf_tab : staging) + ztab + (erf_tab > 0 ? kStageCap : 0);
+    return (erf_tab > staging ? erf_tab : staging) + (erf_tab > 0 ? kStageCap : 0);
 }
 
 struct DirectArgs {
@@ -99,7 +89,7 @@ struct DirectArgs {
     void *out;
     unsigned *err;
     unsigned long long *sched;  // {next chunk, retired warps}; zero between launches
-    int ztab;                   // floats of per-warp z-factor table, z-table mode (0: off)
+    int lane_lists;             // 1: lane-list mode for large molecules (its instantiation)
     int chunk_planes;           // x-planes per dynamically scheduled chunk (>= 1)
     int chunk_order;            // 0: (molecule, channel) order; 1: channel-major
     int erf_tab;                // floats of per-warp factor table, voxel-integrated form (0: off)
@@ -166,7 +156,7 @@ cudaError_t direct_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tun
 // adjoint.
 cudaError_t backward_plan(const BackwardArgs &a, int grad_dtype, int sm_count, KernelLaunch *kl);
 
-// General cells (pg_cell.cu): forward over a DirectArgs description (ztab unused) and
+// General cells (pg_cell.cu): forward over a DirectArgs description (lane_lists unused) and
 // the adjoint.  cudaErrorNotSupported for a periodic cell without a cutoff.
 cudaError_t cell_plan(const DirectArgs &a, int dtype, int vec_ok, const pg_tuning &t,
                       int sm_count, KernelLaunch *kl);

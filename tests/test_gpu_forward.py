@@ -240,8 +240,8 @@ def test_register_and_staged_paths_agree_bitwise(pg):
         G1 = run(pg, wl, dtype=dtype)
         G2 = run(pg, wl, dtype=dtype, batch=padded, tuning={"path": 1, "gather_only": 1})
         assert np.array_equal(G1, G2)
-        # With z-table mode allowed, planes of the padded batch with several candidates read
-        # their z factors from a table: the same terms in the same order, identical bits.
+        # With lane-list mode allowed, each lane of a staged plane adds only the candidates
+        # that reach its own voxels: the same terms in the same order, identical bits.
         G3 = run(pg, wl, dtype=dtype, batch=padded, tuning={"path": 1})
         assert np.array_equal(G3, G1)
 
@@ -249,10 +249,11 @@ def test_register_and_staged_paths_agree_bitwise(pg):
 @pytest.mark.parametrize("cutoff,periodic,shape", [
     ("sphere", False, (48, 48, 48)), ("box", False, (48, 48, 48)), ("box", True, (48, 48, 48)),
     ("sphere", True, (40, 44, 45)), ("box", False, (37, 52, 30))])
-def test_ztab_mode_every_cutoff_boundary_and_ragged_plane(pg, cutoff, periodic, shape):
-    # Z-table mode against the gather mode on dense cells, for both cutoffs, open and
-    # periodic boundaries, and ragged planes that take the scalar store path.  The two modes
-    # add the same terms in the same order: identical bits, and both match the oracle.
+def test_lane_list_mode_every_cutoff_boundary_and_ragged_plane(pg, cutoff, periodic, shape):
+    # Lane-list mode against the gather mode on dense cells, for both cutoffs, open and
+    # periodic boundaries, and ragged planes that take the scalar store path (one column per
+    # lane).  The two modes add the same terms in the same order: identical bits, and both
+    # match the oracle.
     wl = synth.crystal_shaped(n_cells=10)
     wl.cutoff, wl.periodic = cutoff, periodic
     wl.nx, wl.ny, wl.nz = shape
@@ -266,10 +267,9 @@ def test_ztab_mode_every_cutoff_boundary_and_ragged_plane(pg, cutoff, periodic, 
             grid_check(G[:4], prob, TOL[dtype], abs_tol=ABS_TOL[dtype])
 
 
-def test_ztab_and_gather_modes_on_dense_cells(pg):
-    # Dense periodic cells: planes with two or more candidates take z-table mode unless
-    # gather_only is set.  Both modes are bitwise equal to each other across launch shapes
-    # and match the oracle.
+def test_lane_list_and_gather_modes_on_dense_cells(pg):
+    # Dense periodic cells: staged planes take lane-list mode unless gather_only is set.
+    # Both modes are bitwise equal to each other across launch shapes and match the oracle.
     wl = synth.crystal_shaped(n_cells=24)
     for dtype in ("f32", "f16"):
         auto = run(pg, wl, dtype=dtype, tuning={"path": 1, "block_threads": 256})
@@ -305,11 +305,10 @@ def test_chunk_orders_give_identical_bits(pg, kind):
 
 
 @pytest.mark.parametrize("periodic", [False, True])
-def test_ztab_mode_wide_discs(pg, periodic):
-    # Wide discs on a fine grid (r_c = 1.5 A on 0.05 A voxels: about 60 voxels across; 64-voxel
-    # table rows) and dense planes of up to about 30 candidates, some above the table's limit
-    # of 32; atoms near the faces so that periodic images wrap.  Bitwise equal to the gather,
-    # and equal to the oracle.
+def test_lane_list_mode_wide_discs(pg, periodic):
+    # Wide discs on a fine grid (r_c = 1.5 A on 0.05 A voxels: about 60 voxels across, wider
+    # than a pass) and dense planes of up to about 30 candidates; atoms near the faces so that
+    # periodic images wrap.  Bitwise equal to the gather, and equal to the oracle.
     rng = np.random.default_rng(41)
     n = 64
     h = 0.05
