@@ -653,13 +653,17 @@ __global__ void __launch_bounds__(128, 1) separable_kernel(const SeparableArgs A
 // the CTA frees its tensor memory.
 constexpr int kPipeStages = 2;
 // Producer warps: 16 for packed tiles (molecules of a few dozen atoms, where building the
-// operands is the critical path and each producer warp waits on long dependent chains), else 4
-// so that two CTAs fit an SM.
-__host__ __device__ constexpr int pipe_prod_warps(bool pack) { return pack ? 16 : 4; }
-// Threads of the pipelined kernel: epilogue, producers, MMA issuer.
-__host__ __device__ constexpr int pipe_threads(bool pack)
+// operands is the critical path and each producer warp waits on long dependent chains) with
+// 2-byte outputs, 8 with FP32 outputs (whose epilogue needs more registers than a 21-warp CTA
+// leaves), else 4 so that two CTAs fit an SM.
+__host__ __device__ constexpr int pipe_prod_warps(bool pack, int esz)
 {
-    return 128 + 32 * pipe_prod_warps(pack) + 32;
+    return pack ? (esz == 4 ? 8 : 16) : 4;
+}
+// Threads of the pipelined kernel: epilogue, producers, MMA issuer.
+__host__ __device__ constexpr int pipe_threads(bool pack, int esz)
+{
+    return 128 + 32 * pipe_prod_warps(pack, esz) + 32;
 }
 
 struct PipeLayout {
@@ -829,10 +833,10 @@ __device__ __forceinline__ PipeItem pipe_item(const SeparableArgs &A, long long 
 }
 
 template <typename T, int CUT, bool PER, int FORM, bool PACK>
-__global__ void __launch_bounds__(pipe_threads(PACK), PACK ? 1 : 2)
+__global__ void __launch_bounds__(pipe_threads(PACK, (int)sizeof(T)), PACK ? 1 : 2)
     separable_pipe_kernel(const __grid_constant__ SeparableArgs A)
 {
-    constexpr int kProdWarps = pipe_prod_warps(PACK);
+    constexpr int kProdWarps = pipe_prod_warps(PACK, (int)sizeof(T));
     constexpr int kProducers = 32 * kProdWarps;
     extern __shared__ __align__(1024) unsigned char smem[];
     const Geometry &G = A.geo;
@@ -1428,7 +1432,7 @@ cudaError_t separable_plan(const SeparableArgs &a0, int dtype, const pg_tuning &
     const void *f = dtype == PG_F32   ? pick_cut<float>(cut, per, pipe, form, pack)
                     : dtype == PG_F16 ? pick_cut<__half>(cut, per, pipe, form, pack)
                                       : pick_cut<__nv_bfloat16>(cut, per, pipe, form, pack);
-    const int threads = pipe ? pipe_threads(a.pack > 0) : kRows;
+    const int threads = pipe ? pipe_threads(a.pack > 0, esz) : kRows;
     const int tmem_cols = pipe ? 2 * n_tile : n_tile;
     cudaError_t e = raise_smem_limit(f, (size_t)smem);
     if (e != cudaSuccess) return e;
