@@ -256,13 +256,16 @@ def write_probe_gbs(nbytes=4 << 30, reps=10):
     return max(res.values()), res
 
 
-KERNEL_SOURCES = {"direct": ("direct_kernel.cuh",), "separable": ("pg_separable.cu",),
-                  "backward": ("pg_backward.cu",), "cell": ("pg_cell.cu",)}
+KERNEL_SOURCES = {"direct": ("direct_kernel.cuh", "pg_internal.h"),
+                  "separable": ("pg_separable.cu", "pg_internal.h"),
+                  "backward": ("pg_backward.cu", "pg_internal.h"),
+                  "cell": ("pg_cell.cu", "direct_kernel.cuh", "pg_internal.h")}
 CELL_WORKLOADS = ("crystal_shaped", "crystal_triclinic")
 
 
 def kernel_source_sha(kernel: str) -> str:
-    """First 16 hex digits of the SHA-256 of the kernel's CUDA source."""
+    """First 16 hex digits of the SHA-256 of the kernel's CUDA sources (the kernel's file and
+    the headers it includes from the package)."""
     h = hashlib.sha256()
     for f in KERNEL_SOURCES[kernel]:
         p = os.path.join(ROOT, "paper_2211_08506_gb300", "csrc", f)
