@@ -137,6 +137,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
     return ok != 0u;
 }
 
+// As mbar_try_wait, but a thread whose phase has not completed is suspended by the hardware
+// until it completes or about kSuspendNs have passed, instead of polling: the waiting warps
+// issue almost nothing and wake as soon as the phase completes.
+constexpr unsigned kSuspendNs = 2000;
+__device__ __forceinline__ bool mbar_wait_suspend(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "n"(kSuspendNs)
+        : "memory");
+    return ok != 0u;
+}
+
 // Bounded wait, at most kDrainNs, for phase 0 of the drain barrier: the final tcgen05.commit a
 // CTA issues before it frees its tensor memory, which arrives once every MMA the committing
 // thread issued has completed (at once when none is outstanding).
@@ -145,9 +162,8 @@ __device__ __forceinline__ bool drain_wait(uint32_t bar)
 {
     const unsigned long long t0 = global_ns();
     for (unsigned it = 0; it < kWaitLimit; ++it) {
-        if (mbar_try_wait(bar, 0u)) return true;
-        if ((it & 63u) == 63u && global_ns() - t0 > kDrainNs) return false;
-        __nanosleep(32);
+        if (mbar_wait_suspend(bar, 0u)) return true;
+        if ((it & 3u) == 3u && global_ns() - t0 > kDrainNs) return false;
     }
     return false;
 }
@@ -748,9 +764,8 @@ __device__ __forceinline__ bool pipe_wait(uint32_t bar, uint32_t parity, volatil
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (unsigned it = 0; it < kWaitLimit; ++it) {
-        __nanosleep(32);  // back off so waiting warps leave issue slots to working ones
-        if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 63u) == 63u && (*flag || global_ns() - t0 > wait_ns)) break;
+        if (mbar_wait_suspend(bar, parity)) return true;
+        if ((it & 3u) == 3u && (*flag || global_ns() - t0 > wait_ns)) break;
     }
     *flag = 1;
     return false;
