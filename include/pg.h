@@ -285,7 +285,9 @@ pg_status pg_sync_status(void *stream, uint32_t *bits_out);
  * the separable path), and record the fastest passing one for PG_PATH_AUTO.
  * Each candidate is timed as the median of single launches that each follow an unrelated
  * 32 MB device fill, as a launch runs inside a larger step; the fastest few of each path
- * are then timed again, 15 launches each, interleaved, and their medians decide.
+ * are then timed again, interleaved, as 15 pairs of launches after the fill (the first of a
+ * pair as after unrelated work, the second right after the same kernel, as consecutive graph
+ * replays run), and the mean of the two medians decides.
  * `out` is used as scratch and holds an arbitrary candidate's result afterwards; the call
  * also allocates and frees a 32 MB spacer buffer.
  * `path` restricts the search (AUTO = all eligible paths).  Synchronizes `stream`.

@@ -932,7 +932,7 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
     constexpr size_t kSpacerBytes = 32u << 20;
     unsigned long long *d_hash = nullptr;
     float *d_cmp = nullptr;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, e2 = nullptr;
     std::vector<float> times(cands.size(), INFINITY);
     auto cleanup = [&]() {
         cudaFree(sample);
@@ -941,6 +941,7 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
         cudaFree(d_cmp);
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
+        if (e2) cudaEventDestroy(e2);
     };
     auto cu = [&](cudaError_t e, const char *what) -> pg_status {
         if (e == cudaSuccess) return PG_OK;
@@ -953,6 +954,7 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
     if ((st = cu(cudaMalloc(&d_cmp, 2 * sizeof(float)), "cudaMalloc"))) return st;
     if ((st = cu(cudaEventCreate(&e0), "cudaEventCreate"))) return st;
     if ((st = cu(cudaEventCreate(&e1), "cudaEventCreate"))) return st;
+    if ((st = cu(cudaEventCreate(&e2), "cudaEventCreate"))) return st;
     const size_t out_bytes = per_mol * (size_t)batch->n_mol * esz;
 
     unsigned long long ref_hash = 0;
@@ -1018,8 +1020,11 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
     }
 
     // Second round: the fastest few candidates of each path are timed again, 15 times each,
-    // interleaved so that clock and memory-state drift affects them alike; their medians
-    // replace the first-round times.
+    // interleaved so that clock and memory-state drift affects them alike.  Each time is a
+    // pair of launches after the spacer fill: the first runs as after unrelated work, the
+    // second right after a launch of the same kernel, as graph replays of one step follow
+    // each other.  The sum of the two medians replaces the first-round time (halved, so that
+    // it stays comparable to a single launch).
     {
         std::vector<int> order;
         for (size_t i = 0; i < cands.size(); ++i)
@@ -1043,7 +1048,7 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
                 t_last_error.clear();
                 kls[t].func = nullptr;
             }
-        std::vector<std::vector<float>> ms(top.size());
+        std::vector<std::vector<float>> ms(top.size()), ms2(top.size());
         for (int r = 0; r < 15; ++r)
             for (size_t t = 0; t < top.size(); ++t) {
                 if (!kls[t].func) continue;
@@ -1051,15 +1056,20 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
                 if ((st = cu(cudaEventRecord(e0, s), "event"))) return st;
                 if ((st = cu(launch(kls[t], s), "tune launch"))) return st;
                 if ((st = cu(cudaEventRecord(e1, s), "event"))) return st;
-                if ((st = cu(cudaEventSynchronize(e1), "event sync"))) return st;
-                float ev = 0;
+                if ((st = cu(launch(kls[t], s), "tune launch"))) return st;
+                if ((st = cu(cudaEventRecord(e2, s), "event"))) return st;
+                if ((st = cu(cudaEventSynchronize(e2), "event sync"))) return st;
+                float ev = 0, ev2 = 0;
                 if ((st = cu(cudaEventElapsedTime(&ev, e0, e1), "elapsed"))) return st;
+                if ((st = cu(cudaEventElapsedTime(&ev2, e1, e2), "elapsed"))) return st;
                 ms[t].push_back(ev);
+                ms2[t].push_back(ev2);
             }
         for (size_t t = 0; t < top.size(); ++t) {
             if (ms[t].empty()) continue;
             std::sort(ms[t].begin(), ms[t].end());
-            times[top[t]] = ms[t][ms[t].size() / 2];
+            std::sort(ms2[t].begin(), ms2[t].end());
+            times[top[t]] = 0.5f * (ms[t][ms[t].size() / 2] + ms2[t][ms2[t].size() / 2]);
         }
     }
     cleanup();
