@@ -53,25 +53,31 @@ __device__ __forceinline__ Frame load_frame(const Inputs &in, int b)
 #pragma unroll
     for (int i = 0; i < 3; ++i) f.o[i] = __ldg(in.origin + 3 * b + i);
     const float *M = f.M;
-    const float c0 = M[4] * M[8] - M[5] * M[7], c1 = M[5] * M[6] - M[3] * M[8],
-                c2 = M[3] * M[7] - M[4] * M[6];
-    const float det = M[0] * c0 + M[1] * c1 + M[2] * c2;
+    // Every product and sum is spelled out (fmaf, __fmul_rn), so that the compiler cannot
+    // contract them differently in different kernel instantiations: forward and adjoint
+    // kernels of any store width get the same bits of the inverse.
+    auto cof = [](float a, float b, float c, float d) {  // a b - c d
+        return fmaf(a, b, -__fmul_rn(c, d));
+    };
+    const float c0 = cof(M[4], M[8], M[5], M[7]), c1 = cof(M[5], M[6], M[3], M[8]),
+                c2 = cof(M[3], M[7], M[4], M[6]);
+    const float det = fmaf(M[0], c0, fmaf(M[1], c1, __fmul_rn(M[2], c2)));
     f.ok = isfinite(det) && det != 0.0f;
     const float id = f.ok ? 1.0f / det : 0.0f;
-    f.Mi[0] = c0 * id;
-    f.Mi[1] = (M[2] * M[7] - M[1] * M[8]) * id;
-    f.Mi[2] = (M[1] * M[5] - M[2] * M[4]) * id;
-    f.Mi[3] = c1 * id;
-    f.Mi[4] = (M[0] * M[8] - M[2] * M[6]) * id;
-    f.Mi[5] = (M[2] * M[3] - M[0] * M[5]) * id;
-    f.Mi[6] = c2 * id;
-    f.Mi[7] = (M[1] * M[6] - M[0] * M[7]) * id;
-    f.Mi[8] = (M[0] * M[4] - M[1] * M[3]) * id;
+    f.Mi[0] = __fmul_rn(c0, id);
+    f.Mi[1] = __fmul_rn(cof(M[2], M[7], M[1], M[8]), id);
+    f.Mi[2] = __fmul_rn(cof(M[1], M[5], M[2], M[4]), id);
+    f.Mi[3] = __fmul_rn(c1, id);
+    f.Mi[4] = __fmul_rn(cof(M[0], M[8], M[2], M[6]), id);
+    f.Mi[5] = __fmul_rn(cof(M[2], M[3], M[0], M[5]), id);
+    f.Mi[6] = __fmul_rn(c2, id);
+    f.Mi[7] = __fmul_rn(cof(M[1], M[6], M[0], M[7]), id);
+    f.Mi[8] = __fmul_rn(cof(M[0], M[4], M[1], M[3]), id);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
         const float x = f.Mi[k], y = f.Mi[3 + k], z = f.Mi[6 + k];
         f.g2[k] = sqrtf(fmaf(x, x, fmaf(y, y, z * z)));
-        f.g1[k] = fabsf(x) + fabsf(y) + fabsf(z);
+        f.g1[k] = __fadd_rn(__fadd_rn(fabsf(x), fabsf(y)), fabsf(z));
         f.ok = f.ok && isfinite(f.g2[k]);
     }
     return f;
@@ -131,6 +137,15 @@ __global__ void __launch_bounds__(kCellThreads) cell_kernel(const DirectArgs A)
     const int y_start = (lane * VEC) / G.nz, z_start = (lane * VEC) % G.nz;
     const int y_step = (32 * VEC) / G.nz, z_step = (32 * VEC) % G.nz;
     const float inx = 1.0f / G.nx, iny = 1.0f / G.ny, inz = 1.0f / G.nz;
+    // Two-row passes when whole rows fill at least 28 of the 32 lanes: with lpr = nz / VEC
+    // lanes per row, lane l < act = rpg * lpr owns columns z0 .. z0 + VEC - 1 of rows
+    // y0 + l / lpr and y0 + l / lpr + rpg of each pass of 2 * rpg rows.
+    const int lpr = G.nz / VEC;
+    const int rpg = (lpr >= 1 && lpr <= 32) ? 32 / lpr : 0;
+    const int act = rpg * lpr;
+    const bool blocked = act >= 28;
+    const int my_row = blocked ? lane / lpr : 0;
+    const int my_z0 = blocked ? (lane - my_row * lpr) * VEC : 0;
 
     int cur_b = -1;
     int a0 = 0, a1 = 0;
@@ -260,6 +275,79 @@ __global__ void __launch_bounds__(kCellThreads) cell_kernel(const DirectArgs A)
                     acc[k] = in ? fmaf(s.w, ex2_approx(-q * d2), acc[k]) : acc[k];
                 }
             };
+            if (staged && blocked) {
+                // Two-row passes: each candidate's e_z terms are formed once per column and
+                // shared by the lane's two rows.  Every voxel adds the same terms, formed by
+                // the same operations, in the same order as with add().
+                float uz[VEC];
+#pragma unroll
+                for (int k = 0; k < VEC; ++k) uz[k] = ((float)(my_z0 + k) + 0.5f) * inz;
+                const float czf = (0.5f * (float)(G.nz - 1) + 0.5f) * inz;
+                const float wzf = 0.5f * (float)(G.nz - 1) * inz;
+                for (int y0 = 0; y0 < G.ny; y0 += 2 * rpg) {
+                    const int y_end = min(y0 + 2 * rpg, G.ny) - 1;
+                    const float cyf = (0.5f * (float)(y0 + y_end) + 0.5f) * iny;
+                    const float wyf = 0.5f * (float)(y_end - y0) * iny;
+                    const int ya = y0 + my_row, yb = ya + rpg;
+                    const float uya = ((float)ya + 0.5f) * iny, uyb = ((float)yb + 0.5f) * iny;
+                    float acc0[VEC], acc1[VEC];
+#pragma unroll
+                    for (int k = 0; k < VEC; ++k) acc0[k] = acc1[k] = 0.0f;
+                    for (int cb = 0; cb < count; cb += 32) {
+                        const int j = cb + lane;
+                        bool ok = false;
+                        if (j < count) {
+                            const float2 s2 = stage2[j];
+                            const float gy = fmaxf(fabsf(wrap1<PER>(cyf - s2.x)) - wyf, 0.0f);
+                            const float gz = fmaxf(fabsf(wrap1<PER>(czf - s2.y)) - wzf, 0.0f);
+                            ok = gy <= ext_y && gz <= ext_z;
+                        }
+                        unsigned m = __ballot_sync(0xffffffffu, ok);
+                        while (m) {
+                            const int src = __ffs(m) - 1;
+                            m &= m - 1;
+                            const float4 sv = stage[cb + src];
+                            const float2 s2 = stage2[cb + src];
+                            const float eya = wrap1<PER>(uya - s2.x);
+                            const float eyb = wrap1<PER>(uyb - s2.x);
+                            const float pxa = fmaf(eya, bx, sv.x), pya = fmaf(eya, by, sv.y),
+                                        pza = fmaf(eya, bz, sv.z);
+                            const float pxb = fmaf(eyb, bx, sv.x), pyb = fmaf(eyb, by, sv.y),
+                                        pzb = fmaf(eyb, bz, sv.z);
+                            const float A2a = fmaf(pxa, pxa, fmaf(pya, pya, pza * pza));
+                            const float A2b = fmaf(pxb, pxb, fmaf(pyb, pyb, pzb * pzb));
+                            const float B2a = 2.0f * fmaf(pxa, cx, fmaf(pya, cy, pza * cz));
+                            const float B2b = 2.0f * fmaf(pxb, cx, fmaf(pyb, cy, pzb * cz));
+#pragma unroll
+                            for (int k = 0; k < VEC; ++k) {
+                                const float ez = wrap1<PER>(uz[k] - s2.y);
+                                const float d2a = fmaf(ez, fmaf(ez, cc, B2a), A2a);
+                                const float d2b = fmaf(ez, fmaf(ez, cc, B2b), A2b);
+                                bool ina = true, inb = true;
+                                if (CUT == PG_CUTOFF_SPHERE) {
+                                    ina = d2a <= r2;
+                                    inb = d2b <= r2;
+                                } else if (CUT == PG_CUTOFF_BOX) {
+                                    const float dxa = fmaf(ez, cx, pxa), dya = fmaf(ez, cy, pya),
+                                                dza = fmaf(ez, cz, pza);
+                                    const float dxb = fmaf(ez, cx, pxb), dyb = fmaf(ez, cy, pyb),
+                                                dzb = fmaf(ez, cz, pzb);
+                                    ina = fmaxf(dxa * dxa, fmaxf(dya * dya, dza * dza)) <= r2;
+                                    inb = fmaxf(dxb * dxb, fmaxf(dyb * dyb, dzb * dzb)) <= r2;
+                                }
+                                acc0[k] = ina ? fmaf(sv.w, ex2_approx(-q * d2a), acc0[k]) : acc0[k];
+                                acc1[k] = inb ? fmaf(sv.w, ex2_approx(-q * d2b), acc1[k]) : acc1[k];
+                            }
+                        }
+                    }
+                    if (lane < act) {
+                        if (ya < G.ny) store_lane<T, VEC, 0>(out, (ya * G.nz + my_z0) / VEC, acc0);
+                        if (yb < G.ny) store_lane<T, VEC, 0>(out, (yb * G.nz + my_z0) / VEC, acc1);
+                    }
+                }
+                __syncwarp();
+                continue;
+            }
             int y = y_start, z0 = z_start;
             for (int g = 0; g < nvec; g += 32) {
                 const int v = g + lane;

@@ -312,3 +312,26 @@ def test_empty_cell_and_atoms_lattice_vectors_away(pg):
     wl.batch.coords = (b.coords[atoms]).astype(np.float32)
     G0 = run(pg, wl)
     assert float((G - G0).abs().max()) <= 2 * TOL["f32"] * float(G0.abs().max())
+
+
+@pytest.mark.parametrize("cutoff,periodic", [("sphere", True), ("box", True), ("sphere", False)])
+@pytest.mark.parametrize("shape", [(17, 21, 40), (12, 19, 32)])
+def test_two_row_passes_equal_row_groups_bitwise(pg, cutoff, periodic, shape):
+    # FP32 with 16-byte stores walks each plane in two-row passes (nz = 40: 10 lanes per row,
+    # 3 rows per lane group; nz = 32: 8 lanes, 4 rows).  An output that is not 16-byte
+    # aligned takes scalar stores: nz = 40 then walks row groups of 32 voxels, nz = 32
+    # two-row passes of one row per lane group.  All add the same terms in the same order:
+    # identical bits, including the partial last pass of an odd row count, and they match the
+    # oracle.
+    wl = triclinic(n_cells=5, shape=shape)
+    wl.cutoff, wl.periodic = cutoff, periodic
+    db = pg.DeviceBatch.from_numpy(wl.batch)
+    grid = pg.Grid.from_workload(wl)
+    passes = pg.voxelize(db, grid, dtype="f32", path="direct")
+    assert pg.sync_status() == 0
+    buf = torch.zeros(passes.numel() + 1, dtype=torch.float32, device="cuda")
+    groups = buf[1:].view(passes.shape)
+    pg.voxelize(db, grid, dtype="f32", path="direct", out=groups)
+    assert pg.sync_status() == 0
+    assert torch.equal(passes, groups)
+    check(passes[:3], wl, "f32", batch=wl.batch.subset(range(3)))
