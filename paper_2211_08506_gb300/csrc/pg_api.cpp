@@ -1074,24 +1074,25 @@ pg_status pg_autotune(const pg_batch *batch, const pg_grid *grid, int32_t out_dt
     }
     cleanup();
 
-    // Fastest candidate, except that direct candidates within 2% of the fastest direct time
-    // count as tied and the tie goes to the largest chunk: fewer grabs of the shared work
-    // counter, which keeps isolated launches (graph replays, one plan run at a time) at the
-    // speed measured back to back.
-    auto better = [&](int i, int j) {
-        if (j < 0) return true;
-        if (cands[i].path == PG_PATH_DIRECT && cands[j].path == PG_PATH_DIRECT &&
-            times[i] <= 1.02f * times[j] && times[j] <= 1.02f * times[i] &&
-            cands[i].chunk_planes != cands[j].chunk_planes)
-            return cands[i].chunk_planes > cands[j].chunk_planes;
-        return times[i] < times[j];
-    };
+    // Fastest candidate, except that direct candidates within 5% of the fastest direct time
+    // count as tied and the tie goes to the largest chunk (then to the faster): fewer grabs
+    // of the shared work counter.  Launches with small chunks that timed close to the fastest
+    // ran up to a third slower as graph replays beside the adjoint.
     int best = -1, best_direct = -1, best_sep = -1;
+    float t_direct = INFINITY;
     for (size_t i = 0; i < cands.size(); ++i) {
         if (!std::isfinite(times[i])) continue;
-        if (cands[i].path == PG_PATH_DIRECT && better((int)i, best_direct)) best_direct = (int)i;
+        if (cands[i].path == PG_PATH_DIRECT) t_direct = std::min(t_direct, times[i]);
         if (cands[i].path == PG_PATH_SEPARABLE && (best_sep < 0 || times[i] < times[best_sep]))
             best_sep = (int)i;
+    }
+    for (size_t i = 0; i < cands.size(); ++i) {
+        if (!std::isfinite(times[i]) || cands[i].path != PG_PATH_DIRECT) continue;
+        if (times[i] > 1.05f * t_direct) continue;
+        if (best_direct < 0 || cands[i].chunk_planes > cands[best_direct].chunk_planes ||
+            (cands[i].chunk_planes == cands[best_direct].chunk_planes &&
+             times[i] < times[best_direct]))
+            best_direct = (int)i;
     }
     if (best_direct >= 0) best = best_direct;
     if (best_sep >= 0 && (best < 0 || times[best_sep] < times[best])) best = best_sep;
